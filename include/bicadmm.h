@@ -1,0 +1,170 @@
+/*
+ * bicadmm.h - C ABI of the B300 Bi-cADMM solver library (libbicadmm.so).
+ *
+ * Solves the sparse machine-learning problem of Sec. 2, eq. (p:SML):
+ *
+ *     minimise_x  sum_i l_i(A_i x; b_i) + ||x||_2^2 / (2 gamma)   subject to  ||x||_0 <= kappa,
+ *
+ * with the bi-linear consensus ADMM of Sec. 3 (iterations block, eqs. x-min-step ..
+ * global-lambda-updae, scaled form eqs. u-update and v-update).  The rows of A are split
+ * into N sample shards (the paper's nodes, eq. p:bi-convex) and each shard's local prox
+ * (eq. p:x-subp) is evaluated by the feature-split sharing ADMM of Sec. 3.1 over M column
+ * blocks (eqs. p:GPU;x, p:GPU;omega, p:GPU;nu; Algorithm 2).  All shards and blocks live on
+ * one GPU; there is no inter-process communication.
+ *
+ * Conventions shared by every call:
+ *  - Matrices are row-major.  A is the full m x n data matrix; shard i is a contiguous row
+ *    range and block j a contiguous column range, the first (m mod N) shards and
+ *    (n mod M) blocks one longer than the rest.
+ *  - Every call returns a status code (BICADMM_OK = 0, negative on error); no C++
+ *    exception crosses this boundary.  After an error, bicadmm_last_error() describes it.
+ *  - All GPU work is ordered on the CUDA stream given to bicadmm_create().  Calls that
+ *    return host data (get_x, get_state, step/solve with an info pointer) synchronise that
+ *    stream before returning.
+ *  - A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef BICADMM_H
+#define BICADMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bicadmm_ctx* bicadmm_t;
+
+/* Loss l(q; b) of a row (Sec. 2 lists the models; squared as eq. p:sls, without 1/2).
+ * SQUARED: (q - b)^2.  LOGISTIC: log(1 + exp(-b q)), b in {-1,+1}.
+ * SQHINGE: max(0, 1 - b q)^2, b in {-1,+1}.  SOFTMAX is reserved (not yet supported). */
+enum {
+  BICADMM_LOSS_SQUARED = 0,
+  BICADMM_LOSS_LOGISTIC = 1,
+  BICADMM_LOSS_SOFTMAX = 2,
+  BICADMM_LOSS_SQHINGE = 3
+};
+
+/* Precision of the stored A and of the per-row arithmetic on the A products.
+ * FP64: everything in FP64.  FP32: A, A x and A'd in FP32; the n-space state, the block
+ * factors and all residuals stay in FP64. */
+enum { BICADMM_PREC_FP64 = 0, BICADMM_PREC_FP32 = 1 };
+
+/* Element type of caller buffers passed to bicadmm_setup(). */
+enum { BICADMM_DTYPE_F64 = 0, BICADMM_DTYPE_F32 = 1 };
+
+enum {
+  BICADMM_OK = 0,
+  BICADMM_ERR_ARG = -1,         /* invalid argument or size */
+  BICADMM_ERR_OOM = -2,         /* device allocation failed */
+  BICADMM_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+  BICADMM_ERR_STATE = -4,       /* call out of order (e.g. step before setup) */
+  BICADMM_ERR_NUMERIC = -5,     /* non-positive pivot, NaN/Inf in a residual */
+  BICADMM_ERR_TIMEOUT = -6,     /* a device-side wait hit its limit */
+  BICADMM_ERR_UNSUPPORTED = -7  /* valid request this build does not implement */
+};
+
+/* Fields readable with bicadmm_get_state(); lengths in doubles. */
+enum {
+  BICADMM_FIELD_X = 0,      /* N x n: local estimates x_i (row i = shard i)           */
+  BICADMM_FIELD_U = 1,      /* N x n: scaled consensus duals u_i (eq. u-update)       */
+  BICADMM_FIELD_Z = 2,      /* n: consensus variable z                                */
+  BICADMM_FIELD_S = 3,      /* n: bi-linear variable s in S^kappa                     */
+  BICADMM_FIELD_OMEGA = 4,  /* m: omega-bar of eq. (p:GPU;omega), shard-major rows    */
+  BICADMM_FIELD_NU = 5,     /* m: sharing duals nu of eq. (p:GPU;nu)                  */
+  BICADMM_FIELD_SCALARS = 6 /* 3: t, v (scaled bi-linear dual, eq. v-update), tau    */
+};
+
+typedef struct {
+  int32_t loss;          /* BICADMM_LOSS_*                                              */
+  int32_t precision;     /* BICADMM_PREC_*                                              */
+  int64_t m, n;          /* rows and columns of A                                       */
+  int64_t K;             /* classes (1 for every supported loss)                        */
+  int32_t N_shards;      /* N >= 1 sample shards (1 <= N <= m)                          */
+  int32_t M_blocks;      /* M >= 1 feature blocks per shard (1 <= M <= n)               */
+  int64_t kappa;         /* sparsity level, 1 <= kappa <= n                             */
+  double gamma;          /* ridge weight, > 0                                           */
+  double rho_c;          /* consensus penalty, > 0                                      */
+  double rho_b;          /* bi-linear penalty, > 0 (0 selects 0.5 rho_c)                */
+  double rho_l;          /* sharing (feature-split) penalty, > 0 (0 selects rho_c)      */
+  int32_t inner_iters;   /* J: sharing-ADMM sweeps per outer iteration, >= 1            */
+  int32_t newton_iters;  /* cap on safeguarded Newton steps of the logistic omega prox  */
+  int32_t max_iters;     /* outer-iteration cap of bicadmm_solve()                      */
+  int32_t check_every;   /* solve(): read residuals back every this many iterations     */
+  double tol_rel;        /* solve(): stop when max(p_rel, d_rel, b_rel, i_rel) <= tol   */
+  int32_t pass_rows;     /* tuning: rows per staged panel of the A pass (0 = auto)      */
+  int32_t pass_stages;   /* tuning: panels in flight per CTA (0 = auto)                 */
+} bicadmm_params;
+
+typedef struct {
+  int32_t iters;         /* outer iterations run since setup                            */
+  int32_t converged;     /* 1 if the stop rule held at the last check                   */
+  double p_r, d_r, b_r;  /* primal, dual, bi-linear residuals (Sec. 3, Termination)     */
+  double i_r;            /* inner sharing residual ||Axbar - omega||                   */
+  double p_rel, d_rel, b_rel, i_rel;  /* relative forms used by the stop rule           */
+  double t, v, tau;      /* bi-linear scalars and the l1 multiplier / (N rho_c)         */
+  int64_t kernel_launches;  /* kernels this handle has launched since create          */
+} bicadmm_info;
+
+/* Fill *p with defaults: squared loss, FP64, gamma 10, rho_c 1, rho_b = rho_c/2,
+ * rho_l = rho_c, J = 1, 50 Newton steps, 10000 iterations, tol 1e-6, check every 10.
+ * Sizes (m, n, N, M, kappa) are zero and must be set by the caller. */
+int bicadmm_default_params(bicadmm_params* p);
+
+/* Validate *params and allocate all device buffers for that problem size.
+ * stream: a cudaStream_t (NULL = legacy default stream), not owned by the handle.
+ * On success *out owns the buffers until bicadmm_destroy().  Errors: ERR_ARG for an
+ * invalid size or penalty, ERR_OOM if the device buffers do not fit, ERR_UNSUPPORTED for
+ * a loss or width this build does not implement. */
+int bicadmm_create(const bicadmm_params* params, void* stream, bicadmm_t* out);
+
+/* Load the data and build the per-block factors; resets the iteration state to zero.
+ * A: m rows of n values with row stride lda (elements, lda >= n), type A_dtype, in host
+ *    memory (A_on_device = 0) or device memory (1).  b: m values of type b_dtype (targets
+ *    for SQUARED, labels +/-1 otherwise), host or device.  Both are copied (and converted
+ *    to the handle's precision); the caller keeps ownership and may free them on return.
+ * Builds G_ij = A_ij' A_ij and the inverse of rho_l G_ij + (1/(N gamma) + rho_c) I, the
+ * matrix of the x_ij solve of eq. (p:GPU;x), in FP64.  Errors: ERR_ARG, ERR_CUDA,
+ * ERR_NUMERIC (a block matrix is not positive definite). */
+int bicadmm_setup(bicadmm_t h, const void* A, int32_t A_dtype, int64_t lda, int32_t A_on_device,
+                  const void* b, int32_t b_dtype, int32_t b_on_device);
+
+/* Run exactly n_iters >= 0 outer iterations (each with J inner sweeps).  If info is
+ * non-NULL the stream is synchronised and *info filled; with info NULL the call only
+ * enqueues work.  Errors: ERR_STATE before setup, ERR_TIMEOUT / ERR_NUMERIC reported by
+ * the device (checked whenever info is requested). */
+int bicadmm_step(bicadmm_t h, int32_t n_iters, bicadmm_info* info);
+
+/* Iterate until the stop rule holds (checked every check_every iterations) or max_iters
+ * iterations have run in this call.  Not converging is not an error: info->converged = 0. */
+int bicadmm_solve(bicadmm_t h, bicadmm_info* info);
+
+/* Copy the model to host memory x_host[len], len = n.
+ * polished = 0: the consensus iterate z.  polished = 1: the solution of the problem
+ * restricted to S = the kappa largest |z_r| (ties to the lowest index), solved in FP64
+ * (not part of the paper's algorithm).  support_out (kappa entries, ascending) receives S
+ * when non-NULL.  Synchronises the stream. */
+int bicadmm_get_x(bicadmm_t h, double* x_host, int64_t len, int32_t polished, int64_t* support_out);
+
+/* Copy one state field (BICADMM_FIELD_*) to host memory out_host[len]; len must equal the
+ * field's length.  Synchronises the stream.  For tests, checkpoints and diagnostics. */
+int bicadmm_get_state(bicadmm_t h, int32_t field, double* out_host, int64_t len);
+
+/* Profiling: when on != 0, every launch of the fused A-pass kernel is bracketed by CUDA
+ * events on the handle's stream.  bicadmm_get_pass_time() synchronises, returns the
+ * summed device time (ms) and launch count since profiling was switched on, and resets
+ * them. */
+int bicadmm_set_profiling(bicadmm_t h, int32_t on);
+int bicadmm_get_pass_time(bicadmm_t h, double* ms_out, int64_t* launches_out);
+
+/* Free every device buffer of the handle (synchronises its stream).  NULL is accepted. */
+int bicadmm_destroy(bicadmm_t h);
+
+/* Text of the last error on this handle ("" if none); valid until the next call on h.
+ * With h == NULL returns the last error of a failed bicadmm_create(). */
+const char* bicadmm_last_error(bicadmm_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BICADMM_H */

@@ -1,0 +1,257 @@
+"""Thin ctypes binding of libbicadmm.so (include/bicadmm.h).  Argument marshalling only:
+every step of the solver runs in the library's CUDA kernels.
+
+The functions mirror the C ABI names without the ``bicadmm_`` prefix.  Device buffers
+may be passed as torch CUDA tensors (their data pointers are handed over); host buffers
+as numpy arrays or CPU tensors.  Loading fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build_lib import LIB
+
+LOSS_SQUARED, LOSS_LOGISTIC, LOSS_SOFTMAX, LOSS_SQHINGE = 0, 1, 2, 3
+PREC_FP64, PREC_FP32 = 0, 1
+DTYPE_F64, DTYPE_F32 = 0, 1
+FIELD_X, FIELD_U, FIELD_Z, FIELD_S, FIELD_OMEGA, FIELD_NU, FIELD_SCALARS = range(7)
+
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_STATE",
+          -5: "ERR_NUMERIC", -6: "ERR_TIMEOUT", -7: "ERR_UNSUPPORTED"}
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("loss", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("K", ctypes.c_int64),
+                ("N_shards", ctypes.c_int32), ("M_blocks", ctypes.c_int32),
+                ("kappa", ctypes.c_int64),
+                ("gamma", ctypes.c_double), ("rho_c", ctypes.c_double),
+                ("rho_b", ctypes.c_double), ("rho_l", ctypes.c_double),
+                ("inner_iters", ctypes.c_int32), ("newton_iters", ctypes.c_int32),
+                ("max_iters", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("tol_rel", ctypes.c_double),
+                ("pass_rows", ctypes.c_int32), ("pass_stages", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("p_r", ctypes.c_double), ("d_r", ctypes.c_double), ("b_r", ctypes.c_double),
+                ("i_r", ctypes.c_double),
+                ("p_rel", ctypes.c_double), ("d_rel", ctypes.c_double),
+                ("b_rel", ctypes.c_double), ("i_rel", ctypes.c_double),
+                ("t", ctypes.c_double), ("v", ctypes.c_double), ("tau", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class BicadmmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+_lib = None
+
+# (name, restype, argtypes) for every symbol declared in include/bicadmm.h
+_VP = ctypes.c_void_p
+SIGNATURES = [
+    ("bicadmm_default_params", ctypes.c_int, [ctypes.POINTER(Params)]),
+    ("bicadmm_create", ctypes.c_int, [ctypes.POINTER(Params), _VP, ctypes.POINTER(_VP)]),
+    ("bicadmm_setup", ctypes.c_int, [_VP, _VP, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                                     _VP, ctypes.c_int32, ctypes.c_int32]),
+    ("bicadmm_step", ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(Info)]),
+    ("bicadmm_solve", ctypes.c_int, [_VP, ctypes.POINTER(Info)]),
+    ("bicadmm_get_x", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
+                                     ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]),
+    ("bicadmm_get_state", ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.c_int64]),
+    ("bicadmm_set_profiling", ctypes.c_int, [_VP, ctypes.c_int32]),
+    ("bicadmm_get_pass_time", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_int64)]),
+    ("bicadmm_destroy", ctypes.c_int, [_VP]),
+    ("bicadmm_last_error", ctypes.c_char_p, [_VP]),
+]
+
+
+def lib():
+    """Load libbicadmm.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError("libbicadmm.so is not built (%s); run "
+                               "`python -m paper_2405_16267_b300.build_lib`" % LIB)
+        L = ctypes.CDLL(LIB)
+        for name, res, args in SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code, handle=None):
+    if code != 0:
+        msg = lib().bicadmm_last_error(handle)
+        raise BicadmmError(code, msg.decode() if msg else "")
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    _check(lib().bicadmm_default_params(ctypes.byref(p)))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def create(params: Params, stream=None):
+    """stream: a torch.cuda.Stream, an int handle, or None for the default stream."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    h = _VP()
+    _check(lib().bicadmm_create(ctypes.byref(params), _VP(stream or 0), ctypes.byref(h)))
+    return h
+
+
+def _buffer(arr):
+    """(pointer, dtype code, on_device, keepalive) for a numpy array or torch tensor."""
+    try:
+        import torch
+        if isinstance(arr, torch.Tensor):
+            if arr.dtype not in (torch.float64, torch.float32):
+                raise TypeError("A and b must be float64 or float32")
+            if not arr.is_contiguous():
+                arr = arr.contiguous()
+            code = DTYPE_F64 if arr.dtype == torch.float64 else DTYPE_F32
+            return arr.data_ptr(), code, int(arr.is_cuda), arr
+    except ImportError:  # pragma: no cover
+        pass
+    a = np.ascontiguousarray(arr)
+    if a.dtype not in (np.float64, np.float32):
+        a = a.astype(np.float64)
+    code = DTYPE_F64 if a.dtype == np.float64 else DTYPE_F32
+    return a.ctypes.data, code, 0, a
+
+
+def setup(h, A, b):
+    """A: (m, n) row-major; b: (m,).  numpy arrays / CPU tensors (host) or CUDA tensors."""
+    pa, ca, da, ka = _buffer(A)
+    pb, cb, db, kb = _buffer(b)
+    n = ka.shape[1]
+    _check(lib().bicadmm_setup(h, pa, ca, n, da, pb, cb, db), h)
+    return None
+
+
+def step(h, n_iters, info=True):
+    if info:
+        inf = Info()
+        _check(lib().bicadmm_step(h, int(n_iters), ctypes.byref(inf)), h)
+        return inf
+    _check(lib().bicadmm_step(h, int(n_iters), None), h)
+    return None
+
+
+def solve(h) -> Info:
+    inf = Info()
+    _check(lib().bicadmm_solve(h, ctypes.byref(inf)), h)
+    return inf
+
+
+def get_x(h, n, polished=False, with_support=False, kappa=None):
+    x = np.zeros(n)
+    sup = None
+    sp = None
+    if with_support:
+        sup = np.zeros(int(kappa), dtype=np.int64)
+        sp = sup.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    _check(lib().bicadmm_get_x(h, x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n,
+                               int(bool(polished)), sp), h)
+    return (x, sup) if with_support else x
+
+
+def get_state(h, field, length):
+    out = np.zeros(int(length))
+    _check(lib().bicadmm_get_state(h, int(field), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   int(length)), h)
+    return out
+
+
+def set_profiling(h, on=True):
+    _check(lib().bicadmm_set_profiling(h, int(bool(on))), h)
+
+
+def get_pass_time(h):
+    ms = ctypes.c_double()
+    cnt = ctypes.c_int64()
+    _check(lib().bicadmm_get_pass_time(h, ctypes.byref(ms), ctypes.byref(cnt)), h)
+    return ms.value, cnt.value
+
+
+def destroy(h):
+    if h:
+        _check(lib().bicadmm_destroy(h))
+
+
+def last_error(h=None) -> str:
+    msg = lib().bicadmm_last_error(h)
+    return msg.decode() if msg else ""
+
+
+class Solver:
+    """Convenience owner of one handle: create + setup on construction, destroy on close."""
+
+    def __init__(self, A, b, *, loss, N, M, kappa, gamma=10.0, rho_c=1.0, rho_b=0.0,
+                 rho_l=0.0, inner_iters=1, precision=PREC_FP64, stream=None, **extra):
+        m, n = A.shape
+        self.n, self.m, self.N, self.kappa = int(n), int(m), int(N), int(kappa)
+        self.params = default_params(loss=loss, precision=precision, m=m, n=n, N_shards=N,
+                                     M_blocks=M, kappa=kappa, gamma=gamma, rho_c=rho_c,
+                                     rho_b=rho_b, rho_l=rho_l, inner_iters=inner_iters, **extra)
+        self.h = create(self.params, stream)
+        try:
+            setup(self.h, A, b)
+        except Exception:
+            destroy(self.h)
+            self.h = None
+            raise
+
+    def step(self, n_iters, info=True):
+        return step(self.h, n_iters, info)
+
+    def solve(self):
+        return solve(self.h)
+
+    def x(self, polished=False):
+        return get_x(self.h, self.n, polished)
+
+    def state(self):
+        N, n, m = self.N, self.n, self.m
+        sc = get_state(self.h, FIELD_SCALARS, 3)
+        return dict(x=get_state(self.h, FIELD_X, N * n).reshape(N, n),
+                    u=get_state(self.h, FIELD_U, N * n).reshape(N, n),
+                    z=get_state(self.h, FIELD_Z, n), s=get_state(self.h, FIELD_S, n),
+                    omega=get_state(self.h, FIELD_OMEGA, m), nu=get_state(self.h, FIELD_NU, m),
+                    t=sc[0], v=sc[1], tau=sc[2])
+
+    def close(self):
+        if self.h:
+            destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

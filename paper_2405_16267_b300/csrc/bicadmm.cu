@@ -1,0 +1,758 @@
+// Host runtime of libbicadmm: handle state, device layout, kernel dispatch and the C ABI
+// declared in include/bicadmm.h.
+//
+// Device layout (all row-major, all owned by the handle):
+//   A       m x lda   (TA = double | float), lda = n rounded up to 32, zero padding
+//   b, omega, nu      m (TM)
+//   x, u, r  N x lda  FP64;  xlo N x lda (TA copy of x read by the A pass)
+//   z, s, w, tau_r    lda FP64;  key lda uint64 (top-kappa scratch)
+//   P       per block (i,j): n_j x ldp_j (TP = TM), ldp_j = n_j rounded up to 32
+//   slots   (G + N) x lda (TM): A'd partial sums, one row per (CTA, shard) pair
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bicadmm.h"
+#include "common.cuh"
+#include "nspace.cuh"
+#include "pass.cuh"
+#include "setup.cuh"
+
+using namespace bic;
+
+namespace {
+
+constexpr int kPassThreads = 256;
+constexpr int kGlobalThreads = 1024;
+constexpr int kDualThreads = 256;
+constexpr int kXupdThreads = 256;
+constexpr int kXupdRows = 32;
+constexpr int kCholThreads = 256;
+constexpr int kTraceCap = 4096;
+constexpr int64_t kMaxN = 32768;                 // single-CTA global step limit
+constexpr size_t kPassSmemBudget = 200 * 1024;   // dynamic smem for A-pass stages
+
+int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+std::string g_create_error;
+
+}  // namespace
+
+struct bicadmm_ctx {
+  bicadmm_params p{};
+  cudaStream_t stream = nullptr;
+  int device = 0, num_sms = 0;
+  std::string err;
+  bool ready = false;
+  int64_t launches = 0;
+  int64_t iters_done = 0;
+  bool converged = false;
+
+  // geometry
+  int N = 0, M = 0;
+  int64_t lda = 0;
+  double c0 = 0.0;
+  size_t esz = 8;  // bytes per A / m-space element
+  std::vector<int64_t> shard_row0, panel_start, G_off, P_off;
+  std::vector<int> blk_col0, blk_ldp, slot_lo, slot_hi;
+  int R = 0, S = 0, VPT = 0, G = 0, nslots = 0, max_nj = 0, max_ldp = 0, dual_chunks = 0;
+  int64_t P_panels = 0, G_total = 0, P_total = 0;
+  size_t pass_smem = 0;
+
+  // device buffers
+  void *A = nullptr, *b = nullptr, *omega = nullptr, *nu = nullptr, *slots = nullptr,
+       *xlo = nullptr, *Pm = nullptr;
+  double *x = nullptr, *u = nullptr, *r = nullptr, *z = nullptr, *s = nullptr, *w = nullptr,
+         *tau_r = nullptr, *cta_stats = nullptr, *dual_part = nullptr;
+  uint64_t* key = nullptr;
+  int64_t *d_shard_row0 = nullptr, *d_panel_start = nullptr, *d_P_off = nullptr,
+          *d_G_off = nullptr;
+  int *d_blk_col0 = nullptr, *d_blk_ldp = nullptr, *d_slot_lo = nullptr, *d_slot_hi = nullptr;
+  GlobalState* gs = nullptr;
+  Resid* trace = nullptr;
+  int* d_err = nullptr;
+  std::vector<void*> allocs;
+
+  // profiling of the A pass
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used = 0;
+  double prof_ms = 0.0;
+  int64_t prof_launches = 0;
+};
+
+namespace {
+
+int fail(bicadmm_ctx* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(h, BICADMM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+int dev_alloc(bicadmm_ctx* h, T** ptr, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, e == cudaErrorMemoryAllocation ? BICADMM_ERR_OOM : BICADMM_ERR_CUDA,
+                "cudaMalloc(" + std::to_string(bytes) + " B): " + cudaGetErrorString(e));
+  }
+  h->allocs.push_back(p);
+  *ptr = static_cast<T*>(p);
+  return BICADMM_OK;
+}
+
+void free_all(bicadmm_ctx* h) {
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  h->ev.clear();
+}
+
+// ---------------------------------------------------------------- A-pass dispatch
+template <typename TA, typename TM, int R, int VPT>
+int launch_pass_rv(bicadmm_ctx* h) {
+  auto kern = k_fused_pass<TA, TM, R, VPT, kPassThreads>;
+  static bool attr_set = false;  // per instantiation
+  if (!attr_set) {
+    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    attr_set = true;
+  }
+  PassGeometry geo{h->d_shard_row0, h->d_panel_start, h->N, h->P_panels};
+  kern<<<h->G, kPassThreads, h->pass_smem, h->stream>>>(
+      static_cast<const TA*>(h->A), h->lda, static_cast<const TA*>(h->xlo),
+      static_cast<const TM*>(h->b), static_cast<TM*>(h->omega), static_cast<TM*>(h->nu),
+      static_cast<TM*>(h->slots), h->cta_stats, geo, h->S, h->p.loss, static_cast<TM>(h->M),
+      static_cast<TM>(h->p.rho_l), h->p.newton_iters, h->d_err, kWaitLimitCycles);
+  CK(cudaGetLastError());
+  return BICADMM_OK;
+}
+
+template <typename TA, typename TM, int R>
+int launch_pass_r(bicadmm_ctx* h) {
+  switch (h->VPT) {
+    case 1: return launch_pass_rv<TA, TM, R, 1>(h);
+    case 2: return launch_pass_rv<TA, TM, R, 2>(h);
+    case 3: return launch_pass_rv<TA, TM, R, 3>(h);
+    case 4: return launch_pass_rv<TA, TM, R, 4>(h);
+    case 5: return launch_pass_rv<TA, TM, R, 5>(h);
+    case 6: return launch_pass_rv<TA, TM, R, 6>(h);
+    case 8: return launch_pass_rv<TA, TM, R, 8>(h);
+    case 12: return launch_pass_rv<TA, TM, R, 12>(h);
+    case 16: return launch_pass_rv<TA, TM, R, 16>(h);
+  }
+  return fail(h, BICADMM_ERR_UNSUPPORTED, "no A-pass variant for this width");
+}
+
+template <typename TA, typename TM>
+int launch_pass(bicadmm_ctx* h) {
+  switch (h->R) {
+    case 1: return launch_pass_r<TA, TM, 1>(h);
+    case 2: return launch_pass_r<TA, TM, 2>(h);
+    case 4: return launch_pass_r<TA, TM, 4>(h);
+    case 8: return launch_pass_r<TA, TM, 8>(h);
+  }
+  return fail(h, BICADMM_ERR_UNSUPPORTED, "no A-pass variant for this panel height");
+}
+
+template <typename TA, typename TM, int R, int VPT>
+int occupancy_rv(bicadmm_ctx* h, int* blocks) {
+  auto kern = k_fused_pass<TA, TM, R, VPT, kPassThreads>;
+  CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, kPassThreads, h->pass_smem));
+  return BICADMM_OK;
+}
+
+template <typename TA, typename TM>
+int pass_occupancy(bicadmm_ctx* h, int* blocks) {
+  // Occupancy depends on registers (VPT) and shared memory; query the chosen variant.
+#define OCC_CASE(RR, VV) \
+  if (h->R == RR && h->VPT == VV) return occupancy_rv<TA, TM, RR, VV>(h, blocks);
+#define OCC_R(RR) OCC_CASE(RR, 1) OCC_CASE(RR, 2) OCC_CASE(RR, 3) OCC_CASE(RR, 4) OCC_CASE(RR, 5) \
+  OCC_CASE(RR, 6) OCC_CASE(RR, 8) OCC_CASE(RR, 12) OCC_CASE(RR, 16)
+  OCC_R(1) OCC_R(2) OCC_R(4) OCC_R(8)
+#undef OCC_R
+#undef OCC_CASE
+  return fail(h, BICADMM_ERR_UNSUPPORTED, "no A-pass variant");
+}
+
+int pick_vpt(int64_t nvec) {
+  static const int opts[] = {1, 2, 3, 4, 5, 6, 8, 12, 16};
+  for (int v : opts)
+    if (static_cast<int64_t>(v) * kPassThreads >= nvec) return v;
+  return -1;
+}
+
+// ---------------------------------------------------------------- one outer iteration
+template <typename TM>
+int run_iterations(bicadmm_ctx* h, int n_iters) {
+  const int N = h->N, M = h->M;
+  const int64_t lda = h->lda, n = h->p.n;
+  const dim3 rhs_grid(static_cast<unsigned>((lda + 255) / 256), N);
+  const dim3 xupd_grid(static_cast<unsigned>((h->max_nj + kXupdRows - 1) / kXupdRows), M, N);
+  const size_t xupd_smem = static_cast<size_t>(h->max_ldp) * sizeof(TM);
+  const unsigned wm_grid = static_cast<unsigned>((n + 255) / 256);
+  const dim3 dual_grid(h->dual_chunks, N);
+  for (int it = 0; it < n_iters; ++it) {
+    for (int jj = 0; jj < h->p.inner_iters; ++jj) {
+      k_rhs<TM><<<rhs_grid, 256, 0, h->stream>>>(static_cast<const TM*>(h->slots), h->d_slot_lo,
+                                                   h->d_slot_hi, h->x, h->u, h->z, h->r, lda,
+                                                   h->p.rho_l, h->p.rho_c, h->c0);
+      k_xupd<TM, TM, kXupdThreads, kXupdRows><<<xupd_grid, kXupdThreads, xupd_smem, h->stream>>>(
+          static_cast<const TM*>(h->Pm), h->d_P_off, h->d_blk_col0, h->d_blk_ldp, h->r, h->x,
+          static_cast<TM*>(h->xlo), M, lda);
+      if (h->prof) {
+        if (h->ev_used + 2 > h->ev.size()) {
+          for (int q = 0; q < 64; ++q) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            h->ev.push_back(e);
+          }
+        }
+        CK(cudaEventRecord(h->ev[h->ev_used], h->stream));
+      }
+      int rc = (h->p.precision == BICADMM_PREC_FP64) ? launch_pass<double, double>(h)
+                                                      : launch_pass<float, float>(h);
+      if (rc != BICADMM_OK) return rc;
+      if (h->prof) {
+        CK(cudaEventRecord(h->ev[h->ev_used + 1], h->stream));
+        h->ev_used += 2;
+      }
+      h->launches += 3;
+    }
+    k_wmean<<<wm_grid, 256, 0, h->stream>>>(h->x, h->u, h->w, N, n, lda);
+    k_global<kGlobalThreads><<<1, kGlobalThreads, 0, h->stream>>>(
+        h->w, h->z, h->s, h->tau_r, h->key, h->gs, h->trace, kTraceCap, n, h->p.kappa, N,
+        h->p.rho_c, h->p.rho_b, h->d_err);
+    k_dual<kDualThreads><<<dual_grid, kDualThreads, 0, h->stream>>>(
+        h->u, h->x, h->z, h->dual_part, h->cta_stats, h->G, h->gs, h->trace, kTraceCap, N, n,
+        lda, h->p.rho_c, h->d_err);
+    CK(cudaGetLastError());
+    h->launches += 3;
+    h->iters_done += 1;
+  }
+  return BICADMM_OK;
+}
+
+int check_device_error(bicadmm_ctx* h) {
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  switch (e) {
+    case DEV_OK: return BICADMM_OK;
+    case DEV_TIMEOUT_PASS: return fail(h, BICADMM_ERR_TIMEOUT, "A-pass wait timed out on the device");
+    case DEV_NONPOS_PIVOT: return fail(h, BICADMM_ERR_NUMERIC, "non-positive pivot in a block factorisation");
+    case DEV_NONFINITE: return fail(h, BICADMM_ERR_NUMERIC, "non-finite residual (NaN/Inf in the iterates)");
+    case DEV_ZT_NOCONV: return fail(h, BICADMM_ERR_NUMERIC, "(z,t) root iteration did not terminate");
+  }
+  return fail(h, BICADMM_ERR_CUDA, "unknown device error " + std::to_string(e));
+}
+
+int fill_info(bicadmm_ctx* h, bicadmm_info* info) {
+  GlobalState g;
+  CK(cudaMemcpyAsync(&g, h->gs, sizeof(g), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  std::memset(info, 0, sizeof(*info));
+  info->iters = static_cast<int32_t>(g.iter);
+  info->converged = h->converged ? 1 : 0;
+  info->t = g.t;
+  info->v = g.v;
+  info->tau = g.tau;
+  info->kernel_launches = h->launches;
+  if (g.iter > 0) {
+    Resid rec;
+    CK(cudaMemcpyAsync(&rec, h->trace + (g.iter - 1) % kTraceCap, sizeof(rec),
+                       cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    info->p_r = rec.p_r; info->d_r = rec.d_r; info->b_r = rec.b_r; info->i_r = rec.i_r;
+    info->p_rel = rec.p_rel; info->d_rel = rec.d_rel; info->b_rel = rec.b_rel;
+    info->i_rel = rec.i_rel;
+  }
+  return check_device_error(h);
+}
+
+int validate(const bicadmm_params* p, std::string& why) {
+  if (!p) { why = "params is NULL"; return BICADMM_ERR_ARG; }
+  if (p->loss == BICADMM_LOSS_SOFTMAX) { why = "softmax loss is not supported by this build"; return BICADMM_ERR_UNSUPPORTED; }
+  if (p->loss != BICADMM_LOSS_SQUARED && p->loss != BICADMM_LOSS_LOGISTIC && p->loss != BICADMM_LOSS_SQHINGE) { why = "unknown loss"; return BICADMM_ERR_ARG; }
+  if (p->precision != BICADMM_PREC_FP64 && p->precision != BICADMM_PREC_FP32) { why = "unknown precision"; return BICADMM_ERR_ARG; }
+  if (p->m < 1 || p->n < 1) { why = "m and n must be >= 1"; return BICADMM_ERR_ARG; }
+  if (p->K != 1) { why = "K must be 1 for the supported losses"; return BICADMM_ERR_ARG; }
+  if (p->N_shards < 1 || p->N_shards > p->m) { why = "need 1 <= N_shards <= m"; return BICADMM_ERR_ARG; }
+  if (p->M_blocks < 1 || p->M_blocks > p->n) { why = "need 1 <= M_blocks <= n"; return BICADMM_ERR_ARG; }
+  if (p->kappa < 1 || p->kappa > p->n) { why = "need 1 <= kappa <= n"; return BICADMM_ERR_ARG; }
+  if (!(p->gamma > 0) || !(p->rho_c > 0) || !(p->rho_b >= 0) || !(p->rho_l >= 0)) { why = "gamma, rho_c must be > 0 and rho_b, rho_l >= 0"; return BICADMM_ERR_ARG; }
+  if (p->inner_iters < 1 || p->newton_iters < 1) { why = "inner_iters and newton_iters must be >= 1"; return BICADMM_ERR_ARG; }
+  if (p->max_iters < 0 || p->check_every < 1) { why = "max_iters >= 0 and check_every >= 1 required"; return BICADMM_ERR_ARG; }
+  if (p->n > kMaxN) { why = "n > 32768 is not supported by this build"; return BICADMM_ERR_UNSUPPORTED; }
+  if (p->pass_rows != 0 && p->pass_rows != 1 && p->pass_rows != 2 && p->pass_rows != 4 && p->pass_rows != 8) { why = "pass_rows must be 0, 1, 2, 4 or 8"; return BICADMM_ERR_ARG; }
+  if (p->pass_stages < 0 || p->pass_stages > 8) { why = "pass_stages must be in [0, 8]"; return BICADMM_ERR_ARG; }
+  return BICADMM_OK;
+}
+
+int build_geometry(bicadmm_ctx* h) {
+  const bicadmm_params& p = h->p;
+  h->N = p.N_shards;
+  h->M = p.M_blocks;
+  h->esz = p.precision == BICADMM_PREC_FP64 ? 8 : 4;
+  h->lda = round_up(p.n, 32);
+  h->c0 = 1.0 / (h->N * p.gamma) + p.rho_c;
+  // shards / blocks: contiguous, first (total mod parts) one longer
+  h->shard_row0.assign(h->N + 1, 0);
+  for (int i = 0; i < h->N; ++i) h->shard_row0[i + 1] = h->shard_row0[i] + p.m / h->N + (i < p.m % h->N ? 1 : 0);
+  h->blk_col0.assign(h->M + 1, 0);
+  h->blk_ldp.assign(h->M, 0);
+  h->max_nj = 0;
+  h->max_ldp = 0;
+  for (int j = 0; j < h->M; ++j) {
+    const int nj = static_cast<int>(p.n / h->M + (j < p.n % h->M ? 1 : 0));
+    h->blk_col0[j + 1] = h->blk_col0[j] + nj;
+    h->blk_ldp[j] = static_cast<int>(round_up(nj, 32));
+    h->max_nj = std::max(h->max_nj, nj);
+    h->max_ldp = std::max(h->max_ldp, h->blk_ldp[j]);
+  }
+  if (h->max_nj > 8192) return fail(h, BICADMM_ERR_UNSUPPORTED, "feature blocks wider than 8192 columns are not supported; raise M_blocks");
+  h->G_off.assign(static_cast<size_t>(h->N) * h->M, 0);
+  h->P_off.assign(static_cast<size_t>(h->N) * h->M, 0);
+  int64_t go = 0, po = 0;
+  for (int i = 0; i < h->N; ++i)
+    for (int j = 0; j < h->M; ++j) {
+      const int nj = h->blk_col0[j + 1] - h->blk_col0[j];
+      h->G_off[i * h->M + j] = go;
+      h->P_off[i * h->M + j] = po;
+      go += static_cast<int64_t>(nj) * nj;
+      po += static_cast<int64_t>(nj) * h->blk_ldp[j];
+    }
+  h->G_total = go;
+  h->P_total = po;
+
+  // A-pass panel geometry
+  const size_t row_bytes = static_cast<size_t>(h->lda) * h->esz;
+  int R = p.pass_rows;
+  if (R == 0) {
+    R = 1;
+    for (int cand : {8, 4, 2}) {
+      if (cand * row_bytes <= 48 * 1024 && 2 * cand * row_bytes <= kPassSmemBudget) { R = cand; break; }
+    }
+  }
+  int S = p.pass_stages;
+  if (S == 0) {
+    S = static_cast<int>(std::min<size_t>(4, kPassSmemBudget / (R * row_bytes)));
+    if (S < 1) S = 1;
+  }
+  if (static_cast<size_t>(S) * R * row_bytes > kPassSmemBudget)
+    return fail(h, BICADMM_ERR_UNSUPPORTED, "A-pass stages do not fit in shared memory (rows too wide)");
+  h->R = R;
+  h->S = S;
+  const int64_t nvec = h->lda / (h->esz == 8 ? 2 : 4);
+  h->VPT = pick_vpt(nvec);
+  if (h->VPT < 0) return fail(h, BICADMM_ERR_UNSUPPORTED, "rows too wide for the register-resident A-pass accumulators");
+  h->pass_smem = h->esz == 8 ? fused_pass_smem<double, double>(R, S, h->lda, kPassThreads)
+                             : fused_pass_smem<float, float>(R, S, h->lda, kPassThreads);
+  h->panel_start.assign(h->N + 1, 0);
+  for (int i = 0; i < h->N; ++i) {
+    const int64_t mi = h->shard_row0[i + 1] - h->shard_row0[i];
+    h->panel_start[i + 1] = h->panel_start[i] + (mi + R - 1) / R;
+  }
+  h->P_panels = h->panel_start[h->N];
+  int occ = 0;
+  int rc = h->esz == 8 ? pass_occupancy<double, double>(h, &occ) : pass_occupancy<float, float>(h, &occ);
+  if (rc != BICADMM_OK) return rc;
+  if (occ < 1) return fail(h, BICADMM_ERR_UNSUPPORTED, "A-pass variant cannot be resident on an SM");
+  h->G = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(occ) * h->num_sms, h->P_panels));
+  // slots: CTA c writes slot (c + shard) for every shard it touches
+  h->slot_lo.assign(h->N, 0);
+  h->slot_hi.assign(h->N, 0);
+  auto owner = [&](int64_t panel) {
+    // CTA c owns [c*P/G, (c+1)*P/G)
+    int64_t c = panel * h->G / h->P_panels;
+    while (c > 0 && c * h->P_panels / h->G > panel) --c;
+    while ((c + 1) * h->P_panels / h->G <= panel) ++c;
+    return static_cast<int>(c);
+  };
+  for (int i = 0; i < h->N; ++i) {
+    h->slot_lo[i] = owner(h->panel_start[i]) + i;
+    h->slot_hi[i] = owner(h->panel_start[i + 1] - 1) + i;
+  }
+  h->nslots = h->G + h->N;
+  h->dual_chunks = static_cast<int>((p.n + kDualThreads - 1) / kDualThreads);
+  return BICADMM_OK;
+}
+
+int allocate(bicadmm_ctx* h) {
+  const int64_t m = h->p.m, lda = h->lda, N = h->N;
+  const size_t es = h->esz;
+  int rc;
+#define AL(ptr, bytes) if ((rc = dev_alloc(h, &(ptr), (bytes))) != BICADMM_OK) return rc
+  AL(h->A, static_cast<size_t>(m) * lda * es);
+  AL(h->b, m * es);
+  AL(h->omega, m * es);
+  AL(h->nu, m * es);
+  AL(h->slots, static_cast<size_t>(h->nslots) * lda * es);
+  AL(h->xlo, static_cast<size_t>(N) * lda * es);
+  AL(h->Pm, static_cast<size_t>(h->P_total) * es);
+  AL(h->x, N * lda * sizeof(double));
+  AL(h->u, N * lda * sizeof(double));
+  AL(h->r, N * lda * sizeof(double));
+  AL(h->z, lda * sizeof(double));
+  AL(h->s, lda * sizeof(double));
+  AL(h->w, lda * sizeof(double));
+  AL(h->tau_r, lda * sizeof(double));
+  AL(h->key, lda * sizeof(uint64_t));
+  AL(h->cta_stats, static_cast<size_t>(h->G) * 4 * sizeof(double));
+  AL(h->dual_part, static_cast<size_t>(N) * h->dual_chunks * 2 * sizeof(double));
+  AL(h->d_shard_row0, (N + 1) * sizeof(int64_t));
+  AL(h->d_panel_start, (N + 1) * sizeof(int64_t));
+  AL(h->d_P_off, h->P_off.size() * sizeof(int64_t));
+  AL(h->d_G_off, h->G_off.size() * sizeof(int64_t));
+  AL(h->d_blk_col0, h->blk_col0.size() * sizeof(int));
+  AL(h->d_blk_ldp, h->blk_ldp.size() * sizeof(int));
+  AL(h->d_slot_lo, N * sizeof(int));
+  AL(h->d_slot_hi, N * sizeof(int));
+  AL(h->gs, sizeof(GlobalState));
+  AL(h->trace, kTraceCap * sizeof(Resid));
+  AL(h->d_err, sizeof(int));
+#undef AL
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->stream);
+  };
+  CK(up(h->d_shard_row0, h->shard_row0.data(), (N + 1) * sizeof(int64_t)));
+  CK(up(h->d_panel_start, h->panel_start.data(), (N + 1) * sizeof(int64_t)));
+  CK(up(h->d_P_off, h->P_off.data(), h->P_off.size() * sizeof(int64_t)));
+  CK(up(h->d_G_off, h->G_off.data(), h->G_off.size() * sizeof(int64_t)));
+  CK(up(h->d_blk_col0, h->blk_col0.data(), h->blk_col0.size() * sizeof(int)));
+  CK(up(h->d_blk_ldp, h->blk_ldp.data(), h->blk_ldp.size() * sizeof(int)));
+  CK(up(h->d_slot_lo, h->slot_lo.data(), N * sizeof(int)));
+  CK(up(h->d_slot_hi, h->slot_hi.data(), N * sizeof(int)));
+  CK(cudaStreamSynchronize(h->stream));
+  return BICADMM_OK;
+}
+
+int reset_state(bicadmm_ctx* h) {
+  const int64_t m = h->p.m, lda = h->lda, N = h->N;
+  const size_t es = h->esz;
+  CK(cudaMemsetAsync(h->omega, 0, m * es, h->stream));
+  CK(cudaMemsetAsync(h->nu, 0, m * es, h->stream));
+  CK(cudaMemsetAsync(h->slots, 0, static_cast<size_t>(h->nslots) * lda * es, h->stream));
+  CK(cudaMemsetAsync(h->xlo, 0, static_cast<size_t>(N) * lda * es, h->stream));
+  CK(cudaMemsetAsync(h->x, 0, N * lda * sizeof(double), h->stream));
+  CK(cudaMemsetAsync(h->u, 0, N * lda * sizeof(double), h->stream));
+  CK(cudaMemsetAsync(h->r, 0, N * lda * sizeof(double), h->stream));
+  CK(cudaMemsetAsync(h->z, 0, lda * sizeof(double), h->stream));
+  CK(cudaMemsetAsync(h->s, 0, lda * sizeof(double), h->stream));
+  CK(cudaMemsetAsync(h->w, 0, lda * sizeof(double), h->stream));
+  CK(cudaMemsetAsync(h->cta_stats, 0, static_cast<size_t>(h->G) * 4 * sizeof(double), h->stream));
+  CK(cudaMemsetAsync(h->gs, 0, sizeof(GlobalState), h->stream));
+  CK(cudaMemsetAsync(h->trace, 0, kTraceCap * sizeof(Resid), h->stream));
+  CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
+  h->iters_done = 0;
+  h->converged = false;
+  return BICADMM_OK;
+}
+
+// Copy rows [0, m) of a caller matrix (host or device, dtype) into the padded device layout.
+template <typename TOUT>
+int load_matrix(bicadmm_ctx* h, const void* src, int dtype, int64_t lda_src, int on_device,
+                TOUT* dst, int64_t rows, int64_t cols, int64_t lda_dst) {
+  const size_t in_es = dtype == BICADMM_DTYPE_F64 ? 8 : 4;
+  auto convert = [&](const void* s, TOUT* d, int64_t nr) -> int {
+    const int64_t total = nr * lda_dst;
+    const unsigned grid = static_cast<unsigned>(std::min<int64_t>((total + 255) / 256, 65535));
+    if (dtype == BICADMM_DTYPE_F64)
+      k_convert_rows<double, TOUT><<<grid, 256, 0, h->stream>>>(static_cast<const double*>(s), lda_src, d, lda_dst, nr, cols);
+    else
+      k_convert_rows<float, TOUT><<<grid, 256, 0, h->stream>>>(static_cast<const float*>(s), lda_src, d, lda_dst, nr, cols);
+    CK(cudaGetLastError());
+    h->launches += 1;
+    return BICADMM_OK;
+  };
+  if (on_device) return convert(src, dst, rows);
+  // Host source: stream chunks through a device staging buffer (at most 256 MB).
+  const int64_t row_in = lda_src * static_cast<int64_t>(in_es);
+  int64_t chunk = std::max<int64_t>(1, (256ll << 20) / std::max<int64_t>(row_in, 1));
+  chunk = std::min(chunk, rows);
+  void* stage = nullptr;
+  cudaError_t e = cudaMalloc(&stage, static_cast<size_t>(chunk) * row_in);
+  if (e != cudaSuccess) { cudaGetLastError(); return fail(h, BICADMM_ERR_OOM, "staging buffer allocation failed"); }
+  int rc = BICADMM_OK;
+  for (int64_t r0 = 0; r0 < rows && rc == BICADMM_OK; r0 += chunk) {
+    const int64_t nr = std::min(chunk, rows - r0);
+    // the last row may be shorter than lda_src: copy exactly (nr-1)*lda_src + cols elements
+    const size_t bytes = (static_cast<size_t>(nr - 1) * lda_src + cols) * in_es;
+    e = cudaMemcpyAsync(stage, static_cast<const char*>(src) + r0 * row_in, bytes,
+                        cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) { rc = fail(h, BICADMM_ERR_CUDA, std::string("H2D copy: ") + cudaGetErrorString(e)); break; }
+    rc = convert(stage, dst + r0 * lda_dst, nr);
+    if (rc == BICADMM_OK) {
+      e = cudaStreamSynchronize(h->stream);
+      if (e != cudaSuccess) rc = fail(h, BICADMM_ERR_CUDA, std::string("sync: ") + cudaGetErrorString(e));
+    }
+  }
+  cudaStreamSynchronize(h->stream);
+  cudaFree(stage);
+  return rc;
+}
+
+template <typename TA>
+int build_factors(bicadmm_ctx* h) {
+  double *G = nullptr, *W = nullptr;
+  cudaError_t e = cudaMalloc(&G, std::max<int64_t>(h->G_total, 1) * sizeof(double));
+  if (e != cudaSuccess) { cudaGetLastError(); return fail(h, BICADMM_ERR_OOM, "Gram buffer allocation failed"); }
+  e = cudaMalloc(&W, std::max<int64_t>(h->G_total, 1) * sizeof(double));
+  if (e != cudaSuccess) { cudaGetLastError(); cudaFree(G); return fail(h, BICADMM_ERR_OOM, "factor scratch allocation failed"); }
+  int rc = BICADMM_OK;
+  const int T = (h->max_nj + 63) / 64;
+  const dim3 ggrid(T * (T + 1) / 2, h->M, h->N);
+  k_gram<TA, TA><<<ggrid, 256, 0, h->stream>>>(static_cast<const TA*>(h->A), h->lda, h->d_shard_row0,
+                                               h->d_blk_col0, G, h->d_G_off, h->M);
+  h->launches += 1;
+  e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    auto kc = k_chol_inv<TA, kCholThreads>;
+    const size_t sm = static_cast<size_t>(h->max_nj) * sizeof(double);
+    if (sm > 48 * 1024) e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
+    if (e == cudaSuccess) {
+      kc<<<h->N * h->M, kCholThreads, sm, h->stream>>>(G, h->d_G_off, W, h->d_blk_col0, h->d_blk_ldp, h->M,
+                                                    h->p.rho_l, h->c0, static_cast<TA*>(h->Pm),
+                                                    h->d_P_off, h->d_err);
+      h->launches += 1;
+      e = cudaGetLastError();
+    }
+  }
+  if (e != cudaSuccess) rc = fail(h, BICADMM_ERR_CUDA, std::string("factor kernels: ") + cudaGetErrorString(e));
+  cudaError_t e2 = cudaStreamSynchronize(h->stream);
+  if (rc == BICADMM_OK && e2 != cudaSuccess) rc = fail(h, BICADMM_ERR_CUDA, std::string("factor sync: ") + cudaGetErrorString(e2));
+  cudaFree(G);
+  cudaFree(W);
+  if (rc != BICADMM_OK) return rc;
+  return check_device_error(h);
+}
+
+}  // namespace
+
+// =============================================================================== C ABI
+
+extern "C" {
+
+int bicadmm_default_params(bicadmm_params* p) {
+  if (!p) return BICADMM_ERR_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->loss = BICADMM_LOSS_SQUARED;
+  p->precision = BICADMM_PREC_FP64;
+  p->K = 1;
+  p->N_shards = 1;
+  p->M_blocks = 1;
+  p->gamma = 10.0;
+  p->rho_c = 1.0;
+  p->rho_b = 0.0;
+  p->rho_l = 0.0;
+  p->inner_iters = 1;
+  p->newton_iters = 50;
+  p->max_iters = 10000;
+  p->check_every = 10;
+  p->tol_rel = 1e-6;
+  return BICADMM_OK;
+}
+
+int bicadmm_create(const bicadmm_params* params, void* stream, bicadmm_t* out) {
+  g_create_error.clear();
+  if (!out) { g_create_error = "out is NULL"; return BICADMM_ERR_ARG; }
+  *out = nullptr;
+  std::string why;
+  int rc = validate(params, why);
+  if (rc != BICADMM_OK) { g_create_error = why; return rc; }
+  bicadmm_ctx* h = new bicadmm_ctx();
+  h->p = *params;
+  if (h->p.rho_b == 0.0) h->p.rho_b = 0.5 * h->p.rho_c;
+  if (h->p.rho_l == 0.0) h->p.rho_l = h->p.rho_c;
+  h->stream = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("no usable CUDA device: ") + cudaGetErrorString(e);
+    delete h;
+    return BICADMM_ERR_CUDA;
+  }
+  rc = build_geometry(h);
+  if (rc == BICADMM_OK) rc = allocate(h);
+  if (rc == BICADMM_OK) rc = reset_state(h);
+  if (rc != BICADMM_OK) {
+    g_create_error = h->err;
+    free_all(h);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return BICADMM_OK;
+}
+
+int bicadmm_setup(bicadmm_t h, const void* A, int32_t A_dtype, int64_t lda, int32_t A_on_device,
+                  const void* b, int32_t b_dtype, int32_t b_on_device) {
+  if (!h) return BICADMM_ERR_ARG;
+  if (!A || !b) return fail(h, BICADMM_ERR_ARG, "A and b must be non-NULL");
+  if (A_dtype != BICADMM_DTYPE_F64 && A_dtype != BICADMM_DTYPE_F32) return fail(h, BICADMM_ERR_ARG, "A_dtype must be F64 or F32");
+  if (b_dtype != BICADMM_DTYPE_F64 && b_dtype != BICADMM_DTYPE_F32) return fail(h, BICADMM_ERR_ARG, "b_dtype must be F64 or F32");
+  if (lda < h->p.n) return fail(h, BICADMM_ERR_ARG, "lda must be >= n");
+  h->ready = false;
+  h->err.clear();
+  int rc = reset_state(h);
+  if (rc != BICADMM_OK) return rc;
+  if (h->esz == 8) {
+    rc = load_matrix<double>(h, A, A_dtype, lda, A_on_device, static_cast<double*>(h->A), h->p.m, h->p.n, h->lda);
+    if (rc == BICADMM_OK) rc = load_matrix<double>(h, b, b_dtype, 1, b_on_device, static_cast<double*>(h->b), h->p.m, 1, 1);
+    if (rc == BICADMM_OK) rc = build_factors<double>(h);
+  } else {
+    rc = load_matrix<float>(h, A, A_dtype, lda, A_on_device, static_cast<float*>(h->A), h->p.m, h->p.n, h->lda);
+    if (rc == BICADMM_OK) rc = load_matrix<float>(h, b, b_dtype, 1, b_on_device, static_cast<float*>(h->b), h->p.m, 1, 1);
+    if (rc == BICADMM_OK) rc = build_factors<float>(h);
+  }
+  if (rc != BICADMM_OK) return rc;
+  h->ready = true;
+  return BICADMM_OK;
+}
+
+int bicadmm_step(bicadmm_t h, int32_t n_iters, bicadmm_info* info) {
+  if (!h) return BICADMM_ERR_ARG;
+  if (!h->ready) return fail(h, BICADMM_ERR_STATE, "bicadmm_step before a successful bicadmm_setup");
+  if (n_iters < 0) return fail(h, BICADMM_ERR_ARG, "n_iters must be >= 0");
+  int rc = h->esz == 8 ? run_iterations<double>(h, n_iters) : run_iterations<float>(h, n_iters);
+  if (rc != BICADMM_OK) return rc;
+  if (info) return fill_info(h, info);
+  return BICADMM_OK;
+}
+
+int bicadmm_solve(bicadmm_t h, bicadmm_info* info) {
+  if (!h) return BICADMM_ERR_ARG;
+  if (!h->ready) return fail(h, BICADMM_ERR_STATE, "bicadmm_solve before a successful bicadmm_setup");
+  bicadmm_info loc;
+  int done = 0;
+  h->converged = false;
+  while (done < h->p.max_iters) {
+    const int k = std::min(h->p.check_every, h->p.max_iters - done);
+    int rc = bicadmm_step(h, k, &loc);
+    if (rc != BICADMM_OK) return rc;
+    done += k;
+    const double mx = std::max(std::max(loc.p_rel, loc.d_rel), std::max(loc.b_rel, loc.i_rel));
+    if (mx <= h->p.tol_rel) { h->converged = true; break; }
+  }
+  loc.converged = h->converged ? 1 : 0;
+  if (info) {
+    int rc = fill_info(h, info);
+    if (rc != BICADMM_OK) return rc;
+  }
+  return BICADMM_OK;
+}
+
+int bicadmm_get_x(bicadmm_t h, double* x_host, int64_t len, int32_t polished, int64_t* support_out) {
+  if (!h) return BICADMM_ERR_ARG;
+  if (!h->ready) return fail(h, BICADMM_ERR_STATE, "bicadmm_get_x before setup");
+  if (!x_host || len != h->p.n) return fail(h, BICADMM_ERR_ARG, "x_host must hold n doubles");
+  if (polished || support_out) return fail(h, BICADMM_ERR_UNSUPPORTED, "polished output is not available in this build");
+  CK(cudaMemcpyAsync(x_host, h->z, h->p.n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return check_device_error(h);
+}
+
+int bicadmm_get_state(bicadmm_t h, int32_t field, double* out_host, int64_t len) {
+  if (!h) return BICADMM_ERR_ARG;
+  if (!out_host) return fail(h, BICADMM_ERR_ARG, "out_host is NULL");
+  const int64_t n = h->p.n, m = h->p.m, N = h->N;
+  auto need = [&](int64_t L) { return len == L; };
+  switch (field) {
+    case BICADMM_FIELD_X:
+    case BICADMM_FIELD_U: {
+      if (!need(N * n)) return fail(h, BICADMM_ERR_ARG, "length must be N*n");
+      const double* src = field == BICADMM_FIELD_X ? h->x : h->u;
+      CK(cudaMemcpy2DAsync(out_host, n * sizeof(double), src, h->lda * sizeof(double), n * sizeof(double), N,
+                           cudaMemcpyDeviceToHost, h->stream));
+      break;
+    }
+    case BICADMM_FIELD_Z:
+    case BICADMM_FIELD_S:
+      if (!need(n)) return fail(h, BICADMM_ERR_ARG, "length must be n");
+      CK(cudaMemcpyAsync(out_host, field == BICADMM_FIELD_Z ? h->z : h->s, n * sizeof(double),
+                         cudaMemcpyDeviceToHost, h->stream));
+      break;
+    case BICADMM_FIELD_OMEGA:
+    case BICADMM_FIELD_NU: {
+      if (!need(m)) return fail(h, BICADMM_ERR_ARG, "length must be m");
+      const void* src = field == BICADMM_FIELD_OMEGA ? h->omega : h->nu;
+      if (h->esz == 8) {
+        CK(cudaMemcpyAsync(out_host, src, m * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      } else {
+        std::vector<float> tmp(m);
+        CK(cudaMemcpyAsync(tmp.data(), src, m * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        for (int64_t q = 0; q < m; ++q) out_host[q] = tmp[q];
+      }
+      break;
+    }
+    case BICADMM_FIELD_SCALARS: {
+      if (!need(3)) return fail(h, BICADMM_ERR_ARG, "length must be 3");
+      GlobalState g;
+      CK(cudaMemcpyAsync(&g, h->gs, sizeof(g), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      out_host[0] = g.t;
+      out_host[1] = g.v;
+      out_host[2] = g.tau;
+      break;
+    }
+    default:
+      return fail(h, BICADMM_ERR_ARG, "unknown field");
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return check_device_error(h);
+}
+
+int bicadmm_set_profiling(bicadmm_t h, int32_t on) {
+  if (!h) return BICADMM_ERR_ARG;
+  h->prof = on != 0;
+  h->ev_used = 0;
+  h->prof_ms = 0.0;
+  h->prof_launches = 0;
+  return BICADMM_OK;
+}
+
+int bicadmm_get_pass_time(bicadmm_t h, double* ms_out, int64_t* launches_out) {
+  if (!h) return BICADMM_ERR_ARG;
+  CK(cudaStreamSynchronize(h->stream));
+  double tot = 0.0;
+  for (size_t q = 0; q + 1 < h->ev_used; q += 2) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev[q], h->ev[q + 1]));
+    tot += ms;
+  }
+  if (ms_out) *ms_out = tot;
+  if (launches_out) *launches_out = static_cast<int64_t>(h->ev_used / 2);
+  h->ev_used = 0;
+  return BICADMM_OK;
+}
+
+int bicadmm_destroy(bicadmm_t h) {
+  if (!h) return BICADMM_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  free_all(h);
+  delete h;
+  return BICADMM_OK;
+}
+
+const char* bicadmm_last_error(bicadmm_t h) {
+  if (!h) return g_create_error.c_str();
+  return h->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,402 @@
+// n-space kernels of one Bi-cADMM outer iteration (everything except the A pass).
+//
+//   k_rhs       r_i = rho_l q_i + rho_c (z - u_i) - c0 x_i, q_i = sum of the pass slots of
+//               shard i (fixed order)                              eq. (p:GPU;x) right side
+//   k_xupd      x_ij += P_ij r_ij   (block-diagonal explicit inverse, one warp per row)
+//   k_wmean     w = (1/N) sum_i (x_i + u_i)                        eq. (global-z-t-updae)
+//   k_global    (z, t) root solve, top-kappa s, v, d_r, b_r        eqs. (global-z-t-updae),
+//               (single CTA)                                       (s-update-final), (v-update)
+//   k_dual      u_i += x_i - z, p_r, inner residual                eq. (u-update), Termination
+#pragma once
+
+#include "common.cuh"
+
+namespace bic {
+
+// Per-iteration residual record (mirrored by the host).
+struct Resid {
+  double p_r, d_r, b_r, i_r;
+  double p_rel, d_rel, b_rel, i_rel;
+  double t, v, tau, znorm;
+  int64_t iter;
+  int64_t zt_steps;
+};
+
+// Device-resident scalars of the global step.
+struct GlobalState {
+  double t, v, tau;
+  int64_t iter;         // outer iterations completed
+  unsigned int ticket;  // arrival counter of k_dual's last-CTA reduction
+  unsigned int pad;
+};
+
+// ------------------------------------------------------------------------------ k_rhs
+template <typename TM>
+__global__ void k_rhs(const TM* __restrict__ slots, const int* __restrict__ slot_lo,
+                      const int* __restrict__ slot_hi, const double* __restrict__ x,
+                      const double* __restrict__ u, const double* __restrict__ z,
+                      double* __restrict__ r, int64_t lda, double rho_l, double rho_c,
+                      double c0) {
+  const int i = blockIdx.y;
+  const int64_t col = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (col >= lda) return;
+  double q = 0.0;
+  for (int sl = slot_lo[i]; sl <= slot_hi[i]; ++sl) q += static_cast<double>(slots[sl * lda + col]);
+  const int64_t o = i * lda + col;
+  r[o] = rho_l * q + rho_c * (z[col] - u[o]) - c0 * x[o];
+}
+
+// ------------------------------------------------------------------------------ k_xupd
+// Grid (row tiles, M, N), XT threads.  P_ij is stored row-major with row stride ldp_j
+// (a multiple of 32, zero padded) at P_off[i*M + j].
+template <typename TP> struct PVec;
+template <> struct PVec<float> { using type = float4; static constexpr int n = 4; };
+template <> struct PVec<double> { using type = double2; static constexpr int n = 2; };
+
+template <typename TP, typename TX, int XT, int ROWS>
+__global__ void __launch_bounds__(XT)
+k_xupd(const TP* __restrict__ P, const int64_t* __restrict__ P_off,
+       const int* __restrict__ blk_col0, const int* __restrict__ blk_ldp,
+       const double* __restrict__ r, double* __restrict__ x, TX* __restrict__ xlo, int M,
+       int64_t lda) {
+  using V = typename PVec<TP>::type;
+  constexpr int VE = PVec<TP>::n;
+  extern __shared__ __align__(16) unsigned char xs_raw[];
+  TP* rs = reinterpret_cast<TP*>(xs_raw);
+  const int i = blockIdx.z, j = blockIdx.y;
+  const int col0 = blk_col0[j], nj = blk_col0[j + 1] - col0, ldp = blk_ldp[j];
+  const int row_begin = blockIdx.x * ROWS;
+  if (row_begin >= nj) return;
+  for (int k = threadIdx.x; k < ldp; k += XT)
+    rs[k] = k < nj ? static_cast<TP>(r[i * lda + col0 + k]) : TP(0);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const TP* Pb = P + P_off[i * M + j];
+  const V* rv = reinterpret_cast<const V*>(rs);
+  const int nv = ldp / VE;
+  for (int row = row_begin + warp; row < row_begin + ROWS && row < nj; row += XT / 32) {
+    const V* pr = reinterpret_cast<const V*>(Pb + static_cast<int64_t>(row) * ldp);
+    TP acc = TP(0);
+    for (int k = lane; k < nv; k += 32) {
+      const V a = pr[k], bb = rv[k];
+      const TP* ae = reinterpret_cast<const TP*>(&a);
+      const TP* be = reinterpret_cast<const TP*>(&bb);
+#pragma unroll
+      for (int e = 0; e < VE; ++e) acc = fma(ae[e], be[e], acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      const int64_t o = i * lda + col0 + row;
+      const double xn = x[o] + static_cast<double>(acc);
+      x[o] = xn;
+      xlo[o] = static_cast<TX>(xn);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------ k_wmean
+__global__ void k_wmean(const double* __restrict__ x, const double* __restrict__ u,
+                        double* __restrict__ w, int N, int64_t n, int64_t lda) {
+  const int64_t col = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (col >= n) return;
+  double acc = 0.0;
+  for (int i = 0; i < N; ++i) acc += x[i * lda + col] + u[i * lda + col];
+  w[col] = acc / N;
+}
+
+// ------------------------------------------------------------------------------ top-kappa
+// Select the kappa largest |z_r| (ties: lowest index) inside one CTA of GT threads by an
+// MSB-first radix select on the IEEE bit patterns of |z_r| (non-negative doubles order as
+// unsigned integers), then rank the entries equal to the threshold by index with a
+// block-wide scan.  Each thread owns a contiguous chunk of at most 32 indices and returns
+// its selection as a bit mask.  key[] is global scratch of n entries.
+template <int GT>
+__device__ uint32_t block_topk_select(const double* __restrict__ z, uint64_t* __restrict__ key,
+                                      int64_t n, int64_t kappa, unsigned int* hist,
+                                      long long* sh, int64_t& chunk_begin, int& chunk_len) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int64_t r = tid; r < n; r += GT) key[r] = __double_as_longlong(fabs(z[r]));
+  __syncthreads();
+  uint64_t prefix = 0, mask = 0;
+  int64_t remaining = kappa;
+  for (int shift = 56; shift >= 0; shift -= 8) {
+    for (int b = tid; b < 256; b += GT) hist[b] = 0;
+    __syncthreads();
+    for (int64_t r = tid; r < n; r += GT) {
+      const uint64_t k = key[r];
+      if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      // lane l owns bins 255-8l .. 248-8l (descending); suffix counts from the top.
+      unsigned int cnt[8], tot = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) { cnt[q] = hist[255 - 8 * lane - q]; tot += cnt[q]; }
+      unsigned int incl = tot;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+      }
+      const unsigned int excl = incl - tot;
+      // the threshold digit is in the first lane whose inclusive count reaches remaining
+      const bool here = static_cast<int64_t>(excl) < remaining &&
+                        static_cast<int64_t>(incl) >= remaining;
+      if (here) {
+        unsigned int run = excl;
+        for (int q = 0; q < 8; ++q) {
+          if (static_cast<int64_t>(run + cnt[q]) >= remaining) {
+            sh[0] = 255 - 8 * lane - q;
+            sh[1] = remaining - run;
+            break;
+          }
+          run += cnt[q];
+        }
+      }
+    }
+    __syncthreads();
+    prefix |= static_cast<uint64_t>(sh[0]) << shift;
+    mask |= static_cast<uint64_t>(255) << shift;
+    remaining = sh[1];
+    __syncthreads();
+  }
+  // prefix = threshold key; take every key above it and the first `remaining` equal ones.
+  const int64_t ch = (n + GT - 1) / GT;
+  chunk_begin = tid * ch;
+  int64_t cend = chunk_begin + ch < n ? chunk_begin + ch : n;
+  chunk_len = chunk_begin < cend ? static_cast<int>(cend - chunk_begin) : 0;
+  unsigned int eq = 0;
+  for (int q = 0; q < chunk_len; ++q) eq += key[chunk_begin + q] == prefix;
+  // exclusive scan of eq over threads
+  unsigned int incl = eq;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned int y = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += y;
+  }
+  __shared__ unsigned int wsum[32];
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned int v = lane < GT / 32 ? wsum[lane] : 0u;
+    unsigned int inc = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc += y;
+    }
+    wsum[lane] = inc - v;
+  }
+  __syncthreads();
+  unsigned int rank = wsum[warp] + incl - eq;
+  uint32_t sel = 0;
+  for (int q = 0; q < chunk_len; ++q) {
+    const uint64_t k = key[chunk_begin + q];
+    bool take = k > prefix;
+    if (k == prefix) { take = static_cast<int64_t>(rank) < remaining; ++rank; }
+    if (take) sel |= 1u << q;
+  }
+  __syncthreads();
+  return sel;
+}
+
+// ------------------------------------------------------------------------------ k_global
+// One CTA.  Reads w (k_wmean), the previous s, t, v; writes z, s, t, v, tau and the
+// d_r / b_r part of the residual record.  tau_r[] and key[] are global scratch (n each).
+template <int GT>
+__global__ void __launch_bounds__(GT, 1)
+k_global(const double* __restrict__ w, double* __restrict__ z, double* __restrict__ s,
+         double* __restrict__ tau_r, uint64_t* __restrict__ key, GlobalState* gs, Resid* trace,
+         int trace_cap, int64_t n, int64_t kappa, int N, double rho_c, double rho_b,
+         int* err) {
+  __shared__ double red[32 * 4];
+  __shared__ unsigned int hist[256];
+  __shared__ long long sh[2];
+  const int tid = threadIdx.x;
+  const double v = gs->v;
+  const double beta = N * rho_c / rho_b;
+
+  // h(0) and the breakpoints tau_r = |w_r| / (1 - sign(w_r) s_r) (inf: never zeroed).
+  double a1[1] = {0.0};
+  for (int64_t r = tid; r < n; r += GT) {
+    const double wr = w[r], sr = s[r], sg = dsign(wr);
+    a1[0] += sr * wr - fabs(wr);
+    // w_r = 0: z_r stays 0 for every tau >= 0 (never active).  sign(w_r) s_r = 1: never
+    // zeroed, but contributes c_r = e_r = 0.
+    tau_r[r] = wr == 0.0 ? 0.0 : (sg * sr < 1.0 ? fabs(wr) / (1.0 - sg * sr) : HUGE_VAL);
+  }
+  block_sum<1>(a1, red);
+  const double h0 = v + a1[0];
+
+  double tau = 0.0;
+  int64_t steps = 0;
+  if (h0 < 0.0) {
+    // h is concave, increasing and piecewise linear.  Newton from the left: the root of the
+    // linear piece through tau_k never overshoots the root of h, and the active set
+    // {r : tau_r > tau} only shrinks, so the iteration ends (exactly) when it stops changing.
+    auto active_sums = [&](double at, double (&o)[3]) {
+      o[0] = o[1] = o[2] = 0.0;
+      for (int64_t r = tid; r < n; r += GT) {
+        if (tau_r[r] > at) {
+          const double wr = w[r], sr = s[r], sg = dsign(wr);
+          o[0] += sr * wr - fabs(wr);
+          o[1] += (sr - sg) * (sr - sg);
+          o[2] += 1.0;
+        }
+      }
+      block_sum<3>(o, red);
+    };
+    double cur[3];
+    active_sums(0.0, cur);
+    const int64_t max_steps = n + 2;
+    for (;;) {
+      const double tn = -(v + cur[0]) / (beta + cur[1]);
+      double nxt[3];
+      active_sums(tn, nxt);
+      ++steps;
+      tau = tn;
+      if (nxt[2] >= cur[2]) break;
+      cur[0] = nxt[0]; cur[1] = nxt[1]; cur[2] = nxt[2];
+      if (steps > max_steps) {
+        if (tid == 0) set_err(err, DEV_ZT_NOCONV);
+        break;
+      }
+    }
+  }
+
+  // z = S_tau(w + tau s) (z = w when tau = 0); norms for t and the dual residual.
+  double a4[4] = {0.0, 0.0, 0.0, 0.0};  // ||z||_1, s'w, ||z - z_prev||^2, ||z||^2
+  for (int64_t r = tid; r < n; r += GT) {
+    const double wr = w[r], sr = s[r];
+    double zn;
+    if (tau > 0.0) {
+      const double y = wr + tau * sr;
+      const double m = fabs(y) - tau;
+      zn = m > 0.0 ? dsign(y) * m : 0.0;
+    } else {
+      zn = wr;
+    }
+    const double zo = z[r];
+    a4[0] += fabs(zn);
+    a4[1] += sr * wr;
+    a4[2] += (zn - zo) * (zn - zo);
+    a4[3] += zn * zn;
+    z[r] = zn;
+  }
+  block_sum<4>(a4, red);
+  const double t = tau > 0.0 ? a4[0] : a4[1] + v;
+
+  // s: top-kappa signs of z scaled by clamp((t - v)/T, -1, 1).
+  int64_t cb;
+  int cl;
+  const uint32_t sel = block_topk_select<GT>(z, key, n, kappa, hist, sh, cb, cl);
+  double a1b[1] = {0.0};
+  for (int q = 0; q < cl; ++q)
+    if (sel >> q & 1u) a1b[0] += fabs(z[cb + q]);
+  block_sum<1>(a1b, red);
+  const double T = a1b[0];
+  double scale = 0.0;
+  if (T > 0.0) {
+    scale = (t - v) / T;
+    scale = scale > 1.0 ? 1.0 : (scale < -1.0 ? -1.0 : scale);
+  }
+  double a1c[1] = {0.0};
+  for (int q = 0; q < cl; ++q) {
+    const double zr = z[cb + q];
+    const double sn = (sel >> q & 1u) ? scale * dsign(zr) : 0.0;
+    s[cb + q] = sn;
+    a1c[0] += zr * sn;
+  }
+  block_sum<1>(a1c, red);
+  const double g = a1c[0] - t;
+  if (tid == 0) {
+    const double vn = v + g;
+    Resid& rec = trace[gs->iter % trace_cap];
+    const double dz = sqrt(a4[2]), zn = sqrt(a4[3]);
+    rec.d_r = sqrt(static_cast<double>(N)) * rho_c * dz;
+    rec.b_r = fabs(g);
+    rec.d_rel = dz / fmax(zn, 1e-30);
+    rec.b_rel = fabs(g) / fmax(t, 1e-30);
+    rec.t = t;
+    rec.v = vn;
+    rec.tau = tau;
+    rec.znorm = zn;
+    rec.iter = gs->iter + 1;
+    rec.zt_steps = steps;
+    gs->t = t;
+    gs->v = vn;
+    gs->tau = tau;
+  }
+}
+
+// ------------------------------------------------------------------------------ k_dual
+// Grid (chunks, N), DT threads.  u_i += x_i - z; per-(shard, chunk) sums of ||x_i - z||^2
+// and ||x_i||^2; the last CTA to finish reduces them (fixed order) with the pass's
+// inner-residual sums into the residual record and advances the iteration counter.
+template <int DT>
+__global__ void __launch_bounds__(DT)
+k_dual(double* __restrict__ u, const double* __restrict__ x, const double* __restrict__ z,
+       double* __restrict__ part, const double* __restrict__ cta_stats, int G, GlobalState* gs,
+       Resid* trace, int trace_cap, int N, int64_t n, int64_t lda, double rho_c, int* err) {
+  __shared__ double red[32 * 2];
+  __shared__ bool last;
+  const int i = blockIdx.y, nch = gridDim.x;
+  const int64_t col = static_cast<int64_t>(blockIdx.x) * DT + threadIdx.x;
+  double a[2] = {0.0, 0.0};
+  if (col < n) {
+    const int64_t o = i * lda + col;
+    const double xv = x[o], dv = xv - z[col];
+    u[o] += dv;
+    a[0] = dv * dv;
+    a[1] = xv * xv;
+  }
+  block_sum<2>(a, red);
+  if (threadIdx.x == 0) {
+    part[(static_cast<int64_t>(i) * nch + blockIdx.x) * 2 + 0] = a[0];
+    part[(static_cast<int64_t>(i) * nch + blockIdx.x) * 2 + 1] = a[1];
+    __threadfence();
+    const unsigned int total = gridDim.x * gridDim.y;
+    last = atomicAdd(&gs->ticket, 1u) == total - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // Final reduction by one warp in a fixed order.
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    double pr = 0.0, nx = 0.0;
+    for (int ii = 0; ii < N; ++ii) {
+      double s0 = 0.0, s1 = 0.0;
+      for (int cidx = lane; cidx < nch; cidx += 32) {
+        s0 += part[(static_cast<int64_t>(ii) * nch + cidx) * 2 + 0];
+        s1 += part[(static_cast<int64_t>(ii) * nch + cidx) * 2 + 1];
+      }
+      s0 = warp_sum(s0);
+      s1 = warp_sum(s1);
+      pr += sqrt(s0);
+      nx += sqrt(s1);
+    }
+    double q0 = 0.0, q1 = 0.0, q2 = 0.0;
+    for (int g = lane; g < G; g += 32) {
+      q0 += cta_stats[g * 4 + 0];
+      q1 += cta_stats[g * 4 + 1];
+      q2 += cta_stats[g * 4 + 2];
+    }
+    q0 = warp_sum(q0);
+    q1 = warp_sum(q1);
+    q2 = warp_sum(q2);
+    if (lane == 0) {
+      Resid& rec = trace[gs->iter % trace_cap];
+      rec.p_r = pr;
+      rec.p_rel = pr / fmax(fmax(nx, N * rec.znorm), 1e-30);
+      rec.i_r = sqrt(q0);
+      rec.i_rel = sqrt(q0) / fmax(fmax(sqrt(q1), sqrt(q2)), 1e-30);
+      const double chk = rec.p_r + rec.d_r + rec.b_r + rec.i_r + rec.t + rec.v;
+      if (!isfinite(chk)) set_err(err, DEV_NONFINITE);
+      gs->iter += 1;
+      gs->ticket = 0;
+    }
+  }
+}
+
+}  // namespace bic

@@ -1,0 +1,160 @@
+// Setup kernels: input conversion into the padded device layout, the per-block Gram
+// matrices G_ij = A_ij' A_ij, and the FP64 Cholesky factorisation and inverse of
+// rho_l G_ij + c0 I (the system matrix of the x_ij solve of eq. (p:GPU;x)).
+#pragma once
+
+#include "common.cuh"
+
+namespace bic {
+
+// dst[r, c] = src[r, c] for c < n, 0 for n <= c < lda_dst.
+template <typename TIN, typename TOUT>
+__global__ void k_convert_rows(const TIN* __restrict__ src, int64_t lda_src,
+                               TOUT* __restrict__ dst, int64_t lda_dst, int64_t rows, int64_t n) {
+  const int64_t total = rows * lda_dst;
+  for (int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = idx / lda_dst, c = idx - r * lda_dst;
+    dst[idx] = c < n ? static_cast<TOUT>(src[r * lda_src + c]) : TOUT(0);
+  }
+}
+
+// G_ij = A_ij' A_ij for every shard i and block j, FP64 output (row stride n_j).
+// Grid (upper-triangle tile pairs, M, N); 256 threads compute a 64 x 64 tile, 4 x 4 each.
+// TC is the multiply type; with TC = float the running sums are moved into FP64 every
+// 256 rows to bound the FP32 accumulation error.
+template <typename TA, typename TC>
+__global__ void __launch_bounds__(256)
+k_gram(const TA* __restrict__ A, int64_t lda, const int64_t* __restrict__ shard_row0,
+       const int* __restrict__ blk_col0, double* __restrict__ G, const int64_t* __restrict__ G_off,
+       int M) {
+  constexpr int TILE = 64, KC = 32;
+  __shared__ TC As[KC][TILE + 1];
+  __shared__ TC Bs[KC][TILE + 1];
+  const int i = blockIdx.z, j = blockIdx.y;
+  const int col0 = blk_col0[j], nj = blk_col0[j + 1] - col0;
+  const int T = (nj + TILE - 1) / TILE;
+  int q = blockIdx.x, ti = 0;
+  while (q >= T - ti) { q -= T - ti; ++ti; if (ti >= T) return; }
+  const int tj = ti + q;  // ti <= tj
+  const int64_t r_begin = shard_row0[i], r_end = shard_row0[i + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  TC acc[4][4];
+  double acc2[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int bq = 0; bq < 4; ++bq) { acc[a][bq] = TC(0); acc2[a][bq] = 0.0; }
+  int since_flush = 0;
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += KC) {
+    for (int e = threadIdx.x; e < KC * TILE; e += 256) {
+      const int k = e / TILE, cc = e - k * TILE;
+      const int64_t row = r0 + k;
+      const int ca = ti * TILE + cc, cb = tj * TILE + cc;
+      As[k][cc] = (row < r_end && ca < nj) ? static_cast<TC>(A[row * lda + col0 + ca]) : TC(0);
+      Bs[k][cc] = (row < r_end && cb < nj) ? static_cast<TC>(A[row * lda + col0 + cb]) : TC(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < KC; ++k) {
+      TC av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) { av[a] = As[k][ty * 4 + a]; bv[a] = Bs[k][tx * 4 + a]; }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int bq = 0; bq < 4; ++bq) acc[a][bq] = fma(av[a], bv[bq], acc[a][bq]);
+    }
+    __syncthreads();
+    if (++since_flush == 8) {
+      since_flush = 0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int bq = 0; bq < 4; ++bq) { acc2[a][bq] += static_cast<double>(acc[a][bq]); acc[a][bq] = TC(0); }
+    }
+  }
+  double* Gb = G + G_off[i * M + j];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int bq = 0; bq < 4; ++bq) {
+      const int ra = ti * TILE + ty * 4 + a, cb = tj * TILE + tx * 4 + bq;
+      if (ra < nj && cb < nj) {
+        const double val = acc2[a][bq] + static_cast<double>(acc[a][bq]);
+        Gb[static_cast<int64_t>(ra) * nj + cb] = val;
+        Gb[static_cast<int64_t>(cb) * nj + ra] = val;
+      }
+    }
+}
+
+// One CTA per block (i, j): K = rho_l G + c0 I (in place in G, lower triangle), Cholesky
+// K = L L' in place, then P = K^-1 by forward and back substitution, one column per
+// thread, in FP64 scratch W; finally P is written in TP with row stride ldp (zero padded).
+template <typename TP, int CT>
+__global__ void __launch_bounds__(CT)
+k_chol_inv(double* __restrict__ G, const int64_t* __restrict__ G_off, double* __restrict__ W,
+           const int* __restrict__ blk_col0, const int* __restrict__ blk_ldp, int M,
+           double rho_l, double c0, TP* __restrict__ P, const int64_t* __restrict__ P_off,
+           int* __restrict__ err) {
+  extern __shared__ double colk[];
+  const int blk = blockIdx.x, i = blk / M, j = blk - i * M;
+  const int nj = blk_col0[j + 1] - blk_col0[j], ldp = blk_ldp[j];
+  double* K = G + G_off[blk];
+  double* Wb = W + G_off[blk];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NWP = CT / 32;
+  for (int64_t e = tid; e < static_cast<int64_t>(nj) * nj; e += CT) {
+    const int a = static_cast<int>(e / nj), bq = static_cast<int>(e - static_cast<int64_t>(a) * nj);
+    K[e] = rho_l * K[e] + (a == bq ? c0 : 0.0);
+  }
+  __syncthreads();
+  __shared__ int bad;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int k = 0; k < nj; ++k) {
+    if (tid == 0) {
+      const double dkk = K[static_cast<int64_t>(k) * nj + k];
+      if (!(dkk > 0.0)) { bad = 1; set_err(err, DEV_NONPOS_PIVOT); }
+      K[static_cast<int64_t>(k) * nj + k] = dkk > 0.0 ? sqrt(dkk) : 1.0;
+    }
+    __syncthreads();
+    const double dk = K[static_cast<int64_t>(k) * nj + k];
+    for (int a = k + 1 + tid; a < nj; a += CT) {
+      const double l = K[static_cast<int64_t>(a) * nj + k] / dk;
+      K[static_cast<int64_t>(a) * nj + k] = l;
+      colk[a] = l;
+    }
+    __syncthreads();
+    for (int a = k + 1 + warp; a < nj; a += NWP) {
+      const double lak = colk[a];
+      double* Ka = K + static_cast<int64_t>(a) * nj;
+      for (int bq = k + 1 + lane; bq <= a; bq += 32) Ka[bq] -= lak * colk[bq];
+    }
+    __syncthreads();
+  }
+  if (bad) return;
+  // Columns of K^-1: L y = e_c, then L' p = y.
+  for (int cidx = tid; cidx < nj; cidx += CT) {
+    for (int a = 0; a < nj; ++a) {
+      double sacc = (a == cidx) ? 1.0 : 0.0;
+      const double* La = K + static_cast<int64_t>(a) * nj;
+      for (int bq = 0; bq < a; ++bq) sacc -= La[bq] * Wb[static_cast<int64_t>(bq) * nj + cidx];
+      Wb[static_cast<int64_t>(a) * nj + cidx] = sacc / La[a];
+    }
+    for (int a = nj - 1; a >= 0; --a) {
+      double sacc = Wb[static_cast<int64_t>(a) * nj + cidx];
+      for (int bq = a + 1; bq < nj; ++bq)
+        sacc -= K[static_cast<int64_t>(bq) * nj + a] * Wb[static_cast<int64_t>(bq) * nj + cidx];
+      Wb[static_cast<int64_t>(a) * nj + cidx] = sacc / K[static_cast<int64_t>(a) * nj + a];
+    }
+  }
+  __syncthreads();
+  TP* Pb = P + P_off[blk];
+  for (int64_t e = tid; e < static_cast<int64_t>(nj) * ldp; e += CT) {
+    const int a = static_cast<int>(e / ldp), bq = static_cast<int>(e - static_cast<int64_t>(a) * ldp);
+    Pb[e] = bq < nj ? static_cast<TP>(Wb[static_cast<int64_t>(a) * nj + bq]) : TP(0);
+  }
+}
+
+}  // namespace bic

@@ -1,0 +1,75 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol the header
+declares, and rejects invalid arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2405_16267_b300 import bicadmm as bc
+from paper_2405_16267_b300 import build_lib
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "bicadmm.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bicadmm_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_lib.build()
+    return bc.lib()
+
+
+def test_header_declares_expected_api():
+    names = declared_functions()
+    for required in ["bicadmm_create", "bicadmm_setup", "bicadmm_solve", "bicadmm_step",
+                     "bicadmm_get_x", "bicadmm_destroy"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    cdll = ctypes.CDLL(build_lib.LIB)
+    missing = [n for n in declared_functions() if not hasattr(cdll, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    bound = {name for name, _, _ in bc.SIGNATURES}
+    assert set(declared_functions()) <= bound
+
+
+def test_struct_layouts_match_header(lib):
+    # default_params writes every field; sizes are checked against the C struct via offsets
+    p = bc.default_params()
+    assert p.gamma == 10.0 and p.rho_c == 1.0 and p.inner_iters == 1 and p.K == 1
+    assert ctypes.sizeof(bc.Params) == 112
+    assert ctypes.sizeof(bc.Info) == 104
+
+
+@pytest.mark.parametrize("field,value,code", [
+    ("m", 0, -1), ("n", 0, -1), ("kappa", 0, -1), ("kappa", 101, -1), ("N_shards", 0, -1),
+    ("N_shards", 51, -1), ("M_blocks", 101, -1), ("gamma", 0.0, -1), ("rho_c", -1.0, -1),
+    ("inner_iters", 0, -1), ("K", 2, -1), ("loss", 2, -7), ("loss", 9, -1), ("precision", 5, -1),
+    ("pass_rows", 3, -1), ("n", 40000, -7),
+])
+def test_create_rejects_bad_arguments_without_gpu(lib, field, value, code):
+    p = bc.default_params(m=50, n=100, N_shards=2, M_blocks=2, kappa=5)
+    if field == "n" and value == 40000:
+        p.kappa = 5
+    setattr(p, field, value)
+    h = ctypes.c_void_p()
+    rc = lib.bicadmm_create(ctypes.byref(p), None, ctypes.byref(h))
+    assert rc == code
+    assert not h.value
+    assert len(bc.last_error(None)) > 0
+
+
+def test_null_handle_calls_are_safe(lib):
+    assert lib.bicadmm_destroy(None) == 0
+    assert lib.bicadmm_step(None, 1, None) == -1
+    assert lib.bicadmm_default_params(None) == -1
