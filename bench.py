@@ -1,0 +1,338 @@
+#!/usr/bin/env python3
+"""Benchmark of the Bi-cADMM hot path on one B300 (replicas on N GPUs).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Workload: sparse logistic regression, A 200000 x 5000 FP32 with Toeplitz column
+correlation 0.3^|i-j|, 50-sparse planted model, labels sign(A x* + N(0, 0.5^2)),
+N = 16 sample shards, M = 8 feature blocks, kappa = 50, rho = 0.5 (synthetic, seeded).
+A step is one outer Bi-cADMM iteration (one inner sweep: x-update, fused A pass,
+global (z,t,s,v) step, dual update).  `value` is outer iterations per second with A
+resident in HBM; `e2e` is the same metric through the public C ABI from pinned host
+buffers (create + setup + K iterations + get_x, H2D of A and b inside the timed region).
+
+--impl reference times the FP64 CPU oracle on a bounded sample (one of the 16 shards)
+and extrapolates to the whole workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2405_16267_b300 import synth  # noqa: E402
+
+WORKLOAD = dict(name="sparse_logistic_200000x5000_fp32", m=200000, n=5000, nnz=50, corr=0.3,
+                noise=0.5, N=16, M=8, kappa=50, rho=0.5, gamma=10.0, seed=0)
+METRIC = "ADMM iters/s"
+UNIT = "iters/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--m", type=int, default=None, help="override rows (profiling small cases)")
+    ap.add_argument("--pass-rows", type=int, default=0)
+    ap.add_argument("--pass-stages", type=int, default=0)
+    return ap.parse_args()
+
+
+def config_dict(wl, extra=None):
+    d = {"workload": wl["name"], "m": wl["m"], "n": wl["n"], "N_shards": wl["N"],
+         "M_blocks": wl["M"], "kappa": wl["kappa"], "rho": wl["rho"], "gamma": wl["gamma"],
+         "loss": "logistic", "inner_iters": 1, "A_dtype": "f32",
+         "l2": "inputs larger than L2 (A is %.1f GB)" % (wl["m"] * wl["n"] * 4 / 1e9),
+         "parallelism": "replicas"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# ----------------------------------------------------------------------------- data
+
+def generate(wl, rows=None):
+    """Seeded FP32 A (pinned host tensor when torch is available) and labels b."""
+    m = wl["m"]
+    r0, r1 = (0, m) if rows is None else rows
+    shards = synth.split_ranges(m, wl["N"])
+    # generate shard by shard in a thread pool (the RNG and IIR filter release the GIL)
+    from concurrent.futures import ThreadPoolExecutor
+    pieces = []
+    for (a, b_) in shards:
+        lo, hi = max(a, r0), min(b_, r1)
+        if lo < hi:
+            pieces.append((lo, hi))
+    out_A = np.empty((r1 - r0, wl["n"]), dtype=np.float32)
+    out_b = np.empty(r1 - r0)
+
+    def job(rng):
+        lo, hi = rng
+        P = synth.sparse_logistic(m=m, n=wl["n"], nnz=wl["nnz"], corr=wl["corr"],
+                                  noise=wl["noise"], seed=wl["seed"], rows=(lo, hi))
+        out_A[lo - r0:hi - r0] = P.A
+        out_b[lo - r0:hi - r0] = P.b
+        return P.x_star
+
+    with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        xs = list(ex.map(job, pieces))
+    return out_A, out_b, xs[0]
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index, interval_ms=50):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.QUERY,
+                                       "--format=csv,noheader,nounits", "-lms", str(interval_ms)],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        self.marks = []
+
+    def mark(self):
+        self.marks.append(time.time())
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [l.strip().split(", ") for l in self.f.read().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def run_gpu(args, rank, world):
+    import torch
+    from paper_2405_16267_b300 import bicadmm as bc
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = dict(WORKLOAD)
+    if args.m:
+        wl["m"] = args.m
+    A_np, b_np, _ = generate(wl)
+    A_pin = torch.from_numpy(A_np).pin_memory()
+    b_pin = torch.from_numpy(b_np).pin_memory()
+    del A_np
+    stream = torch.cuda.current_stream(dev)
+    params = dict(loss=bc.LOSS_LOGISTIC, precision=bc.PREC_FP32, N=wl["N"], M=wl["M"],
+                  kappa=wl["kappa"], gamma=wl["gamma"], rho_c=wl["rho"],
+                  pass_rows=args.pass_rows, pass_stages=args.pass_stages)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---- device-resident timing
+    s = bc.Solver(A_pin, b_pin, stream=stream, **params)
+    s.step(args.warmup, info=False)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    time.sleep(0.15)
+    bc.set_profiling(s.h, True)
+    info0 = s.step(0)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(args.steps, info=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    pass_ms, pass_launches = bc.get_pass_time(s.h)
+    info1 = s.step(0)
+    launches = info1.kernel_launches - info0.kernel_launches
+    s.close()
+
+    # ---- end-to-end through the public API from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        p = bc.default_params(loss=params["loss"], precision=params["precision"], m=wl["m"],
+                              n=wl["n"], N_shards=wl["N"], M_blocks=wl["M"], kappa=wl["kappa"],
+                              gamma=wl["gamma"], rho_c=wl["rho"])
+        h = bc.create(p, stream)
+        bc.setup(h, A_pin, b_pin)
+        bc.step(h, args.steps, info=False)
+        x = bc.get_x(h, wl["n"])
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        bc.destroy(h)
+        barrier()
+        e2e_s = t1 - t0
+        h2d = A_pin.numel() * A_pin.element_size() + b_pin.numel() * b_pin.element_size()
+        d2h = x.nbytes
+        e2e = {"value": args.steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "seconds": e2e_s, "includes": "create+setup(H2D A,b; Gram; Cholesky; inverse)+K iterations+get_x"}
+
+    # max over ranks
+    t_local = ms / 1000.0
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_local], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        if e2e:
+            te = torch.tensor([e2e["seconds"]], device=dev)
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+            e2e["value"] = world * args.steps / float(te.item())
+    else:
+        t_max = t_local
+
+    hbm, peak_kind = peaks()
+    m, n = wl["m"], wl["n"]
+    pass_bytes = m * n * 4 + 4 * m * 4  # A once + b, nu read, omega, nu written (FP32)
+    avg_pass_s = pass_ms / 1000.0 / max(pass_launches, 1)
+    achieved = pass_bytes / avg_pass_s / 1e9
+    result = {
+        "metric": METRIC, "value": world * args.steps / t_max, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded; shapes and distributions of the paper-style logistic workload)",
+        "config": config_dict(wl),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "kernel": "k_fused_pass", "peak_kind": peak_kind + " copy bandwidth",
+                     "algorithmic_bytes_per_launch": pass_bytes,
+                     "avg_launch_ms": avg_pass_s * 1e3, "launches_timed": pass_launches},
+        "clocks": clk,
+        "gpu_launches": int(launches),
+        "e2e": e2e,
+    }
+    return result
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        return max([d.get("num_threads", 1) for d in threadpool_info()] or [1])
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_oracle_sample(wl, steps, warmup, budget_s=90.0):
+    """Time the FP64 oracle on shard 0 of the workload (a bounded sample) and extrapolate
+    one outer iteration of the whole workload as N times one sampled shard iteration."""
+    from oracle import bicadmm_ref as ref
+    r0, r1 = synth.split_ranges(wl["m"], wl["N"])[0]
+    A, b, _ = generate(wl, rows=(r0, r1))
+    A = A.astype(np.float64)
+    o = ref.BiCADMM(A, b, ref.LOSS_LOGISTIC, 1, wl["M"], wl["kappa"], gamma=wl["gamma"],
+                    rho_c=wl["rho"])
+    o.iterate(max(1, min(warmup, 2)))
+    t0 = time.perf_counter()
+    done = 0
+    while done < steps:
+        o.iterate(1)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = (time.perf_counter() - t0) / done
+    value = 1.0 / (wl["N"] * dt)
+    sample = ("shard 0 of %d (%d x %d rows x cols, FP64) with M=%d blocks: %d outer iterations "
+              "timed, %.3f s each; full iteration extrapolated as %d x that"
+              % (wl["N"], r1 - r0, wl["n"], wl["M"], done, dt, wl["N"]))
+    return {"value": value, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+            "sample": sample, "steps_timed": done}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    wl = dict(WORKLOAD)
+    cb = run_oracle_sample(wl, args.steps, args.warmup)
+    return {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
+            "n_gpus": world, "steps": cb["steps_timed"], "warmup": args.warmup,
+            "ms_per_step": 1000.0 / cb["value"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            "config": config_dict(wl), "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "gpu":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        res = run_gpu(args, rank, world)
+        if rank == 0 and not args.no_cpu_baseline and world == 1:
+            res["cpu_baseline"] = run_oracle_sample(dict(WORKLOAD), steps=8, warmup=1, budget_s=20.0)
+    if world > 1 and args.impl == "gpu":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()
