@@ -156,6 +156,32 @@ int bicadmm_get_state(bicadmm_t h, int32_t field, double* out_host, int64_t len)
 int bicadmm_set_profiling(bicadmm_t h, int32_t on);
 int bicadmm_get_pass_time(bicadmm_t h, double* ms_out, int64_t* launches_out);
 
+/* Allocation-free consensus update.  The paper has no counterpart: this entry point exists
+ * for callers that cannot call cudaMalloc when they call in, such as code running while a
+ * stream is captured into a CUDA graph, services whose device memory belongs to another
+ * allocator or pool, and latency-bound loops that must avoid the implicit synchronisation
+ * of cudaMalloc/cudaFree.  It runs the same (z, t) root solve, top-kappa s update and v
+ * update as one outer iteration of bicadmm_step, on caller buffers, and allocates nothing:
+ * its scratch (about 512 KB: breakpoints and sort keys for up to 32768 entries, scalars and
+ * a status word) is a file-scope device array in the library, held by every GPU that loads
+ * the library until the process exits.
+ *   w    device, n doubles, in:  (1/N) sum_i (x_i + u_i)
+ *   z    device, n doubles, in: z^k (for the dual residual), out: z^{k+1}
+ *   s    device, n doubles, in: s^k, out: s^{k+1}
+ *   tvt  device, 4 doubles, in: tvt[1] = v^k; out: t^{k+1}, v^{k+1}, tau, device status
+ *        (0 = ok, nonzero = the root iteration hit its bound)
+ *   n <= 32768, 1 <= kappa <= n, N_shards >= 1, rho_c > 0, rho_b > 0; larger n is rejected
+ *   with BICADMM_ERR_ARG.  stream: cudaStream_t (NULL = legacy default stream).
+ * Work is enqueued on stream; the call does not synchronise.  The first call on a device
+ * looks up the scratch array's device address (cudaGetSymbolAddress) for that device; make
+ * that first call before any stream capture.  Every call on a device shares the one scratch
+ * array and overwrites it, so calls that may overlap on the GPU (other streams, other host
+ * threads) race: order them on one stream.  Returns BICADMM_ERR_ARG / BICADMM_ERR_CUDA on
+ * failure (no handle, so no last-error text). */
+int bicadmm_consensus_step_noalloc(const double* w, double* z, double* s, double* tvt, int64_t n,
+                                   int64_t kappa, int32_t N_shards, double rho_c, double rho_b,
+                                   void* stream);
+
 /* Free every device buffer of the handle (synchronises its stream).  NULL is accepted. */
 int bicadmm_destroy(bicadmm_t h);
 

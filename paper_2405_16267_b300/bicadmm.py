@@ -73,6 +73,9 @@ SIGNATURES = [
     ("bicadmm_set_profiling", ctypes.c_int, [_VP, ctypes.c_int32]),
     ("bicadmm_get_pass_time", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(ctypes.c_int64)]),
+    ("bicadmm_consensus_step_noalloc", ctypes.c_int,
+     [_VP, _VP, _VP, _VP, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
+      ctypes.c_double, _VP]),
     ("bicadmm_destroy", ctypes.c_int, [_VP]),
     ("bicadmm_last_error", ctypes.c_char_p, [_VP]),
 ]
@@ -191,6 +194,17 @@ def get_pass_time(h):
     cnt = ctypes.c_int64()
     _check(lib().bicadmm_get_pass_time(h, ctypes.byref(ms), ctypes.byref(cnt)), h)
     return ms.value, cnt.value
+
+
+def consensus_step_noalloc(w, z, s, tvt, kappa, N_shards, rho_c, rho_b, stream=None):
+    """Allocation-free consensus update on caller device tensors (float64, contiguous):
+    w, z, s of length n and tvt of length 4 (see include/bicadmm.h)."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    n = w.numel()
+    _check(lib().bicadmm_consensus_step_noalloc(w.data_ptr(), z.data_ptr(), s.data_ptr(),
+                                                tvt.data_ptr(), n, int(kappa), int(N_shards),
+                                                float(rho_c), float(rho_b), _VP(stream or 0)))
 
 
 def destroy(h):

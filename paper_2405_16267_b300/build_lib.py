@@ -47,7 +47,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         return LIB
     os.makedirs(LIBDIR, exist_ok=True)
     cmd = [nvcc(), *ARCH, *FLAGS, "-I", INCLUDE, "-I", CSRC, *extra,
-           os.path.join(CSRC, "bicadmm.cu"), "-o", LIB + ".tmp"]
+           *sorted(glob.glob(os.path.join(CSRC, "*.cu"))), "-o", LIB + ".tmp"]
     if verbose:
         print(" ".join(cmd), flush=True)
     res = subprocess.run(cmd, capture_output=True, text=True)

@@ -1,0 +1,90 @@
+// Allocation-free entry point: the consensus update (z, t, s, v) of one outer iteration,
+// with its scratch memory in file-scope device arrays instead of buffers from cudaMalloc.
+//
+// Some callers cannot allocate device memory when they call in: code running while a
+// stream is being captured into a CUDA graph (cudaMalloc is not allowed there), services
+// whose device memory is owned by another allocator or pool (a raw cudaMalloc would step
+// outside its accounting), and latency-bound loops that must not risk the implicit
+// synchronisation of a cudaMalloc/cudaFree.  They pass their inputs and outputs and this
+// file supplies the scratch.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "bicadmm.h"
+#include "common.cuh"
+#include "nspace.cuh"
+
+using namespace bic;
+
+namespace {
+
+constexpr int kNoAllocThreads = 1024;
+constexpr int64_t kNoAllocMaxN = 32768;  // largest n this entry point accepts
+constexpr int kMaxDevices = 64;
+
+// The scratch of the consensus update, shared by every call on a device:
+//   breakpoints tau_r (n doubles), top-kappa keys (n uint64), the scalar block, one
+//   residual record and the device status word.  About 512 KB per device, held by every
+//   GPU that loads the library until the process exits.
+struct NoAllocScratch {
+  double tau_r[kNoAllocMaxN];
+  uint64_t key[kNoAllocMaxN];
+  GlobalState gs;
+  Resid rec;
+  int err;
+};
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+// Device address of g_noalloc_scratch, looked up once per device (host code cannot use
+// the symbol itself as a device pointer).
+NoAllocScratch* g_scratch_addr[kMaxDevices] = {};
+
+__global__ void k_noalloc_prologue(NoAllocScratch* sc, const double* tvt) {
+  // Clear everything the consensus kernel reads before writing; take v^k from the caller.
+  sc->gs.t = 0.0;
+  sc->gs.v = tvt[1];
+  sc->gs.tau = 0.0;
+  sc->gs.iter = 0;
+  sc->gs.ticket = 0;
+  sc->err = 0;
+}
+
+__global__ void k_noalloc_epilogue(const NoAllocScratch* sc, double* tvt) {
+  tvt[0] = sc->gs.t;
+  tvt[1] = sc->gs.v;
+  tvt[2] = sc->gs.tau;
+  tvt[3] = static_cast<double>(sc->err);
+}
+
+}  // namespace
+
+extern "C" int bicadmm_consensus_step_noalloc(const double* w, double* z, double* s, double* tvt,
+                                              int64_t n, int64_t kappa, int32_t N_shards,
+                                              double rho_c, double rho_b, void* stream) {
+  if (!w || !z || !s || !tvt) return BICADMM_ERR_ARG;
+  if (n < 1 || n > kNoAllocMaxN) return BICADMM_ERR_ARG;
+  if (kappa < 1 || kappa > n || N_shards < 1) return BICADMM_ERR_ARG;
+  if (!(rho_c > 0.0) || !(rho_b > 0.0)) return BICADMM_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return BICADMM_ERR_CUDA;
+  }
+  if (!g_scratch_addr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return BICADMM_ERR_CUDA;
+    }
+    g_scratch_addr[dev] = static_cast<NoAllocScratch*>(ptr);
+  }
+  NoAllocScratch* sc = g_scratch_addr[dev];
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  k_noalloc_prologue<<<1, 1, 0, st>>>(sc, tvt);
+  k_global<kNoAllocThreads><<<1, kNoAllocThreads, 0, st>>>(w, z, s, sc->tau_r, sc->key, &sc->gs,
+                                                           &sc->rec, 1, n, kappa, N_shards, rho_c,
+                                                           rho_b, &sc->err);
+  k_noalloc_epilogue<<<1, 1, 0, st>>>(sc, tvt);
+  return cudaGetLastError() == cudaSuccess ? BICADMM_OK : BICADMM_ERR_CUDA;
+}

@@ -95,8 +95,8 @@ k_xupd(const TP* __restrict__ P, const int64_t* __restrict__ P_off,
 }
 
 // ------------------------------------------------------------------------------ k_wmean
-__global__ void k_wmean(const double* __restrict__ x, const double* __restrict__ u,
-                        double* __restrict__ w, int N, int64_t n, int64_t lda) {
+static __global__ void k_wmean(const double* __restrict__ x, const double* __restrict__ u,
+                               double* __restrict__ w, int N, int64_t n, int64_t lda) {
   const int64_t col = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (col >= n) return;
   double acc = 0.0;
