@@ -162,9 +162,9 @@ int bicadmm_get_pass_time(bicadmm_t h, double* ms_out, int64_t* launches_out);
  * allocator or pool, and latency-bound loops that must avoid the implicit synchronisation
  * of cudaMalloc/cudaFree.  It runs the same (z, t) root solve, top-kappa s update and v
  * update as one outer iteration of bicadmm_step, on caller buffers, and allocates nothing:
- * its scratch (about 512 KB: breakpoints and sort keys for up to 32768 entries, scalars and
- * a status word) is a file-scope device array in the library, held by every GPU that loads
- * the library until the process exits.
+ * its scratch (about 1 MB: breakpoints, their coefficients and sort keys for up to 32768
+ * entries, scalars and a status word) is a file-scope device array in the library, held by
+ * every GPU that loads the library until the process exits.
  *   w    device, n doubles, in:  (1/N) sum_i (x_i + u_i)
  *   z    device, n doubles, in: z^k (for the dual residual), out: z^{k+1}
  *   s    device, n doubles, in: s^k, out: s^{k+1}

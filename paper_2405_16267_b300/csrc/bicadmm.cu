@@ -5,9 +5,10 @@
 //   A       m x lda   (TA = double | float), lda = n rounded up to 32, zero padding
 //   b, omega, nu      m (TM)
 //   x, u, r  N x lda  FP64;  xlo N x lda (TA copy of x read by the A pass)
-//   z, s, w, tau_r    lda FP64;  key lda uint64 (top-kappa scratch)
+//   z, s, w           lda FP64;  tau_r, c_arr, e_arr lda FP64 and key lda uint64
+//                     (scratch of the consensus CTA)
 //   P       per block (i,j): n_j x ldp_j (TP = TM), ldp_j = n_j rounded up to 32
-//   slots   (G + N) x lda (TM): A'd partial sums, one row per (CTA, shard) pair
+//   slots   (G + N) x lda (TM): A'd partial sums, one row per (panel CTA, shard) pair
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,7 +29,6 @@ using namespace bic;
 namespace {
 
 constexpr int kPassThreads = 256;
-constexpr int kGlobalThreads = 1024;
 constexpr int kDualThreads = 256;
 constexpr int kXupdThreads = 256;
 constexpr int kXupdRows = 32;
@@ -36,6 +36,7 @@ constexpr int kCholThreads = 256;
 constexpr int kTraceCap = 4096;
 constexpr int64_t kMaxN = 32768;                 // single-CTA global step limit
 constexpr size_t kPassSmemBudget = 200 * 1024;   // dynamic smem for A-pass stages
+constexpr size_t kPassCtaTarget = 100 * 1024;    // auto sizing aims at two CTAs per SM
 
 int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
@@ -68,7 +69,8 @@ struct bicadmm_ctx {
   void *A = nullptr, *b = nullptr, *omega = nullptr, *nu = nullptr, *slots = nullptr,
        *xlo = nullptr, *Pm = nullptr;
   double *x = nullptr, *u = nullptr, *r = nullptr, *z = nullptr, *s = nullptr, *w = nullptr,
-         *tau_r = nullptr, *cta_stats = nullptr, *dual_part = nullptr;
+         *tau_r = nullptr, *c_arr = nullptr, *e_arr = nullptr, *cta_stats = nullptr,
+         *dual_part = nullptr;
   uint64_t* key = nullptr;
   int64_t *d_shard_row0 = nullptr, *d_panel_start = nullptr, *d_P_off = nullptr,
           *d_G_off = nullptr;
@@ -123,47 +125,83 @@ void free_all(bicadmm_ctx* h) {
 }
 
 // ---------------------------------------------------------------- A-pass dispatch
+ConsensusArgs consensus_args(bicadmm_ctx* h, bool enabled) {
+  ConsensusArgs a{};
+  a.x = h->x;
+  a.u = h->u;
+  a.w = h->w;
+  a.z = h->z;
+  a.s = h->s;
+  a.tau_r = h->tau_r;
+  a.c_arr = h->c_arr;
+  a.e_arr = h->e_arr;
+  a.key = h->key;
+  a.gs = h->gs;
+  a.trace = h->trace;
+  a.trace_cap = kTraceCap;
+  a.N = h->N;
+  a.n = h->p.n;
+  a.kappa = h->p.kappa;
+  a.lda = h->lda;
+  a.rho_c = h->p.rho_c;
+  a.rho_b = h->p.rho_b;
+  a.err = h->d_err;
+  a.enabled = enabled ? 1 : 0;
+  return a;
+}
+
+// Allow the largest dynamic shared memory the kernel can take next to its static part.
+template <typename K>
+cudaError_t allow_max_dynamic_smem(K kern) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              227 * 1024 - static_cast<int>(fa.sharedSizeBytes));
+}
+
 template <typename TA, typename TM, int R, int VPT>
-int launch_pass_rv(bicadmm_ctx* h) {
+int launch_pass_rv(bicadmm_ctx* h, bool with_consensus) {
   auto kern = k_fused_pass<TA, TM, R, VPT, kPassThreads>;
   static bool attr_set = false;  // per instantiation
   if (!attr_set) {
-    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    CK(allow_max_dynamic_smem(kern));
     attr_set = true;
   }
   PassGeometry geo{h->d_shard_row0, h->d_panel_start, h->N, h->P_panels};
-  kern<<<h->G, kPassThreads, h->pass_smem, h->stream>>>(
+  kern<<<h->G + (with_consensus ? 1 : 0), kPassThreads, h->pass_smem, h->stream>>>(
       static_cast<const TA*>(h->A), h->lda, static_cast<const TA*>(h->xlo),
       static_cast<const TM*>(h->b), static_cast<TM*>(h->omega), static_cast<TM*>(h->nu),
       static_cast<TM*>(h->slots), h->cta_stats, geo, h->S, h->p.loss, static_cast<TM>(h->M),
-      static_cast<TM>(h->p.rho_l), h->p.newton_iters, h->d_err, kWaitLimitCycles);
+      static_cast<TM>(h->p.rho_l), h->p.newton_iters, h->d_err, kWaitLimitCycles,
+      consensus_args(h, with_consensus));
   CK(cudaGetLastError());
   return BICADMM_OK;
 }
 
 template <typename TA, typename TM, int R>
-int launch_pass_r(bicadmm_ctx* h) {
+int launch_pass_r(bicadmm_ctx* h, bool wc) {
   switch (h->VPT) {
-    case 1: return launch_pass_rv<TA, TM, R, 1>(h);
-    case 2: return launch_pass_rv<TA, TM, R, 2>(h);
-    case 3: return launch_pass_rv<TA, TM, R, 3>(h);
-    case 4: return launch_pass_rv<TA, TM, R, 4>(h);
-    case 5: return launch_pass_rv<TA, TM, R, 5>(h);
-    case 6: return launch_pass_rv<TA, TM, R, 6>(h);
-    case 8: return launch_pass_rv<TA, TM, R, 8>(h);
-    case 12: return launch_pass_rv<TA, TM, R, 12>(h);
-    case 16: return launch_pass_rv<TA, TM, R, 16>(h);
+    case 1: return launch_pass_rv<TA, TM, R, 1>(h, wc);
+    case 2: return launch_pass_rv<TA, TM, R, 2>(h, wc);
+    case 3: return launch_pass_rv<TA, TM, R, 3>(h, wc);
+    case 4: return launch_pass_rv<TA, TM, R, 4>(h, wc);
+    case 5: return launch_pass_rv<TA, TM, R, 5>(h, wc);
+    case 6: return launch_pass_rv<TA, TM, R, 6>(h, wc);
+    case 8: return launch_pass_rv<TA, TM, R, 8>(h, wc);
+    case 12: return launch_pass_rv<TA, TM, R, 12>(h, wc);
+    case 16: return launch_pass_rv<TA, TM, R, 16>(h, wc);
   }
   return fail(h, BICADMM_ERR_UNSUPPORTED, "no A-pass variant for this width");
 }
 
 template <typename TA, typename TM>
-int launch_pass(bicadmm_ctx* h) {
+int launch_pass(bicadmm_ctx* h, bool with_consensus) {
   switch (h->R) {
-    case 1: return launch_pass_r<TA, TM, 1>(h);
-    case 2: return launch_pass_r<TA, TM, 2>(h);
-    case 4: return launch_pass_r<TA, TM, 4>(h);
-    case 8: return launch_pass_r<TA, TM, 8>(h);
+    case 1: return launch_pass_r<TA, TM, 1>(h, with_consensus);
+    case 2: return launch_pass_r<TA, TM, 2>(h, with_consensus);
+    case 4: return launch_pass_r<TA, TM, 4>(h, with_consensus);
+    case 8: return launch_pass_r<TA, TM, 8>(h, with_consensus);
   }
   return fail(h, BICADMM_ERR_UNSUPPORTED, "no A-pass variant for this panel height");
 }
@@ -171,7 +209,7 @@ int launch_pass(bicadmm_ctx* h) {
 template <typename TA, typename TM, int R, int VPT>
 int occupancy_rv(bicadmm_ctx* h, int* blocks) {
   auto kern = k_fused_pass<TA, TM, R, VPT, kPassThreads>;
-  CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  CK(allow_max_dynamic_smem(kern));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, kPassThreads, h->pass_smem));
   return BICADMM_OK;
 }
@@ -204,7 +242,6 @@ int run_iterations(bicadmm_ctx* h, int n_iters) {
   const dim3 rhs_grid(static_cast<unsigned>((lda + 255) / 256), N);
   const dim3 xupd_grid(static_cast<unsigned>((h->max_nj + kXupdRows - 1) / kXupdRows), M, N);
   const size_t xupd_smem = static_cast<size_t>(h->max_ldp) * sizeof(TM);
-  const unsigned wm_grid = static_cast<unsigned>((n + 255) / 256);
   const dim3 dual_grid(h->dual_chunks, N);
   for (int it = 0; it < n_iters; ++it) {
     for (int jj = 0; jj < h->p.inner_iters; ++jj) {
@@ -224,8 +261,10 @@ int run_iterations(bicadmm_ctx* h, int n_iters) {
         }
         CK(cudaEventRecord(h->ev[h->ev_used], h->stream));
       }
-      int rc = (h->p.precision == BICADMM_PREC_FP64) ? launch_pass<double, double>(h)
-                                                      : launch_pass<float, float>(h);
+      // The last sweep's pass also runs the global step in its spare CTA.
+      const bool last = jj == h->p.inner_iters - 1;
+      int rc = (h->p.precision == BICADMM_PREC_FP64) ? launch_pass<double, double>(h, last)
+                                                      : launch_pass<float, float>(h, last);
       if (rc != BICADMM_OK) return rc;
       if (h->prof) {
         CK(cudaEventRecord(h->ev[h->ev_used + 1], h->stream));
@@ -233,15 +272,11 @@ int run_iterations(bicadmm_ctx* h, int n_iters) {
       }
       h->launches += 3;
     }
-    k_wmean<<<wm_grid, 256, 0, h->stream>>>(h->x, h->u, h->w, N, n, lda);
-    k_global<kGlobalThreads><<<1, kGlobalThreads, 0, h->stream>>>(
-        h->w, h->z, h->s, h->tau_r, h->key, h->gs, h->trace, kTraceCap, n, h->p.kappa, N,
-        h->p.rho_c, h->p.rho_b, h->d_err);
     k_dual<kDualThreads><<<dual_grid, kDualThreads, 0, h->stream>>>(
         h->u, h->x, h->z, h->dual_part, h->cta_stats, h->G, h->gs, h->trace, kTraceCap, N, n,
         lda, h->p.rho_c, h->d_err);
     CK(cudaGetLastError());
-    h->launches += 3;
+    h->launches += 1;
     h->iters_done += 1;
   }
   return BICADMM_OK;
@@ -342,15 +377,18 @@ int build_geometry(bicadmm_ctx* h) {
   // A-pass panel geometry
   const size_t row_bytes = static_cast<size_t>(h->lda) * h->esz;
   int R = p.pass_rows;
+  // Auto: the tallest panel (<= 48 KB) of which two stages fit a two-CTA-per-SM budget, and
+  // up to four stages in that budget (one stage if a single row exceeds it).
   if (R == 0) {
     R = 1;
     for (int cand : {8, 4, 2}) {
-      if (cand * row_bytes <= 48 * 1024 && 2 * cand * row_bytes <= kPassSmemBudget) { R = cand; break; }
+      if (cand * row_bytes <= 48 * 1024 && 2 * cand * row_bytes <= kPassCtaTarget) { R = cand; break; }
     }
   }
   int S = p.pass_stages;
   if (S == 0) {
-    S = static_cast<int>(std::min<size_t>(4, kPassSmemBudget / (R * row_bytes)));
+    const size_t budget = 2 * R * row_bytes <= kPassCtaTarget ? kPassCtaTarget : kPassSmemBudget;
+    S = static_cast<int>(std::min<size_t>(4, budget / (R * row_bytes)));
     if (S < 1) S = 1;
   }
   if (static_cast<size_t>(S) * R * row_bytes > kPassSmemBudget)
@@ -372,7 +410,10 @@ int build_geometry(bicadmm_ctx* h) {
   int rc = h->esz == 8 ? pass_occupancy<double, double>(h, &occ) : pass_occupancy<float, float>(h, &occ);
   if (rc != BICADMM_OK) return rc;
   if (occ < 1) return fail(h, BICADMM_ERR_UNSUPPORTED, "A-pass variant cannot be resident on an SM");
-  h->G = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(occ) * h->num_sms, h->P_panels));
+  // One resident slot is kept for the consensus CTA that rides on the last pass.
+  const int64_t slots_total = static_cast<int64_t>(occ) * h->num_sms - 1;
+  if (slots_total < 1) return fail(h, BICADMM_ERR_UNSUPPORTED, "A-pass needs at least two resident CTAs");
+  h->G = static_cast<int>(std::min<int64_t>(slots_total, h->P_panels));
   // slots: CTA c writes slot (c + shard) for every shard it touches
   h->slot_lo.assign(h->N, 0);
   h->slot_hi.assign(h->N, 0);
@@ -411,6 +452,8 @@ int allocate(bicadmm_ctx* h) {
   AL(h->s, lda * sizeof(double));
   AL(h->w, lda * sizeof(double));
   AL(h->tau_r, lda * sizeof(double));
+  AL(h->c_arr, lda * sizeof(double));
+  AL(h->e_arr, lda * sizeof(double));
   AL(h->key, lda * sizeof(uint64_t));
   AL(h->cta_stats, static_cast<size_t>(h->G) * 4 * sizeof(double));
   AL(h->dual_part, static_cast<size_t>(N) * h->dual_chunks * 2 * sizeof(double));

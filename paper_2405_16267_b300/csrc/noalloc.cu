@@ -24,11 +24,14 @@ constexpr int64_t kNoAllocMaxN = 32768;  // largest n this entry point accepts
 constexpr int kMaxDevices = 64;
 
 // The scratch of the consensus update, shared by every call on a device:
-//   breakpoints tau_r (n doubles), top-kappa keys (n uint64), the scalar block, one
-//   residual record and the device status word.  About 512 KB per device, held by every
-//   GPU that loads the library until the process exits.
+//   breakpoints tau_r, their intercepts and slopes c_r, e_r (n doubles each), top-kappa
+//   keys (n uint64), the scalar block, one residual record and the device status word.
+//   About 1 MB per device, held by every GPU that loads the library until the process
+//   exits.
 struct NoAllocScratch {
   double tau_r[kNoAllocMaxN];
+  double c_arr[kNoAllocMaxN];
+  double e_arr[kNoAllocMaxN];
   uint64_t key[kNoAllocMaxN];
   GlobalState gs;
   Resid rec;
@@ -82,9 +85,28 @@ extern "C" int bicadmm_consensus_step_noalloc(const double* w, double* z, double
   NoAllocScratch* sc = g_scratch_addr[dev];
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   k_noalloc_prologue<<<1, 1, 0, st>>>(sc, tvt);
-  k_global<kNoAllocThreads><<<1, kNoAllocThreads, 0, st>>>(w, z, s, sc->tau_r, sc->key, &sc->gs,
-                                                           &sc->rec, 1, n, kappa, N_shards, rho_c,
-                                                           rho_b, &sc->err);
+  ConsensusArgs a{};
+  a.x = nullptr;
+  a.u = nullptr;
+  a.w = const_cast<double*>(w);  // read only when x is null
+  a.z = z;
+  a.s = s;
+  a.tau_r = sc->tau_r;
+  a.c_arr = sc->c_arr;
+  a.e_arr = sc->e_arr;
+  a.key = sc->key;
+  a.gs = &sc->gs;
+  a.trace = &sc->rec;
+  a.trace_cap = 1;
+  a.N = N_shards;
+  a.n = n;
+  a.kappa = kappa;
+  a.lda = n;
+  a.rho_c = rho_c;
+  a.rho_b = rho_b;
+  a.err = &sc->err;
+  a.enabled = 1;
+  k_global<kNoAllocThreads, 1><<<1, kNoAllocThreads, 0, st>>>(a);
   k_noalloc_epilogue<<<1, 1, 0, st>>>(sc, tvt);
   return cudaGetLastError() == cudaSuccess ? BICADMM_OK : BICADMM_ERR_CUDA;
 }

@@ -3,9 +3,9 @@
 //   k_rhs       r_i = rho_l q_i + rho_c (z - u_i) - c0 x_i, q_i = sum of the pass slots of
 //               shard i (fixed order)                              eq. (p:GPU;x) right side
 //   k_xupd      x_ij += P_ij r_ij   (block-diagonal explicit inverse, one warp per row)
-//   k_wmean     w = (1/N) sum_i (x_i + u_i)                        eq. (global-z-t-updae)
-//   k_global    (z, t) root solve, top-kappa s, v, d_r, b_r        eqs. (global-z-t-updae),
-//               (single CTA)                                       (s-update-final), (v-update)
+//   consensus   w = (1/N) sum_i (x_i + u_i), (z, t) root solve,    eqs. (global-z-t-updae),
+//               top-kappa s, v, d_r, b_r (one CTA; run by the      (s-update-final), (v-update)
+//               fused pass's spare CTA or by k_global)
 //   k_dual      u_i += x_i - z, p_r, inner residual                eq. (u-update), Termination
 #pragma once
 
@@ -94,26 +94,19 @@ k_xupd(const TP* __restrict__ P, const int64_t* __restrict__ P_off,
   }
 }
 
-// ------------------------------------------------------------------------------ k_wmean
-static __global__ void k_wmean(const double* __restrict__ x, const double* __restrict__ u,
-                               double* __restrict__ w, int N, int64_t n, int64_t lda) {
-  const int64_t col = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (col >= n) return;
-  double acc = 0.0;
-  for (int i = 0; i < N; ++i) acc += x[i * lda + col] + u[i * lda + col];
-  w[col] = acc / N;
-}
-
 // ------------------------------------------------------------------------------ top-kappa
 // Select the kappa largest |z_r| (ties: lowest index) inside one CTA of GT threads by an
 // MSB-first radix select on the IEEE bit patterns of |z_r| (non-negative doubles order as
 // unsigned integers), then rank the entries equal to the threshold by index with a
-// block-wide scan.  Each thread owns a contiguous chunk of at most 32 indices and returns
+// block-wide scan.  Each thread owns a contiguous chunk of at most 32*MW indices and gets
 // its selection as a bit mask.  key[] is global scratch of n entries.
-template <int GT>
-__device__ uint32_t block_topk_select(const double* __restrict__ z, uint64_t* __restrict__ key,
-                                      int64_t n, int64_t kappa, unsigned int* hist,
-                                      long long* sh, int64_t& chunk_begin, int& chunk_len) {
+template <int GT, int MW>
+__device__ void block_topk_select(const double* __restrict__ z, uint64_t* __restrict__ key,
+                                  int64_t n, int64_t kappa, uint32_t (&sel)[MW],
+                                  int64_t& chunk_begin, int& chunk_len) {
+  __shared__ unsigned int hist[256];
+  __shared__ long long sh[2];
+  __shared__ unsigned int wsum[32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int64_t r = tid; r < n; r += GT) key[r] = __double_as_longlong(fabs(z[r]));
   __syncthreads();
@@ -128,7 +121,7 @@ __device__ uint32_t block_topk_select(const double* __restrict__ z, uint64_t* __
     }
     __syncthreads();
     if (warp == 0) {
-      // lane l owns bins 255-8l .. 248-8l (descending); suffix counts from the top.
+      // lane l owns bins 255-8l .. 248-8l (descending); counts accumulate from the top.
       unsigned int cnt[8], tot = 0;
 #pragma unroll
       for (int q = 0; q < 8; ++q) { cnt[q] = hist[255 - 8 * lane - q]; tot += cnt[q]; }
@@ -163,22 +156,20 @@ __device__ uint32_t block_topk_select(const double* __restrict__ z, uint64_t* __
   // prefix = threshold key; take every key above it and the first `remaining` equal ones.
   const int64_t ch = (n + GT - 1) / GT;
   chunk_begin = tid * ch;
-  int64_t cend = chunk_begin + ch < n ? chunk_begin + ch : n;
+  const int64_t cend = chunk_begin + ch < n ? chunk_begin + ch : n;
   chunk_len = chunk_begin < cend ? static_cast<int>(cend - chunk_begin) : 0;
   unsigned int eq = 0;
   for (int q = 0; q < chunk_len; ++q) eq += key[chunk_begin + q] == prefix;
-  // exclusive scan of eq over threads
   unsigned int incl = eq;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
     const unsigned int y = __shfl_up_sync(0xffffffffu, incl, off);
     if (lane >= off) incl += y;
   }
-  __shared__ unsigned int wsum[32];
   if (lane == 31) wsum[warp] = incl;
   __syncthreads();
   if (warp == 0) {
-    unsigned int v = lane < GT / 32 ? wsum[lane] : 0u;
+    const unsigned int v = lane < GT / 32 ? wsum[lane] : 0u;
     unsigned int inc = v;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -189,65 +180,107 @@ __device__ uint32_t block_topk_select(const double* __restrict__ z, uint64_t* __
   }
   __syncthreads();
   unsigned int rank = wsum[warp] + incl - eq;
-  uint32_t sel = 0;
+#pragma unroll
+  for (int q = 0; q < MW; ++q) sel[q] = 0u;
   for (int q = 0; q < chunk_len; ++q) {
     const uint64_t k = key[chunk_begin + q];
     bool take = k > prefix;
     if (k == prefix) { take = static_cast<int64_t>(rank) < remaining; ++rank; }
-    if (take) sel |= 1u << q;
+    if (take) sel[q >> 5] |= 1u << (q & 31);
   }
   __syncthreads();
-  return sel;
 }
 
-// ------------------------------------------------------------------------------ k_global
-// One CTA.  Reads w (k_wmean), the previous s, t, v; writes z, s, t, v, tau and the
-// d_r / b_r part of the residual record.  tau_r[] and key[] are global scratch (n each).
-template <int GT>
-__global__ void __launch_bounds__(GT, 1)
-k_global(const double* __restrict__ w, double* __restrict__ z, double* __restrict__ s,
-         double* __restrict__ tau_r, uint64_t* __restrict__ key, GlobalState* gs, Resid* trace,
-         int trace_cap, int64_t n, int64_t kappa, int N, double rho_c, double rho_b,
-         int* err) {
+// ------------------------------------------------------------------------------ consensus
+// The global step of one outer iteration, executed by one CTA:
+//   w = (1/N) sum_i (x_i + u_i)              (or taken from the caller)
+//   (z, t) of eq. (global-z-t-updae), s of eq. (s-update-final), v of eq. (v-update)
+//   and the d_r / b_r part of the residual record.
+// The (z,t) root: h(tau) = v + beta tau + sum_{r: tau_r > tau} (c_r + e_r tau) is concave,
+// increasing and piecewise linear (c_r = s_r w_r - |w_r|, e_r = (s_r - sign w_r)^2,
+// tau_r = |w_r| / (1 - sign(w_r) s_r) the point where z_r reaches 0).  Newton from the left
+// never overshoots the root and the active set only shrinks, so the iteration ends, exactly,
+// when the active set stops changing.  It starts from the previous iteration's tau when
+// h is still non-positive there, else from 0.
+struct ConsensusArgs {
+  const double* x;   // N x lda, or nullptr when w is given
+  const double* u;   // N x lda
+  double* w;         // n: written when x is given, read otherwise
+  double* z;         // n: in z^k (dual residual), out z^{k+1}
+  double* s;         // n: in s^k, out s^{k+1}
+  double* tau_r;     // n scratch
+  double* c_arr;     // n scratch
+  double* e_arr;     // n scratch
+  uint64_t* key;     // n scratch
+  GlobalState* gs;
+  Resid* trace;
+  int trace_cap;
+  int N;
+  int64_t n, kappa, lda;
+  double rho_c, rho_b;
+  int* err;
+  int enabled;       // used by the fused pass: 1 = its last CTA runs this step
+};
+
+template <int GT, int MW>
+__device__ void consensus_block(const ConsensusArgs& a) {
   __shared__ double red[32 * 4];
-  __shared__ unsigned int hist[256];
-  __shared__ long long sh[2];
   const int tid = threadIdx.x;
-  const double v = gs->v;
-  const double beta = N * rho_c / rho_b;
+  const int64_t n = a.n;
+  const double v = a.gs->v, tau_prev = a.gs->tau;
+  const double beta = a.N * a.rho_c / a.rho_b;
 
-  // h(0) and the breakpoints tau_r = |w_r| / (1 - sign(w_r) s_r) (inf: never zeroed).
-  double a1[1] = {0.0};
   for (int64_t r = tid; r < n; r += GT) {
-    const double wr = w[r], sr = s[r], sg = dsign(wr);
-    a1[0] += sr * wr - fabs(wr);
+    double wr;
+    if (a.x) {
+      double acc = 0.0;
+      for (int i = 0; i < a.N; ++i) acc += a.x[i * a.lda + r] + a.u[i * a.lda + r];
+      wr = acc / a.N;
+      a.w[r] = wr;
+    } else {
+      wr = a.w[r];
+    }
+    const double sr = a.s[r], sg = dsign(wr);
+    a.c_arr[r] = sr * wr - fabs(wr);
+    a.e_arr[r] = (sr - sg) * (sr - sg);
     // w_r = 0: z_r stays 0 for every tau >= 0 (never active).  sign(w_r) s_r = 1: never
-    // zeroed, but contributes c_r = e_r = 0.
-    tau_r[r] = wr == 0.0 ? 0.0 : (sg * sr < 1.0 ? fabs(wr) / (1.0 - sg * sr) : HUGE_VAL);
+    // zeroed, and contributes c_r = e_r = 0.
+    a.tau_r[r] = wr == 0.0 ? 0.0 : (sg * sr < 1.0 ? fabs(wr) / (1.0 - sg * sr) : HUGE_VAL);
   }
-  block_sum<1>(a1, red);
-  const double h0 = v + a1[0];
+  __syncthreads();
 
-  double tau = 0.0;
-  int64_t steps = 0;
-  if (h0 < 0.0) {
-    // h is concave, increasing and piecewise linear.  Newton from the left: the root of the
-    // linear piece through tau_k never overshoots the root of h, and the active set
-    // {r : tau_r > tau} only shrinks, so the iteration ends (exactly) when it stops changing.
-    auto active_sums = [&](double at, double (&o)[3]) {
-      o[0] = o[1] = o[2] = 0.0;
-      for (int64_t r = tid; r < n; r += GT) {
-        if (tau_r[r] > at) {
-          const double wr = w[r], sr = s[r], sg = dsign(wr);
-          o[0] += sr * wr - fabs(wr);
-          o[1] += (sr - sg) * (sr - sg);
-          o[2] += 1.0;
-        }
+  // sums of c_r, e_r and the count over the active set {r : tau_r > at}; breakpoints are
+  // non-negative, so they compare as their bit patterns.
+  auto active_sums = [&](double at, double (&o)[3]) {
+    o[0] = o[1] = o[2] = 0.0;
+    const long long atb = __double_as_longlong(at);
+    for (int64_t r = tid; r < n; r += GT) {
+      if (__double_as_longlong(a.tau_r[r]) > atb) {
+        o[0] += a.c_arr[r];
+        o[1] += a.e_arr[r];
+        o[2] += 1.0;
       }
-      block_sum<3>(o, red);
-    };
-    double cur[3];
+    }
+    block_sum<3>(o, red);
+  };
+
+  double cur[3];
+  double tau = 0.0, tstart = 0.0;
+  bool active = true;
+  bool warm = false;
+  if (tau_prev > 0.0) {
+    active_sums(tau_prev, cur);
+    warm = v + cur[0] + (beta + cur[1]) * tau_prev <= 0.0;  // h(tau_prev) <= 0
+  }
+  if (warm) {
+    tstart = tau_prev;
+  } else {
     active_sums(0.0, cur);
+    active = v + cur[0] < 0.0;  // h(0) < 0: the l1 constraint binds
+  }
+  int64_t steps = 0;
+  if (active) {
+    tau = tstart;
     const int64_t max_steps = n + 2;
     for (;;) {
       const double tn = -(v + cur[0]) / (beta + cur[1]);
@@ -258,30 +291,30 @@ k_global(const double* __restrict__ w, double* __restrict__ z, double* __restric
       if (nxt[2] >= cur[2]) break;
       cur[0] = nxt[0]; cur[1] = nxt[1]; cur[2] = nxt[2];
       if (steps > max_steps) {
-        if (tid == 0) set_err(err, DEV_ZT_NOCONV);
+        if (tid == 0) set_err(a.err, DEV_ZT_NOCONV);
         break;
       }
     }
   }
 
-  // z = S_tau(w + tau s) (z = w when tau = 0); norms for t and the dual residual.
+  // z = S_tau(w + tau s) (z = w when the constraint is inactive); norms for t and d_r.
   double a4[4] = {0.0, 0.0, 0.0, 0.0};  // ||z||_1, s'w, ||z - z_prev||^2, ||z||^2
   for (int64_t r = tid; r < n; r += GT) {
-    const double wr = w[r], sr = s[r];
+    const double wr = a.w[r], sr = a.s[r];
     double zn;
     if (tau > 0.0) {
       const double y = wr + tau * sr;
-      const double m = fabs(y) - tau;
-      zn = m > 0.0 ? dsign(y) * m : 0.0;
+      const double mg = fabs(y) - tau;
+      zn = mg > 0.0 ? dsign(y) * mg : 0.0;
     } else {
       zn = wr;
     }
-    const double zo = z[r];
+    const double zo = a.z[r];
     a4[0] += fabs(zn);
     a4[1] += sr * wr;
     a4[2] += (zn - zo) * (zn - zo);
     a4[3] += zn * zn;
-    z[r] = zn;
+    a.z[r] = zn;
   }
   block_sum<4>(a4, red);
   const double t = tau > 0.0 ? a4[0] : a4[1] + v;
@@ -289,10 +322,11 @@ k_global(const double* __restrict__ w, double* __restrict__ z, double* __restric
   // s: top-kappa signs of z scaled by clamp((t - v)/T, -1, 1).
   int64_t cb;
   int cl;
-  const uint32_t sel = block_topk_select<GT>(z, key, n, kappa, hist, sh, cb, cl);
+  uint32_t sel[MW];
+  block_topk_select<GT, MW>(a.z, a.key, n, a.kappa, sel, cb, cl);
   double a1b[1] = {0.0};
   for (int q = 0; q < cl; ++q)
-    if (sel >> q & 1u) a1b[0] += fabs(z[cb + q]);
+    if (sel[q >> 5] >> (q & 31) & 1u) a1b[0] += fabs(a.z[cb + q]);
   block_sum<1>(a1b, red);
   const double T = a1b[0];
   double scale = 0.0;
@@ -302,18 +336,18 @@ k_global(const double* __restrict__ w, double* __restrict__ z, double* __restric
   }
   double a1c[1] = {0.0};
   for (int q = 0; q < cl; ++q) {
-    const double zr = z[cb + q];
-    const double sn = (sel >> q & 1u) ? scale * dsign(zr) : 0.0;
-    s[cb + q] = sn;
+    const double zr = a.z[cb + q];
+    const double sn = (sel[q >> 5] >> (q & 31) & 1u) ? scale * dsign(zr) : 0.0;
+    a.s[cb + q] = sn;
     a1c[0] += zr * sn;
   }
   block_sum<1>(a1c, red);
   const double g = a1c[0] - t;
   if (tid == 0) {
     const double vn = v + g;
-    Resid& rec = trace[gs->iter % trace_cap];
+    Resid& rec = a.trace[a.gs->iter % a.trace_cap];
     const double dz = sqrt(a4[2]), zn = sqrt(a4[3]);
-    rec.d_r = sqrt(static_cast<double>(N)) * rho_c * dz;
+    rec.d_r = sqrt(static_cast<double>(a.N)) * a.rho_c * dz;
     rec.b_r = fabs(g);
     rec.d_rel = dz / fmax(zn, 1e-30);
     rec.b_rel = fabs(g) / fmax(t, 1e-30);
@@ -321,12 +355,18 @@ k_global(const double* __restrict__ w, double* __restrict__ z, double* __restric
     rec.v = vn;
     rec.tau = tau;
     rec.znorm = zn;
-    rec.iter = gs->iter + 1;
+    rec.iter = a.gs->iter + 1;
     rec.zt_steps = steps;
-    gs->t = t;
-    gs->v = vn;
-    gs->tau = tau;
+    a.gs->t = t;
+    a.gs->v = vn;
+    a.gs->tau = tau;
   }
+}
+
+// Standalone single-CTA consensus step (n <= 32 * MW * GT).
+template <int GT, int MW>
+__global__ void __launch_bounds__(GT, 1) k_global(ConsensusArgs a) {
+  consensus_block<GT, MW>(a);
 }
 
 // ------------------------------------------------------------------------------ k_dual

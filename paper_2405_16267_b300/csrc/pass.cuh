@@ -20,6 +20,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "nspace.cuh"
 
 namespace bic {
 
@@ -54,6 +55,10 @@ __device__ __forceinline__ T omega_prox(int loss, T a, T b, T M, T rho_l, int ne
   const T step0 = b / rho_l;
   T lo = a < a + step0 ? a : a + step0;
   T hi = a < a + step0 ? a + step0 : a;
+  // Stop once a step is below a few ulps of the bracket's scale |a| + 1/rho_l (a test
+  // relative to |w| alone never fires when the root is near 0).
+  const T scale = (a < T(0) ? -a : a) + (step0 < T(0) ? -step0 : step0);
+  const T stop = T(4) * FpLim<T>::eps * scale;
   T w = a;
   for (int it = 0; it < newton_iters; ++it) {
     const T sg = T(1) / (T(1) + dev_exp<T>(b * M * w));   // sigma(-b M w)
@@ -64,10 +69,7 @@ __device__ __forceinline__ T omega_prox(int loss, T a, T b, T M, T rho_l, int ne
     if (!(wn > lo && wn < hi)) wn = T(0.5) * (lo + hi);
     const T dw = wn - w;
     w = wn;
-    const T aw = w < T(0) ? -w : w;
-    const T adw = dw < T(0) ? -dw : dw;
-    if (adw <= T(4) * FpLim<T>::eps * aw || hi - lo <= FpLim<T>::tiny)
-      break;
+    if ((dw < T(0) ? -dw : dw) <= stop || hi - lo <= stop) break;
   }
   return w;
 }
@@ -89,13 +91,22 @@ __device__ __forceinline__ void locate_panel(const PassGeometry& g, int64_t p, i
   nrows = rem < R ? static_cast<int>(rem) : R;
 }
 
+// Consensus-step mask words for NT threads: n <= 32 * kConsMW * NT.
+constexpr int kConsMW = 4;
+
 template <typename TA, typename TM, int R, int VPT, int NT>
 __global__ void __launch_bounds__(NT, 1)
 k_fused_pass(const TA* __restrict__ A, int64_t lda, const TA* __restrict__ xlo,
              const TM* __restrict__ b, TM* __restrict__ omega, TM* __restrict__ nu,
              TM* __restrict__ slots, double* __restrict__ cta_stats, PassGeometry geo,
              int S, int loss, TM Mf, TM rho_l, int newton_iters, int* __restrict__ err,
-             long long wait_limit) {
+             long long wait_limit, ConsensusArgs cons) {
+  // With cons.enabled the last CTA runs the global (z, t, s, v) step of this outer
+  // iteration, which needs only x and u, concurrently with the A stream of the others.
+  if (cons.enabled && blockIdx.x == gridDim.x - 1) {
+    consensus_block<NT, kConsMW>(cons);
+    return;
+  }
   using V = typename Vec16<TA>::type;
   constexpr int VE = Vec16<TA>::n;
   constexpr int NW = NT / 32;
@@ -109,7 +120,7 @@ k_fused_pass(const TA* __restrict__ A, int64_t lda, const TA* __restrict__ xlo,
   TM* d_s = red + R * NW;                     // [R]
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int c = blockIdx.x, G = gridDim.x;
+  const int c = blockIdx.x, G = gridDim.x - (cons.enabled ? 1 : 0);
   const int64_t p_begin = static_cast<int64_t>(c) * geo.P / G;
   const int64_t p_end = static_cast<int64_t>(c + 1) * geo.P / G;
   const int64_t np = p_end - p_begin;
