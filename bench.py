@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--m", type=int, default=None, help="override rows (profiling small cases)")
     ap.add_argument("--pass-rows", type=int, default=0)
     ap.add_argument("--pass-stages", type=int, default=0)
+    ap.add_argument("--inner", type=int, default=1, help="inner sharing sweeps J per iteration")
     return ap.parse_args()
 
 
@@ -170,7 +171,7 @@ def run_gpu(args, rank, world):
     stream = torch.cuda.current_stream(dev)
     params = dict(loss=bc.LOSS_LOGISTIC, precision=bc.PREC_FP32, N=wl["N"], M=wl["M"],
                   kappa=wl["kappa"], gamma=wl["gamma"], rho_c=wl["rho"],
-                  pass_rows=args.pass_rows, pass_stages=args.pass_stages)
+                  pass_rows=args.pass_rows, pass_stages=args.pass_stages, inner_iters=args.inner)
 
     def barrier():
         if world > 1:
@@ -209,7 +210,7 @@ def run_gpu(args, rank, world):
         t0 = time.perf_counter()
         p = bc.default_params(loss=params["loss"], precision=params["precision"], m=wl["m"],
                               n=wl["n"], N_shards=wl["N"], M_blocks=wl["M"], kappa=wl["kappa"],
-                              gamma=wl["gamma"], rho_c=wl["rho"])
+                              gamma=wl["gamma"], rho_c=wl["rho"], inner_iters=args.inner)
         h = bc.create(p, stream)
         bc.setup(h, A_pin, b_pin)
         bc.step(h, args.steps, info=False)
@@ -249,7 +250,7 @@ def run_gpu(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded; shapes and distributions of the paper-style logistic workload)",
-        "config": config_dict(wl),
+        "config": config_dict(wl, {"inner_iters": args.inner}),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None,
                      "kernel": "k_fused_pass", "peak_kind": peak_kind + " copy bandwidth",

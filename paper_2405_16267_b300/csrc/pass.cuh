@@ -40,36 +40,53 @@ template <typename T> __device__ __forceinline__ T dev_exp(T x);
 template <> __device__ __forceinline__ float dev_exp<float>(float x) { return expf(x); }
 template <> __device__ __forceinline__ double dev_exp<double>(double x) { return exp(x); }
 
+// Quotient for a Newton step (its rounding does not enter the root: the bracket and the
+// stopping test use phi' itself): the fast approximate division in FP32.
+template <typename T> __device__ __forceinline__ T step_div(T g, T h);
+template <> __device__ __forceinline__ float step_div<float>(float g, float h) { return __fdividef(g, h); }
+template <> __device__ __forceinline__ double step_div<double>(double g, double h) { return g / h; }
+
 // omega-bar prox of eq. (p:GPU;omega) for one row:
-//   argmin_w  l(M w; b) + (M rho_l / 2) (w - a)^2.
+//   argmin_w  l(M w; b) + (M rho_l / 2) (w - a)^2,
+// w0: a starting point (the previous outer iteration's omega for this row).
 template <typename T>
-__device__ __forceinline__ T omega_prox(int loss, T a, T b, T M, T rho_l, int newton_iters) {
+__device__ __forceinline__ T omega_prox(int loss, T a, T b, T M, T rho_l, int newton_iters, T w0) {
   if (loss == LOSS_SQUARED) return (T(2) * b + rho_l * a) / (T(2) * M + rho_l);
   if (loss == LOSS_SQHINGE) {
     if (T(1) - b * M * a > T(0)) return (T(2) * b + rho_l * a) / (T(2) * M + rho_l);
     return a;
   }
   // Logistic: phi'(w) = -b M sig(-b M w) + M rho_l (w - a) is increasing with its root in
-  // [min(a, a + b/rho_l), max(...)].  Newton steps, replaced by bisection whenever a step
-  // leaves the current bracket.
+  // [min(a, a + b/rho_l), max(...)].  Safeguarded Newton: a bisection step replaces the
+  // Newton step when the latter leaves the bracket or does not shrink at least half as fast
+  // as bisection would (plain Newton can cycle on this function); the bracket follows the
+  // sign of phi'.  Stops once the step is below a few ulps of the bracket's scale.
   const T step0 = b / rho_l;
   T lo = a < a + step0 ? a : a + step0;
   T hi = a < a + step0 ? a + step0 : a;
-  // Stop once a step is below a few ulps of the bracket's scale |a| + 1/rho_l (a test
-  // relative to |w| alone never fires when the root is near 0).
   const T scale = (a < T(0) ? -a : a) + (step0 < T(0) ? -step0 : step0);
   const T stop = T(4) * FpLim<T>::eps * scale;
-  T w = a;
+  T w = w0 > lo ? (w0 < hi ? w0 : hi) : lo;
+  T dx_old = hi - lo, dx = dx_old;
   for (int it = 0; it < newton_iters; ++it) {
     const T sg = T(1) / (T(1) + dev_exp<T>(b * M * w));   // sigma(-b M w)
     const T g = -b * M * sg + M * rho_l * (w - a);
-    if (g > T(0)) hi = w; else lo = w;
+    if (g == T(0)) break;  // landed on the root
     const T h = M * M * sg * (T(1) - sg) + M * rho_l;
-    T wn = w - g / h;
-    if (!(wn > lo && wn < hi)) wn = T(0.5) * (lo + hi);
-    const T dw = wn - w;
+    if (g > T(0)) hi = w; else lo = w;
+    T wn = w - step_div<T>(g, h);
+    const T ag2 = g < T(0) ? T(-2) * g : T(2) * g;
+    const T adh = (dx_old < T(0) ? -dx_old : dx_old) * h;
+    if (!(wn >= lo && wn <= hi) || ag2 > adh) {
+      dx_old = dx;
+      dx = T(0.5) * (hi - lo);
+      wn = lo + dx;
+    } else {
+      dx_old = dx;
+      dx = w - wn;
+    }
     w = wn;
-    if ((dw < T(0) ? -dw : dw) <= stop || hi - lo <= stop) break;
+    if ((dx < T(0) ? -dx : dx) <= stop || hi - lo <= stop) break;
   }
   return w;
 }
@@ -150,7 +167,8 @@ k_fused_pass(const TA* __restrict__ A, int64_t lda, const TA* __restrict__ xlo,
   TA xr[VPT][VE];
   TM acc[VPT][VE];
   int cur = -1, shard = 0;
-  double st_res = 0.0, st_om = 0.0, st_ax = 0.0;  // lane r of warp 0: inner-residual sums
+
+  TM st_res = TM(0), st_om = TM(0), st_ax = TM(0);  // lane r of warp 0: inner-residual sums
 
   auto flush = [&](int i) {
     TM* dst = slots + static_cast<int64_t>(c + i) * lda;
@@ -182,11 +200,12 @@ k_fused_pass(const TA* __restrict__ A, int64_t lda, const TA* __restrict__ xlo,
         for (int e = 0; e < VE; ++e) { xr[kk][e] = te[e]; acc[kk][e] = TM(0); }
       }
     }
-    // Per-row scalars for the epilogue, fetched before waiting on the panel.
-    TM b_r = TM(0), nu_r = TM(0);
+    // Per-row scalars for the epilogue (the previous omega warm-starts the prox).
+    TM b_r = TM(0), nu_r = TM(0), om_r = TM(0);
     if (warp == 0 && lane < nrows) {
       b_r = b[row0 + lane];
       nu_r = nu[row0 + lane];
+      om_r = omega[row0 + lane];
     }
     const int st = static_cast<int>(k % S);
     const uint32_t parity = static_cast<uint32_t>((k / S) & 1);
@@ -230,20 +249,32 @@ k_fused_pass(const TA* __restrict__ A, int64_t lda, const TA* __restrict__ xlo,
     __syncthreads();
 
     // Row epilogue: mean block product, omega prox, nu update, target shift d.
-    if (warp == 0 && lane < nrows) {
+    if (warp == 0) {
+      // row totals: lanes [r*NW, (r+1)*NW) hold row r's per-warp partials; reduce in groups
       TM tot = TM(0);
 #pragma unroll
-      for (int w = 0; w < NW; ++w) tot += red[lane * NW + w];
+      for (int base = 0; base < R * NW; base += 32) {
+        TM pv = base + lane < R * NW ? red[base + lane] : TM(0);
+#pragma unroll
+        for (int off = NW / 2; off > 0; off >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, off);
+#pragma unroll
+        for (int rr = 0; rr < 32 / NW; ++rr) {
+          const TM t = __shfl_sync(0xffffffffu, pv, rr * NW);
+          if (lane == base / NW + rr) tot = t;
+        }
+      }
+      if (lane < nrows) {
       const TM Axb = tot / Mf;
-      const TM om = omega_prox<TM>(loss, Axb + nu_r, b_r, Mf, rho_l, newton_iters);
+      const TM om = omega_prox<TM>(loss, Axb + nu_r, b_r, Mf, rho_l, newton_iters, om_r);
       const TM nun = nu_r + Axb - om;
       omega[row0 + lane] = om;
       nu[row0 + lane] = nun;
       d_s[lane] = om - Axb - nun;
-      const double rr = static_cast<double>(Axb) - static_cast<double>(om);
-      st_res += rr * rr;
-      st_om += static_cast<double>(om) * static_cast<double>(om);
-      st_ax += static_cast<double>(Axb) * static_cast<double>(Axb);
+      const TM rr = Axb - om;
+      st_res = fma(rr, rr, st_res);
+      st_om = fma(om, om, st_om);
+      st_ax = fma(Axb, Axb, st_ax);
+      }
     }
     __syncthreads();
 
@@ -279,9 +310,9 @@ k_fused_pass(const TA* __restrict__ A, int64_t lda, const TA* __restrict__ xlo,
     st_om = warp_sum(st_om);
     st_ax = warp_sum(st_ax);
     if (lane == 0) {
-      cta_stats[c * 4 + 0] = st_res;
-      cta_stats[c * 4 + 1] = st_om;
-      cta_stats[c * 4 + 2] = st_ax;
+      cta_stats[c * 4 + 0] = static_cast<double>(st_res);
+      cta_stats[c * 4 + 1] = static_cast<double>(st_om);
+      cta_stats[c * 4 + 2] = static_cast<double>(st_ax);
       cta_stats[c * 4 + 3] = 0.0;
     }
   }
