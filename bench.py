@@ -143,6 +143,49 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ----------------------------------------------------------------------------- helpers
+
+# DRAM traffic of one pass launch from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of a 20000-row launch of the same kernel, scaled by rows to the
+# 200000-row launch.  Reported only while the kernel sources are the captured ones.
+PASS_TRAFFIC = {"sources_sha256": "61e3166fce92e110e57213d482f5f1083716ad6a620e4f3398754283abdd7000", "bytes_per_launch": 4.0712e9,
+                "capture": "profiles/k_fused_pass_r2s2_sparse_logistic_200000x5000_fp32.md"}
+PASS_SOURCES = ["paper_2405_16267_b300/csrc/pass.cuh", "paper_2405_16267_b300/csrc/nspace.cuh",
+                "paper_2405_16267_b300/csrc/common.cuh"]
+
+
+def pass_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in PASS_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def pass_traffic():
+    try:
+        if pass_sources_sha256() == PASS_TRAFFIC["sources_sha256"]:
+            return PASS_TRAFFIC["bytes_per_launch"]
+    except OSError:
+        pass
+    return None
+
+
+def reduce_max(x, device):
+    """Max of a per-rank scalar over all ranks (the timing rule: slowest rank)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(world, steps, t_max):
+    """Whole-job throughput: every rank runs `steps` iterations of its own replica."""
+    return world * steps / t_max
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def peaks():
@@ -228,17 +271,9 @@ def run_gpu(args, rank, world):
 
     # max over ranks
     t_local = ms / 1000.0
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_local], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-        if e2e:
-            te = torch.tensor([e2e["seconds"]], device=dev)
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-            e2e["value"] = world * args.steps / float(te.item())
-    else:
-        t_max = t_local
+    t_max = reduce_max(t_local, dev) if world > 1 else t_local
+    if e2e and world > 1:
+        e2e["value"] = aggregate_value(world, args.steps, reduce_max(e2e["seconds"], dev))
 
     hbm, peak_kind = peaks()
     m, n = wl["m"], wl["n"]
@@ -246,13 +281,15 @@ def run_gpu(args, rank, world):
     avg_pass_s = pass_ms / 1000.0 / max(pass_launches, 1)
     achieved = pass_bytes / avg_pass_s / 1e9
     result = {
-        "metric": METRIC, "value": world * args.steps / t_max, "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": aggregate_value(world, args.steps, t_max), "unit": UNIT,
+        "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded; shapes and distributions of the paper-style logistic workload)",
         "config": config_dict(wl, {"inner_iters": args.inner}),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
+                     "frac": achieved / hbm,
+                     "traffic": pass_traffic() if wl["m"] == WORKLOAD["m"] else None,
                      "kernel": "k_fused_pass", "peak_kind": peak_kind + " copy bandwidth",
                      "algorithmic_bytes_per_launch": pass_bytes,
                      "avg_launch_ms": avg_pass_s * 1e3, "launches_timed": pass_launches},
