@@ -22,6 +22,7 @@
 #include "common.cuh"
 #include "nspace.cuh"
 #include "pass.cuh"
+#include "polish.cuh"
 #include "setup.cuh"
 
 using namespace bic;
@@ -79,6 +80,14 @@ struct bicadmm_ctx {
   Resid* trace = nullptr;
   int* d_err = nullptr;
   std::vector<void*> allocs;
+
+  // polish buffers (allocated on first use)
+  int64_t* supp = nullptr;
+  double *AS = nullptr, *pq = nullptr, *pd1 = nullptr, *pd2 = nullptr, *pp = nullptr,
+         *pxs = nullptr, *pstep = nullptr, *pfpart = nullptr, *pgpart = nullptr,
+         *pHpart = nullptr, *pH = nullptr;
+  int* pflag = nullptr;
+  bool polish_ready = false;
 
   // profiling of the A pass
   bool prof = false;
@@ -584,6 +593,115 @@ int build_factors(bicadmm_ctx* h) {
   return check_device_error(h);
 }
 
+// ---------------------------------------------------------------- support and polish
+constexpr int kPolishRowBlocks = 592;
+constexpr int kPolishChunks = 64;
+constexpr int kMaxPolishKappa = 1024;
+
+int compute_support(bicadmm_ctx* h) {
+  if (!h->supp) {
+    int rc = dev_alloc(h, &h->supp, h->p.kappa * sizeof(int64_t));
+    if (rc != BICADMM_OK) return rc;
+  }
+  k_support<1024, 1><<<1, 1024, 0, h->stream>>>(h->z, h->key, h->p.n, h->p.kappa, h->supp);
+  CK(cudaGetLastError());
+  h->launches += 1;
+  return BICADMM_OK;
+}
+
+template <typename TA, typename TM>
+int run_polish(bicadmm_ctx* h, std::vector<double>& xs_out) {
+  const int64_t m = h->p.m;
+  const int kappa = static_cast<int>(h->p.kappa);
+  const double gamma = h->p.gamma;
+  const int nblk = static_cast<int>(std::min<int64_t>(kPolishRowBlocks, (m + 255) / 256));
+  const int nch = static_cast<int>(std::min<int64_t>(kPolishChunks, (m + 255) / 256));
+  const int64_t chunk = (m + nch - 1) / nch;
+  if (!h->polish_ready) {
+    int rc;
+#define AL(ptr, bytes) if ((rc = dev_alloc(h, &(ptr), (bytes))) != BICADMM_OK) return rc
+    AL(h->AS, static_cast<size_t>(kappa) * m * sizeof(double));
+    AL(h->pq, m * sizeof(double));
+    AL(h->pd1, m * sizeof(double));
+    AL(h->pd2, m * sizeof(double));
+    AL(h->pp, m * sizeof(double));
+    AL(h->pxs, kappa * sizeof(double));
+    AL(h->pstep, kappa * sizeof(double));
+    AL(h->pfpart, nblk * sizeof(double));
+    AL(h->pgpart, static_cast<size_t>(nch) * kappa * sizeof(double));
+    AL(h->pHpart, static_cast<size_t>(nch) * kappa * kappa * sizeof(double));
+    AL(h->pH, static_cast<size_t>(kappa) * kappa * sizeof(double));
+    AL(h->pflag, sizeof(int));
+#undef AL
+    h->polish_ready = true;
+  }
+  int rc = compute_support(h);
+  if (rc != BICADMM_OK) return rc;
+  const dim3 ggrid(static_cast<unsigned>(std::min<int64_t>((m + 255) / 256, 1024)), kappa);
+  k_gather_support<TA><<<ggrid, 256, 0, h->stream>>>(static_cast<const TA*>(h->A), h->lda, h->supp, m, h->AS);
+  CK(cudaGetLastError());
+  h->launches += 1;
+  std::vector<double> xs(kappa, 0.0), step(kappa), fpart(nblk);
+  CK(cudaMemsetAsync(h->pxs, 0, kappa * sizeof(double), h->stream));
+  const int T = (kappa + 31) / 32;
+  const size_t ksm = kappa * sizeof(double);
+  auto objective = [&](double alpha, double* out) -> int {
+    k_polish_rows<TM, 256><<<nblk, 256, ksm, h->stream>>>(h->AS, h->pxs, kappa, m,
+        static_cast<const TM*>(h->b), h->p.loss, h->pq, h->pd1, h->pd2, h->pp, alpha, h->pfpart);
+    CK(cudaGetLastError());
+    h->launches += 1;
+    CK(cudaMemcpyAsync(fpart.data(), h->pfpart, nblk * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    double f = 0.0;
+    for (double v : fpart) f += v;
+    *out = f;
+    return BICADMM_OK;
+  };
+  for (int it = 0; it < 100; ++it) {
+    double f0;
+    if ((rc = objective(0.0, &f0)) != BICADMM_OK) return rc;  // also fills q, l', l''
+    double xx = 0.0;
+    for (double v : xs) xx += v * v;
+    f0 += xx / (2.0 * gamma);
+    k_polish_grad<256><<<dim3(nch, kappa), 256, 0, h->stream>>>(h->AS, h->pd1, kappa, m, chunk, h->pgpart);
+    k_polish_hess<<<dim3(T * (T + 1) / 2, nch), 256, 0, h->stream>>>(h->AS, h->pd2, kappa, m, chunk, h->pHpart);
+    k_polish_solve<256><<<1, 256, 2 * ksm, h->stream>>>(h->pHpart, h->pgpart, nch, h->pxs, kappa, gamma,
+                                                        h->pH, h->pstep, h->pflag);
+    k_polish_dir<256><<<nblk, 256, ksm, h->stream>>>(h->AS, h->pstep, kappa, m, h->pp);
+    CK(cudaGetLastError());
+    h->launches += 4;
+    int flag = 0;
+    CK(cudaMemcpyAsync(step.data(), h->pstep, kappa * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&flag, h->pflag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (flag) return fail(h, BICADMM_ERR_NUMERIC, "polish: restricted Hessian is not positive definite");
+    double alpha = 1.0;
+    for (;;) {
+      double ft;
+      if ((rc = objective(alpha, &ft)) != BICADMM_OK) return rc;
+      double x2 = 0.0;
+      for (int k = 0; k < kappa; ++k) {
+        const double v = xs[k] - alpha * step[k];
+        x2 += v * v;
+      }
+      ft += x2 / (2.0 * gamma);
+      if (!(ft > f0 + 1e-16 * std::fabs(f0)) || !(alpha > 1e-12)) break;
+      alpha *= 0.5;
+    }
+    double sn = 0.0, xn = 0.0;
+    for (int k = 0; k < kappa; ++k) {
+      xs[k] -= alpha * step[k];
+      sn += (alpha * step[k]) * (alpha * step[k]);
+      xn += xs[k] * xs[k];
+    }
+    CK(cudaMemcpyAsync(h->pxs, xs.data(), kappa * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (std::sqrt(sn) <= 1e-13 * std::max(1.0, std::sqrt(xn))) break;
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  xs_out = xs;
+  return BICADMM_OK;
+}
+
 }  // namespace
 
 // =============================================================================== C ABI
@@ -703,8 +821,26 @@ int bicadmm_get_x(bicadmm_t h, double* x_host, int64_t len, int32_t polished, in
   if (!h) return BICADMM_ERR_ARG;
   if (!h->ready) return fail(h, BICADMM_ERR_STATE, "bicadmm_get_x before setup");
   if (!x_host || len != h->p.n) return fail(h, BICADMM_ERR_ARG, "x_host must hold n doubles");
-  if (polished || support_out) return fail(h, BICADMM_ERR_UNSUPPORTED, "polished output is not available in this build");
-  CK(cudaMemcpyAsync(x_host, h->z, h->p.n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (polished && h->p.kappa > kMaxPolishKappa)
+    return fail(h, BICADMM_ERR_UNSUPPORTED, "polish supports kappa <= 1024");
+  if (!polished) {
+    CK(cudaMemcpyAsync(x_host, h->z, h->p.n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (support_out) {
+      int rc = compute_support(h);
+      if (rc != BICADMM_OK) return rc;
+    }
+  } else {
+    std::vector<double> xs;
+    int rc = h->esz == 8 ? run_polish<double, double>(h, xs) : run_polish<float, float>(h, xs);
+    if (rc != BICADMM_OK) return rc;
+    std::vector<int64_t> sp(h->p.kappa);
+    CK(cudaMemcpyAsync(sp.data(), h->supp, h->p.kappa * sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    std::fill(x_host, x_host + h->p.n, 0.0);
+    for (int64_t k = 0; k < h->p.kappa; ++k) x_host[sp[k]] = xs[k];
+  }
+  if (support_out)
+    CK(cudaMemcpyAsync(support_out, h->supp, h->p.kappa * sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return check_device_error(h);
 }
