@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--pass-rows", type=int, default=0)
     ap.add_argument("--pass-stages", type=int, default=0)
     ap.add_argument("--inner", type=int, default=1, help="inner sharing sweeps J per iteration")
+    ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance leg")
     return ap.parse_args()
 
 
@@ -300,6 +301,46 @@ def run_gpu(args, rank, world):
     return result
 
 
+# ----------------------------------------------------------------------------- time to tol
+
+TABLE1 = dict(m=100000, n=2000, sparsity=0.9, noise=0.01, N=4, M=4, rho=1.0, gamma=10.0, seed=0)
+TABLE1_PAPER_S = 1.1  # Table 1: m = 1e5, n = 2k, s_l = 0.9 (RTX 4070 + i7-13700; tolerance unstated)
+
+
+def run_time_to_tol(stream, tol=1e-6):
+    """Time to max(p_rel, d_rel, b_rel, i_rel) <= tol on the paper's Table-1 setting, for the
+    plain FP64 path and the FP32 path on the same inputs (A on the device before timing)."""
+    import torch
+    from paper_2405_16267_b300 import bicadmm as bc
+    P = synth.table1_sls(**TABLE1)
+    A64 = torch.from_numpy(P.A).cuda()
+    b64 = torch.from_numpy(P.b).cuda()
+    truth = set(np.flatnonzero(P.x_star).tolist())
+    out = {"workload": P.name, "tol_rel": tol, "N_shards": P.N, "M_blocks": P.M, "kappa": P.kappa,
+           "check_every": 5}
+    for name, prec in (("fp64", bc.PREC_FP64), ("fp32", bc.PREC_FP32)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = bc.Solver(A64 if prec == bc.PREC_FP64 else A64.float(), b64, loss=P.loss, N=P.N, M=P.M,
+                      kappa=P.kappa, gamma=P.gamma, rho_c=P.rho, precision=prec, tol_rel=tol,
+                      check_every=5, max_iters=5000, stream=stream)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        info = s.solve()
+        t2 = time.perf_counter()
+        x, supp = bc.get_x(s.h, P.n, polished=True, with_support=True, kappa=P.kappa)
+        t3 = time.perf_counter()
+        s.close()
+        out[name] = {"setup_s": t1 - t0, "solve_s": t2 - t1, "polish_s": t3 - t2,
+                     "iters": int(info.iters), "converged": bool(info.converged),
+                     "support_recovered": set(supp.tolist()) == truth,
+                     "rel_err_polished_vs_planted": float(np.linalg.norm(x - P.x_star) / np.linalg.norm(P.x_star))}
+    out["solve_speedup_fp32_vs_fp64"] = out["fp64"]["solve_s"] / out["fp32"]["solve_s"]
+    out["paper_table1_s"] = {"value": TABLE1_PAPER_S, "hardware": "RTX 4070 + i7-13700, PyTorch 2.3",
+                             "note": "context only: other machine, tolerance unstated"}
+    return out
+
+
 # ----------------------------------------------------------------------------- CPU oracle
 
 def blas_threads():
@@ -363,6 +404,9 @@ def main():
         res = run_reference(args, rank, world)
     else:
         res = run_gpu(args, rank, world)
+        if rank == 0 and not args.no_ttt:
+            import torch
+            res["time_to_tol"] = run_time_to_tol(torch.cuda.current_stream())
         if rank == 0 and not args.no_cpu_baseline and world == 1:
             res["cpu_baseline"] = run_oracle_sample(dict(WORKLOAD), steps=8, warmup=1, budget_s=20.0)
     if world > 1 and args.impl == "gpu":

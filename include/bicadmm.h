@@ -151,11 +151,15 @@ int bicadmm_get_x(bicadmm_t h, double* x_host, int64_t len, int32_t polished, in
  * field's length.  Synchronises the stream.  For tests, checkpoints and diagnostics. */
 int bicadmm_get_state(bicadmm_t h, int32_t field, double* out_host, int64_t len);
 
-/* Profiling: when on != 0, every launch of the fused A-pass kernel is bracketed by CUDA
- * events on the handle's stream.  bicadmm_get_pass_time() synchronises, returns the
- * summed device time (ms) and launch count since profiling was switched on, and resets
- * them. */
+/* Profiling with CUDA events on the handle's stream.  on = 1: every launch of the fused
+ * A-pass kernel is bracketed; on = 2: every kernel of the iteration (pass, x-update, dual,
+ * extra right-hand-side sweeps); on = 0: off.  Switching resets the records.
+ * bicadmm_get_kernel_times() synchronises and writes, per kernel kind (0 pass, 1 x-update,
+ * 2 dual, 3 right-hand side), the summed device time in ms to ms_out[4] and the launch
+ * count to launches_out[4] (either may be NULL); reset != 0 clears the records.
+ * bicadmm_get_pass_time() returns the pass's entries and clears the records. */
 int bicadmm_set_profiling(bicadmm_t h, int32_t on);
+int bicadmm_get_kernel_times(bicadmm_t h, double* ms_out, int64_t* launches_out, int32_t reset);
 int bicadmm_get_pass_time(bicadmm_t h, double* ms_out, int64_t* launches_out);
 
 /* Allocation-free consensus update.  The paper has no counterpart: this entry point exists

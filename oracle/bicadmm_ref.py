@@ -197,7 +197,7 @@ class BiCADMM:
     """
 
     def __init__(self, A, b, loss, N, M, kappa, gamma=10.0, rho_c=1.0, rho_b=None,
-                 rho_l=None, inner_iters=1):
+                 rho_l=None, inner_iters=1, n_shards_total=None):
         self.A = np.asarray(A, dtype=np.float64)
         self.b = np.asarray(b, dtype=np.float64)
         self.m, self.n = self.A.shape
@@ -208,8 +208,11 @@ class BiCADMM:
         self.J = int(inner_iters)
         self.shards = split_ranges(self.m, self.N)
         self.blocks = split_ranges(self.n, self.M)
-        # coefficient of x_ij in r_j (eq. before the sharing problem): 1/(N gamma) + rho_c
-        self.c0 = 1.0 / (self.N * self.gamma) + self.rho_c
+        # coefficient of x_ij in r_j (eq. before the sharing problem): 1/(N gamma) + rho_c.
+        # n_shards_total lets an instance hold a subset of the shards of a larger problem
+        # (its x-steps are then those of the full problem; its z-step is not).
+        N_all = self.N if n_shards_total is None else int(n_shards_total)
+        self.c0 = 1.0 / (N_all * self.gamma) + self.rho_c
         # Block factors for the x_ij solve of eq. (p:GPU;x): setting its gradient to zero
         # gives (rho_l A_ij'A_ij + c0 I) x_ij = rho_l A_ij' c_ij + rho_c (z_j - u_ij).
         self.factors = []

@@ -73,6 +73,8 @@ SIGNATURES = [
     ("bicadmm_set_profiling", ctypes.c_int, [_VP, ctypes.c_int32]),
     ("bicadmm_get_pass_time", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(ctypes.c_int64)]),
+    ("bicadmm_get_kernel_times", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
+                                                ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
     ("bicadmm_consensus_step_noalloc", ctypes.c_int,
      [_VP, _VP, _VP, _VP, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
       ctypes.c_double, _VP]),
@@ -185,8 +187,20 @@ def get_state(h, field, length):
     return out
 
 
+KERNEL_KINDS = ("pass", "xupd", "dual", "rhs")
+
+
 def set_profiling(h, on=True):
-    _check(lib().bicadmm_set_profiling(h, int(bool(on))), h)
+    """on: False/0 off, True/1 the A pass only, 2 every kernel of the iteration."""
+    _check(lib().bicadmm_set_profiling(h, int(on)), h)
+
+
+def get_kernel_times(h, reset=True):
+    """{kind: (total ms, launches)} for the kernels timed since profiling was switched on."""
+    ms = (ctypes.c_double * 4)()
+    cnt = (ctypes.c_int64 * 4)()
+    _check(lib().bicadmm_get_kernel_times(h, ms, cnt, int(bool(reset))), h)
+    return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_KINDS)}
 
 
 def get_pass_time(h):

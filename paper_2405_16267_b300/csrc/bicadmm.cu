@@ -89,12 +89,11 @@ struct bicadmm_ctx {
   int* pflag = nullptr;
   bool polish_ready = false;
 
-  // profiling of the A pass
-  bool prof = false;
-  std::vector<cudaEvent_t> ev;
-  size_t ev_used = 0;
-  double prof_ms = 0.0;
-  int64_t prof_launches = 0;
+  // profiling: CUDA events around kernel launches on the handle's stream
+  int prof = 0;                 // 0 off, 1 the A pass only, 2 every kernel of the iteration
+  std::vector<cudaEvent_t> ev;  // pairs (start, end)
+  std::vector<int> ev_kind;     // kernel kind of each pair
+  size_t ev_used = 0;           // events recorded
 };
 
 namespace {
@@ -243,6 +242,34 @@ int pick_vpt(int64_t nvec) {
   return -1;
 }
 
+// ---------------------------------------------------------------- profiling events
+enum KernelKind { KIND_PASS = 0, KIND_XUPD = 1, KIND_DUAL = 2, KIND_RHS = 3, KIND_COUNT = 4 };
+
+bool prof_on(const bicadmm_ctx* h, int kind) {
+  return h->prof == 2 || (h->prof == 1 && kind == KIND_PASS);
+}
+
+int prof_begin(bicadmm_ctx* h, int kind) {
+  if (!prof_on(h, kind)) return BICADMM_OK;
+  if (h->ev_used + 2 > h->ev.size()) {
+    for (int q = 0; q < 64; ++q) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      h->ev.push_back(e);
+    }
+  }
+  CK(cudaEventRecord(h->ev[h->ev_used], h->stream));
+  return BICADMM_OK;
+}
+
+int prof_end(bicadmm_ctx* h, int kind) {
+  if (!prof_on(h, kind)) return BICADMM_OK;
+  CK(cudaEventRecord(h->ev[h->ev_used + 1], h->stream));
+  h->ev_kind.push_back(kind);
+  h->ev_used += 2;
+  return BICADMM_OK;
+}
+
 // ---------------------------------------------------------------- one outer iteration
 template <typename TM>
 int run_iterations(bicadmm_ctx* h, int n_iters) {
@@ -254,37 +281,39 @@ int run_iterations(bicadmm_ctx* h, int n_iters) {
   const dim3 dual_grid(h->dual_chunks, N);
   for (int it = 0; it < n_iters; ++it) {
     for (int jj = 0; jj < h->p.inner_iters; ++jj) {
-      k_rhs<TM><<<rhs_grid, 256, 0, h->stream>>>(static_cast<const TM*>(h->slots), h->d_slot_lo,
-                                                   h->d_slot_hi, h->x, h->u, h->z, h->r, lda,
-                                                   h->p.rho_l, h->p.rho_c, h->c0);
+      // The first sweep's right-hand side was formed by the previous iteration's k_dual (or
+      // is zero after setup); later sweeps form it from the previous pass's slots.
+      int rc;
+      if (jj > 0) {
+        if ((rc = prof_begin(h, KIND_RHS)) != BICADMM_OK) return rc;
+        k_rhs<TM><<<rhs_grid, 256, 0, h->stream>>>(static_cast<const TM*>(h->slots), h->d_slot_lo,
+                                                     h->d_slot_hi, h->x, h->u, h->z, h->r, lda,
+                                                     h->p.rho_l, h->p.rho_c, h->c0);
+        if ((rc = prof_end(h, KIND_RHS)) != BICADMM_OK) return rc;
+        h->launches += 1;
+      }
+      if ((rc = prof_begin(h, KIND_XUPD)) != BICADMM_OK) return rc;
       k_xupd<TM, TM, kXupdThreads, kXupdRows><<<xupd_grid, kXupdThreads, xupd_smem, h->stream>>>(
           static_cast<const TM*>(h->Pm), h->d_P_off, h->d_blk_col0, h->d_blk_ldp, h->r, h->x,
           static_cast<TM*>(h->xlo), M, lda);
-      if (h->prof) {
-        if (h->ev_used + 2 > h->ev.size()) {
-          for (int q = 0; q < 64; ++q) {
-            cudaEvent_t e;
-            CK(cudaEventCreate(&e));
-            h->ev.push_back(e);
-          }
-        }
-        CK(cudaEventRecord(h->ev[h->ev_used], h->stream));
-      }
+      if ((rc = prof_end(h, KIND_XUPD)) != BICADMM_OK) return rc;
+      if ((rc = prof_begin(h, KIND_PASS)) != BICADMM_OK) return rc;
       // The last sweep's pass also runs the global step in its spare CTA.
       const bool last = jj == h->p.inner_iters - 1;
-      int rc = (h->p.precision == BICADMM_PREC_FP64) ? launch_pass<double, double>(h, last)
-                                                      : launch_pass<float, float>(h, last);
+      rc = (h->p.precision == BICADMM_PREC_FP64) ? launch_pass<double, double>(h, last)
+                                                  : launch_pass<float, float>(h, last);
       if (rc != BICADMM_OK) return rc;
-      if (h->prof) {
-        CK(cudaEventRecord(h->ev[h->ev_used + 1], h->stream));
-        h->ev_used += 2;
-      }
-      h->launches += 3;
+      if ((rc = prof_end(h, KIND_PASS)) != BICADMM_OK) return rc;
+      h->launches += 2;
     }
-    k_dual<kDualThreads><<<dual_grid, kDualThreads, 0, h->stream>>>(
-        h->u, h->x, h->z, h->dual_part, h->cta_stats, h->G, h->gs, h->trace, kTraceCap, N, n,
+    int rc;
+    if ((rc = prof_begin(h, KIND_DUAL)) != BICADMM_OK) return rc;
+    k_dual<TM, kDualThreads><<<dual_grid, kDualThreads, 0, h->stream>>>(
+        h->u, h->x, h->z, static_cast<const TM*>(h->slots), h->d_slot_lo, h->d_slot_hi, h->r,
+        h->p.rho_l, h->c0, h->dual_part, h->cta_stats, h->G, h->gs, h->trace, kTraceCap, N, n,
         lda, h->p.rho_c, h->d_err);
     CK(cudaGetLastError());
+    if ((rc = prof_end(h, KIND_DUAL)) != BICADMM_OK) return rc;
     h->launches += 1;
     h->iters_done += 1;
   }
@@ -438,7 +467,7 @@ int build_geometry(bicadmm_ctx* h) {
     h->slot_hi[i] = owner(h->panel_start[i + 1] - 1) + i;
   }
   h->nslots = h->G + h->N;
-  h->dual_chunks = static_cast<int>((p.n + kDualThreads - 1) / kDualThreads);
+  h->dual_chunks = static_cast<int>((h->lda + kDualThreads - 1) / kDualThreads);
   return BICADMM_OK;
 }
 
@@ -898,25 +927,43 @@ int bicadmm_get_state(bicadmm_t h, int32_t field, double* out_host, int64_t len)
 
 int bicadmm_set_profiling(bicadmm_t h, int32_t on) {
   if (!h) return BICADMM_ERR_ARG;
-  h->prof = on != 0;
+  if (on < 0 || on > 2) return fail(h, BICADMM_ERR_ARG, "profiling mode must be 0, 1 or 2");
+  h->prof = on;
   h->ev_used = 0;
-  h->prof_ms = 0.0;
-  h->prof_launches = 0;
+  h->ev_kind.clear();
+  return BICADMM_OK;
+}
+
+int bicadmm_get_kernel_times(bicadmm_t h, double* ms_out, int64_t* launches_out, int32_t reset) {
+  if (!h) return BICADMM_ERR_ARG;
+  CK(cudaStreamSynchronize(h->stream));
+  double tot[KIND_COUNT] = {0.0, 0.0, 0.0, 0.0};
+  int64_t cnt[KIND_COUNT] = {0, 0, 0, 0};
+  for (size_t q = 0; q + 1 < h->ev_used; q += 2) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev[q], h->ev[q + 1]));
+    const int kind = h->ev_kind[q / 2];
+    tot[kind] += ms;
+    cnt[kind] += 1;
+  }
+  for (int k = 0; k < KIND_COUNT; ++k) {
+    if (ms_out) ms_out[k] = tot[k];
+    if (launches_out) launches_out[k] = cnt[k];
+  }
+  if (reset) {
+    h->ev_used = 0;
+    h->ev_kind.clear();
+  }
   return BICADMM_OK;
 }
 
 int bicadmm_get_pass_time(bicadmm_t h, double* ms_out, int64_t* launches_out) {
-  if (!h) return BICADMM_ERR_ARG;
-  CK(cudaStreamSynchronize(h->stream));
-  double tot = 0.0;
-  for (size_t q = 0; q + 1 < h->ev_used; q += 2) {
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, h->ev[q], h->ev[q + 1]));
-    tot += ms;
-  }
-  if (ms_out) *ms_out = tot;
-  if (launches_out) *launches_out = static_cast<int64_t>(h->ev_used / 2);
-  h->ev_used = 0;
+  double ms[KIND_COUNT];
+  int64_t cnt[KIND_COUNT];
+  int rc = bicadmm_get_kernel_times(h, ms, cnt, 1);
+  if (rc != BICADMM_OK) return rc;
+  if (ms_out) *ms_out = ms[KIND_PASS];
+  if (launches_out) *launches_out = cnt[KIND_PASS];
   return BICADMM_OK;
 }
 

@@ -6,7 +6,7 @@
 //   consensus   w = (1/N) sum_i (x_i + u_i), (z, t) root solve,    eqs. (global-z-t-updae),
 //               top-kappa s, v, d_r, b_r (one CTA; run by the      (s-update-final), (v-update)
 //               fused pass's spare CTA or by k_global)
-//   k_dual      u_i += x_i - z, p_r, inner residual                eq. (u-update), Termination
+//   k_dual      u_i += x_i - z, p_r, inner residual, next r_i      eq. (u-update), Termination
 #pragma once
 
 #include "common.cuh"
@@ -74,15 +74,28 @@ k_xupd(const TP* __restrict__ P, const int64_t* __restrict__ P_off,
   const TP* Pb = P + P_off[i * M + j];
   const V* rv = reinterpret_cast<const V*>(rs);
   const int nv = ldp / VE;
+  constexpr int U = 8;  // 16-byte loads in flight per lane
   for (int row = row_begin + warp; row < row_begin + ROWS && row < nj; row += XT / 32) {
     const V* pr = reinterpret_cast<const V*>(Pb + static_cast<int64_t>(row) * ldp);
     TP acc = TP(0);
-    for (int k = lane; k < nv; k += 32) {
-      const V a = pr[k], bb = rv[k];
-      const TP* ae = reinterpret_cast<const TP*>(&a);
-      const TP* be = reinterpret_cast<const TP*>(&bb);
+    for (int k0 = 0; k0 < nv; k0 += 32 * U) {
+      V a[U];
 #pragma unroll
-      for (int e = 0; e < VE; ++e) acc = fma(ae[e], be[e], acc);
+      for (int q = 0; q < U; ++q) {
+        const int k = k0 + q * 32 + lane;
+        if (k < nv) a[q] = pr[k]; else a[q] = V{};
+      }
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int k = k0 + q * 32 + lane;
+        if (k < nv) {
+          const V bb = rv[k];
+          const TP* ae = reinterpret_cast<const TP*>(&a[q]);
+          const TP* be = reinterpret_cast<const TP*>(&bb);
+#pragma unroll
+          for (int e = 0; e < VE; ++e) acc = fma(ae[e], be[e], acc);
+        }
+      }
     }
     acc = warp_sum(acc);
     if (lane == 0) {
@@ -370,12 +383,17 @@ __global__ void __launch_bounds__(GT, 1) k_global(ConsensusArgs a) {
 }
 
 // ------------------------------------------------------------------------------ k_dual
-// Grid (chunks, N), DT threads.  u_i += x_i - z; per-(shard, chunk) sums of ||x_i - z||^2
-// and ||x_i||^2; the last CTA to finish reduces them (fixed order) with the pass's
-// inner-residual sums into the residual record and advances the iteration counter.
-template <int DT>
+// Grid (chunks, N), DT threads.  End of an outer iteration: u_i += x_i - z (eq. u-update),
+// per-(shard, chunk) sums of ||x_i - z||^2 and ||x_i||^2, and the right-hand side of the next
+// iteration's first x-block solve, r_i = rho_l q_i + rho_c (z - u_i) - c0 x_i with q_i the
+// fixed-order sum of the last pass's slots of shard i.  The last CTA to finish reduces the
+// sums (fixed order) with the pass's inner-residual sums into the residual record and
+// advances the iteration counter.
+template <typename TM, int DT>
 __global__ void __launch_bounds__(DT)
 k_dual(double* __restrict__ u, const double* __restrict__ x, const double* __restrict__ z,
+       const TM* __restrict__ slots, const int* __restrict__ slot_lo,
+       const int* __restrict__ slot_hi, double* __restrict__ r, double rho_l, double c0,
        double* __restrict__ part, const double* __restrict__ cta_stats, int G, GlobalState* gs,
        Resid* trace, int trace_cap, int N, int64_t n, int64_t lda, double rho_c, int* err) {
   __shared__ double red[32 * 2];
@@ -383,11 +401,15 @@ k_dual(double* __restrict__ u, const double* __restrict__ x, const double* __res
   const int i = blockIdx.y, nch = gridDim.x;
   const int64_t col = static_cast<int64_t>(blockIdx.x) * DT + threadIdx.x;
   double a[2] = {0.0, 0.0};
-  if (col < n) {
+  if (col < lda) {
     const int64_t o = i * lda + col;
-    const double xv = x[o], dv = xv - z[col];
-    u[o] += dv;
-    a[0] = dv * dv;
+    const double xv = x[o], zv = z[col], dv = xv - zv;
+    const double un = u[o] + dv;
+    u[o] = un;
+    TM q = TM(0);  // the slots are partial sums in the arithmetic type of the pass
+    for (int sl = slot_lo[i]; sl <= slot_hi[i]; ++sl) q += slots[sl * lda + col];
+    r[o] = rho_l * static_cast<double>(q) + rho_c * (zv - un) - c0 * xv;
+    a[0] = dv * dv;  // padding columns hold zeros
     a[1] = xv * xv;
   }
   block_sum<2>(a, red);
@@ -401,21 +423,21 @@ k_dual(double* __restrict__ u, const double* __restrict__ x, const double* __res
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // Final reduction by one warp in a fixed order.
+  // Final reduction by one warp in a fixed order: lane l takes shards l, l+32, ...
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     double pr = 0.0, nx = 0.0;
-    for (int ii = 0; ii < N; ++ii) {
+    for (int ii = lane; ii < N; ii += 32) {
       double s0 = 0.0, s1 = 0.0;
-      for (int cidx = lane; cidx < nch; cidx += 32) {
+      for (int cidx = 0; cidx < nch; ++cidx) {
         s0 += part[(static_cast<int64_t>(ii) * nch + cidx) * 2 + 0];
         s1 += part[(static_cast<int64_t>(ii) * nch + cidx) * 2 + 1];
       }
-      s0 = warp_sum(s0);
-      s1 = warp_sum(s1);
       pr += sqrt(s0);
       nx += sqrt(s1);
     }
+    pr = warp_sum(pr);
+    nx = warp_sum(nx);
     double q0 = 0.0, q1 = 0.0, q2 = 0.0;
     for (int g = lane; g < G; g += 32) {
       q0 += cta_stats[g * 4 + 0];

@@ -151,11 +151,15 @@ def sparse_linear(m=2000, n=200, nnz=10, noise=0.1, N=4, M=2, kappa=10, rho=1.0,
     indices, b = A x* + N(0, noise^2).  Defaults are the 2000 x 200 FP64 workload
     (N=4 shards of 500 rows, M=2 blocks of 100 columns, kappa=10, rho=1, 200 iterations).
 
-    unit_columns=True normalises the columns of A to unit l2 norm, as the paper's
-    experiments do (Sec. 4).
+    unit_columns=True normalises the columns of A to unit l2 norm; unit_columns="shard"
+    normalises the columns of each shard's rows A_i separately, as the paper's experiments
+    do (Sec. 4, "Hardware and Software").
     """
     A = gaussian_rows(m, n, seed)
-    if unit_columns:
+    if unit_columns == "shard":
+        for (r0, r1) in split_ranges(m, N):
+            A[r0:r1] /= np.linalg.norm(A[r0:r1], axis=0, keepdims=True)
+    elif unit_columns:
         A /= np.linalg.norm(A, axis=0, keepdims=True)
     x_star = planted_support(n, nnz, seed, "pm_uniform12")
     b = A @ x_star + noise * _noise(m, seed)
@@ -188,6 +192,19 @@ def sparse_logistic(m=200000, n=5000, nnz=50, corr=0.3, noise=0.5, N=16, M=8, ka
         r = c
     return Problem("sparse_logistic_%dx%d" % (m, n), A, b, x_star, LOSS_LOGISTIC, N, M, kappa,
                    rho, gamma, iters)
+
+
+def table1_sls(m=100000, n=2000, sparsity=0.9, noise=0.01, N=4, M=4, rho=1.0, gamma=10.0,
+               seed=0) -> Problem:
+    """The paper's timing experiment (Sec. 4, Table 1): sparse least squares over N = 4 nodes
+    of m/N rows, A_i i.i.d. N(0,1) with unit-norm columns per node, x_true with
+    kappa = round(n (1 - sparsity)) nonzeros (+/-U[1,2] here; the paper does not say), and
+    b = A x_true + e with e ~ N(0, noise^2) (the paper leaves Sigma unstated)."""
+    kappa = int(round(n * (1.0 - sparsity)))
+    P = sparse_linear(m=m, n=n, nnz=kappa, noise=noise, N=N, M=M, kappa=kappa, rho=rho,
+                      gamma=gamma, seed=seed, unit_columns="shard")
+    P.name = "sls_table1_%dx%d_s%.1f" % (m, n, sparsity)
+    return P
 
 
 def sparse_sqhinge(m=4000, n=400, nnz=12, noise=0.1, N=4, M=2, kappa=12, rho=1.0,
