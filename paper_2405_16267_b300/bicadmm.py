@@ -75,6 +75,8 @@ SIGNATURES = [
                                              ctypes.POINTER(ctypes.c_int64)]),
     ("bicadmm_get_kernel_times", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
                                                 ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
+    ("bicadmm_get_trace", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_int64)]),
     ("bicadmm_consensus_step_noalloc", ctypes.c_int,
      [_VP, _VP, _VP, _VP, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
       ctypes.c_double, _VP]),
@@ -185,6 +187,20 @@ def get_state(h, field, length):
     _check(lib().bicadmm_get_state(h, int(field), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                    int(length)), h)
     return out
+
+
+TRACE_FIELDS = ("iter", "p_r", "d_r", "b_r", "i_r", "p_rel", "d_rel", "b_rel", "i_rel", "t", "v",
+                "tau", "znorm", "zt_steps")
+
+
+def get_trace(h, max_records=4096):
+    """Residual records of the last iterations as a dict of numpy arrays (oldest first)."""
+    out = np.zeros((int(max_records), len(TRACE_FIELDS)))
+    cnt = ctypes.c_int64()
+    _check(lib().bicadmm_get_trace(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   int(max_records), ctypes.byref(cnt)), h)
+    out = out[:cnt.value]
+    return {k: out[:, i] for i, k in enumerate(TRACE_FIELDS)}
 
 
 KERNEL_KINDS = ("pass", "xupd", "dual", "rhs")

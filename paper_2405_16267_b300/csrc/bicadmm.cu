@@ -925,6 +925,29 @@ int bicadmm_get_state(bicadmm_t h, int32_t field, double* out_host, int64_t len)
   return check_device_error(h);
 }
 
+int bicadmm_get_trace(bicadmm_t h, double* out_host, int64_t max_records, int64_t* n_out) {
+  if (!h) return BICADMM_ERR_ARG;
+  if (!out_host || max_records < 0) return fail(h, BICADMM_ERR_ARG, "out_host is NULL or max_records < 0");
+  GlobalState g;
+  CK(cudaMemcpyAsync(&g, h->gs, sizeof(g), cudaMemcpyDeviceToHost, h->stream));
+  std::vector<Resid> recs(kTraceCap);
+  CK(cudaMemcpyAsync(recs.data(), h->trace, kTraceCap * sizeof(Resid), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const int64_t avail = std::min<int64_t>(g.iter, kTraceCap);
+  const int64_t cnt = std::min<int64_t>(avail, max_records);
+  for (int64_t q = 0; q < cnt; ++q) {
+    const Resid& r = recs[(g.iter - cnt + q) % kTraceCap];
+    double* o = out_host + q * 14;
+    o[0] = static_cast<double>(r.iter);
+    o[1] = r.p_r; o[2] = r.d_r; o[3] = r.b_r; o[4] = r.i_r;
+    o[5] = r.p_rel; o[6] = r.d_rel; o[7] = r.b_rel; o[8] = r.i_rel;
+    o[9] = r.t; o[10] = r.v; o[11] = r.tau; o[12] = r.znorm;
+    o[13] = static_cast<double>(r.zt_steps);
+  }
+  if (n_out) *n_out = cnt;
+  return check_device_error(h);
+}
+
 int bicadmm_set_profiling(bicadmm_t h, int32_t on) {
   if (!h) return BICADMM_ERR_ARG;
   if (on < 0 || on > 2) return fail(h, BICADMM_ERR_ARG, "profiling mode must be 0, 1 or 2");
