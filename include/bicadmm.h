@@ -196,6 +196,38 @@ int bicadmm_consensus_step_noalloc(const double* w, double* z, double* s, double
                                    int64_t kappa, int32_t N_shards, double rho_c, double rho_b,
                                    void* stream);
 
+/* Batched execution (not part of the paper): advance several independent, set-up handles
+ * together, one launch per kernel kind per outer iteration for all of them (x-update, one
+ * persistent A pass over a panel list spanning every instance's shards, consensus step,
+ * dual update).  Each instance's iterates are those of bicadmm_step up to rounding (the
+ * A'd partial sums are grouped differently).  Requirements: every handle set up, all of
+ * one precision and device, inner_iters = 1.  The batch references the handles (it does
+ * not own them); destroy the batch before any of its handles.  Handles may still be stepped
+ * alone between batch steps.
+ * flags: BICADMM_BATCH_GRAPH captures one iteration into a CUDA graph and replays it (needs
+ * a non-default stream); BICADMM_BATCH_PROFILE times each launch (not with GRAPH);
+ * BICADMM_BATCH_AUTOTUNE spends the first iterations timing each
+ * tiling that fits — shared-memory stage size (16..64 KB; each instance's panels take as
+ * many rows, at most 8, as fit in a stage) and stage count (2..4) — 2 iterations each
+ * (ordinary iterations of every instance), and keeps the fastest.
+ * stream: cudaStream_t used for all batch work.
+ * bicadmm_batch_step runs n_iters iterations of every instance (does not synchronise) and
+ * writes the batch's kernel-launch count so far to *launches_out when non-NULL.
+ * bicadmm_batch_tiling reports the stage size in KB and the stage count in use.  Errors with a NULL batch
+ * are described by bicadmm_batch_last_error(NULL). */
+typedef struct bicadmm_batch_ctx* bicadmm_batch_t;
+enum { BICADMM_BATCH_GRAPH = 1, BICADMM_BATCH_AUTOTUNE = 2, BICADMM_BATCH_PROFILE = 4 };
+int bicadmm_batch_create(bicadmm_t* handles, int32_t count, void* stream, int32_t flags,
+                         bicadmm_batch_t* out);
+int bicadmm_batch_step(bicadmm_batch_t b, int32_t n_iters, int64_t* launches_out);
+int bicadmm_batch_tiling(bicadmm_batch_t b, int32_t* stage_kb_out, int32_t* stages_out);
+/* With BICADMM_BATCH_PROFILE (eager launches only) every batched launch is bracketed by CUDA
+ * events; this synchronises and writes per kernel kind (0 pass, 1 x-update, 2 dual,
+ * 3 consensus) the summed ms and launch counts since the last call, then clears them. */
+int bicadmm_batch_kernel_times(bicadmm_batch_t b, double* ms_out, int64_t* launches_out);
+int bicadmm_batch_destroy(bicadmm_batch_t b);
+const char* bicadmm_batch_last_error(bicadmm_batch_t b);
+
 /* Free every device buffer of the handle (synchronises its stream).  NULL is accepted. */
 int bicadmm_destroy(bicadmm_t h);
 

@@ -80,6 +80,15 @@ SIGNATURES = [
     ("bicadmm_consensus_step_noalloc", ctypes.c_int,
      [_VP, _VP, _VP, _VP, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
       ctypes.c_double, _VP]),
+    ("bicadmm_batch_create", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int32, _VP, ctypes.c_int32,
+                                            ctypes.POINTER(_VP)]),
+    ("bicadmm_batch_step", ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]),
+    ("bicadmm_batch_tiling", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_int32)]),
+    ("bicadmm_batch_kernel_times", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
+                                                  ctypes.POINTER(ctypes.c_int64)]),
+    ("bicadmm_batch_destroy", ctypes.c_int, [_VP]),
+    ("bicadmm_batch_last_error", ctypes.c_char_p, [_VP]),
     ("bicadmm_destroy", ctypes.c_int, [_VP]),
     ("bicadmm_last_error", ctypes.c_char_p, [_VP]),
 ]
@@ -235,6 +244,52 @@ def consensus_step_noalloc(w, z, s, tvt, kappa, N_shards, rho_c, rho_b, stream=N
     _check(lib().bicadmm_consensus_step_noalloc(w.data_ptr(), z.data_ptr(), s.data_ptr(),
                                                 tvt.data_ptr(), n, int(kappa), int(N_shards),
                                                 float(rho_c), float(rho_b), _VP(stream or 0)))
+
+
+BATCH_GRAPH, BATCH_AUTOTUNE, BATCH_PROFILE = 1, 2, 4
+
+
+def _bcheck(code, b=None):
+    if code != 0:
+        msg = lib().bicadmm_batch_last_error(b)
+        raise BicadmmError(code, msg.decode() if msg else "")
+
+
+def batch_create(handles, stream=None, flags=0):
+    """Batch over set-up handles (raw handles or Solver objects)."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    hs = [getattr(h, "h", h) for h in handles]
+    arr = (_VP * len(hs))(*[h.value if hasattr(h, "value") else h for h in hs])
+    b = _VP()
+    _bcheck(lib().bicadmm_batch_create(arr, len(hs), _VP(stream or 0), int(flags), ctypes.byref(b)))
+    return b
+
+
+def batch_step(b, n_iters):
+    cnt = ctypes.c_int64()
+    _bcheck(lib().bicadmm_batch_step(b, int(n_iters), ctypes.byref(cnt)), b)
+    return cnt.value
+
+
+def batch_tiling(b):
+    r = ctypes.c_int32()
+    st = ctypes.c_int32()
+    _bcheck(lib().bicadmm_batch_tiling(b, ctypes.byref(r), ctypes.byref(st)), b)
+    return r.value, st.value
+
+
+def batch_kernel_times(b):
+    """{kind: (ms, launches)} since the last call (needs BATCH_PROFILE)."""
+    ms = (ctypes.c_double * 4)()
+    cnt = (ctypes.c_int64 * 4)()
+    _bcheck(lib().bicadmm_batch_kernel_times(b, ms, cnt), b)
+    return {k: (ms[i], cnt[i]) for i, k in enumerate(("pass", "xupd", "dual", "consensus"))}
+
+
+def batch_destroy(b):
+    if b:
+        _bcheck(lib().bicadmm_batch_destroy(b))
 
 
 def destroy(h):

@@ -1,0 +1,439 @@
+// Batched execution: many independent Bi-cADMM instances advanced together, one launch per
+// kernel kind per outer iteration.  Every instance keeps its own buffers (those of its
+// handle); the batch adds device tables that describe them.
+//
+// The pass runs over a global panel list: the rows of every (instance, shard) pair form a
+// "segment", segments are laid end to end, and each persistent CTA takes a contiguous range
+// of panels exactly as the single-instance pass does over shards.  Crossing a segment
+// boundary reloads x, flushes the A'd accumulators to the instance's slot
+// (cta - first CTA of the instance) + shard, and, crossing an instance boundary, flushes the
+// inner-residual sums.  The instance's slot ranges for this partition are kept by the batch
+// so the dual kernel sums the right slots.
+#pragma once
+
+#include "common.cuh"
+#include "nspace.cuh"
+#include "pass.cuh"
+
+namespace bic {
+
+// Per-instance constants and pointers used by the batched kernels.
+struct BatchInst {
+  // pass
+  const void* A;
+  int64_t lda;
+  const void* xlo;
+  const void* b;
+  void* omega;
+  void* nu;
+  void* slots;
+  double* cta_stats;
+  int c_lo;          // first panel CTA of the batch partition touching this instance
+  int G_inst;        // panel CTAs touching it
+  int loss, newton_iters;
+  double M, rho_l;
+  // x-update and dual
+  const void* P;
+  const int64_t* P_off;
+  const int* blk_col0;
+  const int* blk_ldp;
+  int M_blocks, N;
+  double* x;
+  double* u;
+  double* r;
+  const double* z;
+  double rho_c, c0;
+  const int* slot_lo;  // per shard, for this batch partition
+  const int* slot_hi;
+  double* dual_part;
+  int dual_chunks;
+  int64_t n;
+  GlobalState* gs;
+  Resid* trace;
+  int* err;
+};
+
+// One segment: the rows of shard `shard` of instance `inst`, cut into panels of `rpp` rows
+// (rpp * row bytes <= the stage size, rpp <= R of the kernel).
+struct BatchSeg {
+  int inst, shard;
+  int64_t first_panel;  // global index of its first panel
+  int64_t row0;         // first row within the instance
+  int64_t rows;
+  int rpp;
+  int pad;
+};
+
+template <typename TA, typename TM, int R, int VPT, int NT>
+__global__ void __launch_bounds__(NT, 1)
+k_fused_pass_batch(const BatchInst* __restrict__ inst, const BatchSeg* __restrict__ seg, int nseg,
+                   int64_t P, int S, size_t stage_bytes, long long wait_limit) {
+  using V = typename Vec16<TA>::type;
+  constexpr int VE = Vec16<TA>::n;
+  constexpr int NW = NT / 32;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c = blockIdx.x, G = gridDim.x;
+  const int64_t p_begin = static_cast<int64_t>(c) * P / G;
+  const int64_t p_end = static_cast<int64_t>(c + 1) * P / G;
+  const int64_t np = p_end - p_begin;
+
+  // layout: S stages of stage_bytes | S mbarriers | red[R][NW] | d[R]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + S * stage_bytes);
+  TM* red = reinterpret_cast<TM*>(bars + S);
+  TM* d_s = red + R * NW;
+
+  if (tid == 0) {
+    for (int st = 0; st < S; ++st) mbar_init(&bars[st], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+
+  auto locate = [&](int64_t p, int& s, int64_t& row0, int& nrows) {
+    while (s + 1 < nseg && seg[s + 1].first_panel <= p) ++s;
+    const BatchSeg& g = seg[s];
+    row0 = g.row0 + (p - g.first_panel) * g.rpp;
+    const int64_t rem = g.row0 + g.rows - row0;
+    nrows = rem < g.rpp ? static_cast<int>(rem) : g.rpp;
+  };
+
+  // segment holding this CTA's first panel (binary search; later lookups walk forward)
+  int seg0 = 0;
+  {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (seg[mid].first_panel <= p_begin) lo = mid; else hi = mid - 1;
+    }
+    seg0 = lo;
+  }
+
+  int64_t n_issued = 0;
+  int issue_seg = seg0;
+  auto issue = [&](int64_t k) {
+    int64_t row0;
+    int nrows;
+    locate(p_begin + k, issue_seg, row0, nrows);
+    const BatchInst& I = inst[seg[issue_seg].inst];
+    const int st = static_cast<int>(k % S);
+    const uint32_t bytes = static_cast<uint32_t>(nrows * I.lda * sizeof(TA));
+    mbar_arrive_expect_tx(&bars[st], bytes);
+    bulk_copy_g2s(smem_raw + st * stage_bytes, static_cast<const TA*>(I.A) + row0 * I.lda, bytes,
+                  &bars[st]);
+  };
+  if (tid == 0) {
+    for (; n_issued < np && n_issued < S; ++n_issued) issue(n_issued);
+  }
+
+  TA xr[VPT][VE];
+  TM acc[VPT][VE];
+  int cur_seg = -1, cur_inst = -1, sidx = seg0;
+  int64_t nvec = 0, lda = 0;
+  int loss = 0, newton_iters = 0;
+  TM Mf = TM(1), rho_l = TM(1);
+  TM st_res = TM(0), st_om = TM(0), st_ax = TM(0);
+
+  auto flush_acc = [&](int s) {
+    const BatchSeg& g = seg[s];
+    const BatchInst& I = inst[g.inst];
+    TM* dst = static_cast<TM*>(I.slots) + static_cast<int64_t>(c - I.c_lo + g.shard) * I.lda;
+#pragma unroll
+    for (int kk = 0; kk < VPT; ++kk) {
+      const int64_t v = tid + static_cast<int64_t>(kk) * NT;
+      if (v < nvec) {
+#pragma unroll
+        for (int e = 0; e < VE; ++e) dst[v * VE + e] = acc[kk][e];
+      }
+    }
+  };
+  auto flush_stats = [&](int ii) {
+    if (warp == 0) {
+      const TM a0 = warp_sum(st_res), a1 = warp_sum(st_om), a2 = warp_sum(st_ax);
+      if (lane == 0) {
+        const BatchInst& I = inst[ii];
+        double* cs = I.cta_stats + (c - I.c_lo) * 4;
+        cs[0] = static_cast<double>(a0);
+        cs[1] = static_cast<double>(a1);
+        cs[2] = static_cast<double>(a2);
+        cs[3] = 0.0;
+      }
+    }
+    st_res = st_om = st_ax = TM(0);
+  };
+
+  for (int64_t k = 0; k < np; ++k) {
+    int64_t row0;
+    int nrows;
+    locate(p_begin + k, sidx, row0, nrows);
+    if (sidx != cur_seg) {
+      if (cur_seg >= 0) flush_acc(cur_seg);
+      const int ni = seg[sidx].inst;
+      if (ni != cur_inst) {
+        if (cur_inst >= 0) flush_stats(cur_inst);
+        const BatchInst& I = inst[ni];
+        lda = I.lda;
+        nvec = lda / VE;
+        loss = I.loss;
+        newton_iters = I.newton_iters;
+        Mf = static_cast<TM>(I.M);
+        rho_l = static_cast<TM>(I.rho_l);
+        cur_inst = ni;
+      }
+      cur_seg = sidx;
+      const V* xv = reinterpret_cast<const V*>(static_cast<const TA*>(inst[ni].xlo) +
+                                               static_cast<int64_t>(seg[sidx].shard) * lda);
+#pragma unroll
+      for (int kk = 0; kk < VPT; ++kk) {
+        const int64_t v = tid + static_cast<int64_t>(kk) * NT;
+        V t;
+        if (v < nvec) t = xv[v]; else t = V{};
+        const TA* te = reinterpret_cast<const TA*>(&t);
+#pragma unroll
+        for (int e = 0; e < VE; ++e) { xr[kk][e] = te[e]; acc[kk][e] = TM(0); }
+      }
+    }
+    const BatchInst& I = inst[cur_inst];
+    TM b_r = TM(0), nu_r = TM(0), om_r = TM(0);
+    if (warp == 0 && lane < nrows) {
+      b_r = static_cast<const TM*>(I.b)[row0 + lane];
+      nu_r = static_cast<const TM*>(I.nu)[row0 + lane];
+      om_r = static_cast<const TM*>(I.omega)[row0 + lane];
+    }
+    const int st = static_cast<int>(k % S);
+    const uint32_t parity = static_cast<uint32_t>((k / S) & 1);
+    const bool ok = mbar_wait_bounded(&bars[st], parity, wait_limit);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        set_err(I.err, DEV_TIMEOUT_PASS);
+        for (int64_t q = k; q < n_issued; ++q)
+          mbar_wait_bounded(&bars[q % S], static_cast<uint32_t>((q / S) & 1), wait_limit);
+      }
+      return;
+    }
+    const V* sv = reinterpret_cast<const V*>(smem_raw + st * stage_bytes);
+
+    TM dot[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) dot[r] = TM(0);
+#pragma unroll
+    for (int kk = 0; kk < VPT; ++kk) {
+      const int64_t v = tid + static_cast<int64_t>(kk) * NT;
+      if (v < nvec) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if (r < nrows) {
+            const V a = sv[r * nvec + v];
+            const TA* ae = reinterpret_cast<const TA*>(&a);
+#pragma unroll
+            for (int e = 0; e < VE; ++e) dot[r] = fma(TM(ae[e]), TM(xr[kk][e]), dot[r]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) dot[r] = warp_sum(dot[r]);
+    if (lane == 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) red[r * NW + warp] = dot[r];
+    }
+    __syncthreads();
+
+    if (warp == 0) {
+      TM tot = TM(0);
+#pragma unroll
+      for (int base = 0; base < R * NW; base += 32) {
+        TM pv = base + lane < R * NW ? red[base + lane] : TM(0);
+#pragma unroll
+        for (int off = NW / 2; off > 0; off >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, off);
+#pragma unroll
+        for (int rr = 0; rr < 32 / NW; ++rr) {
+          const TM t = __shfl_sync(0xffffffffu, pv, rr * NW);
+          if (lane == base / NW + rr) tot = t;
+        }
+      }
+      if (lane < nrows) {
+        const TM Axb = tot / Mf;
+        const TM om = omega_prox<TM>(loss, Axb + nu_r, b_r, Mf, rho_l, newton_iters, om_r);
+        const TM nun = nu_r + Axb - om;
+        static_cast<TM*>(I.omega)[row0 + lane] = om;
+        static_cast<TM*>(I.nu)[row0 + lane] = nun;
+        d_s[lane] = om - Axb - nun;
+        const TM rr = Axb - om;
+        st_res = fma(rr, rr, st_res);
+        st_om = fma(om, om, st_om);
+        st_ax = fma(Axb, Axb, st_ax);
+      }
+    }
+    __syncthreads();
+
+    TM dr[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) dr[r] = r < nrows ? d_s[r] : TM(0);
+#pragma unroll
+    for (int kk = 0; kk < VPT; ++kk) {
+      const int64_t v = tid + static_cast<int64_t>(kk) * NT;
+      if (v < nvec) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if (r < nrows) {
+            const V a = sv[r * nvec + v];
+            const TA* ae = reinterpret_cast<const TA*>(&a);
+#pragma unroll
+            for (int e = 0; e < VE; ++e) acc[kk][e] = fma(dr[r], TM(ae[e]), acc[kk][e]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && n_issued < np) {
+      issue(n_issued);
+      ++n_issued;
+    }
+  }
+  if (cur_seg >= 0) flush_acc(cur_seg);
+  if (cur_inst >= 0) flush_stats(cur_inst);
+}
+
+// x-update over a flattened list of (instance, shard, block, row tile) items.
+struct XItem {
+  int inst, shard, block, row_begin;
+};
+
+template <typename TP, int XT, int ROWS>
+__global__ void __launch_bounds__(XT)
+k_xupd_batch(const BatchInst* __restrict__ inst, const XItem* __restrict__ items) {
+  using V = typename PVec<TP>::type;
+  constexpr int VE = PVec<TP>::n;
+  extern __shared__ __align__(16) unsigned char xs_raw[];
+  TP* rs = reinterpret_cast<TP*>(xs_raw);
+  const XItem it = items[blockIdx.x];
+  const BatchInst& I = inst[it.inst];
+  const int i = it.shard, j = it.block;
+  const int col0 = I.blk_col0[j], nj = I.blk_col0[j + 1] - col0, ldp = I.blk_ldp[j];
+  const int64_t lda = I.lda;
+  for (int k = threadIdx.x; k < ldp; k += XT)
+    rs[k] = k < nj ? static_cast<TP>(I.r[i * lda + col0 + k]) : TP(0);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const TP* Pb = static_cast<const TP*>(I.P) + I.P_off[i * I.M_blocks + j];
+  const V* rv = reinterpret_cast<const V*>(rs);
+  const int nv = ldp / VE;
+  constexpr int U = 8;
+  for (int row = it.row_begin + warp; row < it.row_begin + ROWS && row < nj; row += XT / 32) {
+    const V* pr = reinterpret_cast<const V*>(Pb + static_cast<int64_t>(row) * ldp);
+    TP acc = TP(0);
+    for (int k0 = 0; k0 < nv; k0 += 32 * U) {
+      V a[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int k = k0 + q * 32 + lane;
+        if (k < nv) a[q] = pr[k]; else a[q] = V{};
+      }
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int k = k0 + q * 32 + lane;
+        if (k < nv) {
+          const V bb = rv[k];
+          const TP* ae = reinterpret_cast<const TP*>(&a[q]);
+          const TP* be = reinterpret_cast<const TP*>(&bb);
+#pragma unroll
+          for (int e = 0; e < VE; ++e) acc = fma(ae[e], be[e], acc);
+        }
+      }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      const int64_t o = i * lda + col0 + row;
+      const double xn = I.x[o] + static_cast<double>(acc);
+      I.x[o] = xn;
+      static_cast<TP*>(const_cast<void*>(I.xlo))[o] = static_cast<TP>(xn);
+    }
+  }
+}
+
+// Consensus step, one CTA per instance.
+template <int GT, int MW>
+__global__ void __launch_bounds__(GT, 1) k_global_batch(const ConsensusArgs* __restrict__ args) {
+  consensus_block<GT, MW>(args[blockIdx.x]);
+}
+
+// Dual update + next right-hand side over a flattened list of (instance, shard, chunk)
+// items; per instance the last CTA reduces its residual record.
+struct DItem {
+  int inst, shard, chunk;
+};
+
+template <typename TM, int DT>
+__global__ void __launch_bounds__(DT)
+k_dual_batch(const BatchInst* __restrict__ inst, const DItem* __restrict__ items) {
+  __shared__ double red[32 * 2];
+  __shared__ bool last;
+  const DItem it = items[blockIdx.x];
+  const BatchInst& I = inst[it.inst];
+  const int i = it.shard, nch = I.dual_chunks, N = I.N;
+  const int64_t lda = I.lda, n = I.n;
+  const int64_t col = static_cast<int64_t>(it.chunk) * DT + threadIdx.x;
+  double a[2] = {0.0, 0.0};
+  if (col < lda) {
+    const int64_t o = i * lda + col;
+    const double xv = I.x[o], zv = I.z[col], dv = xv - zv;
+    const double un = I.u[o] + dv;
+    I.u[o] = un;
+    TM q = TM(0);
+    const TM* slots = static_cast<const TM*>(I.slots);
+    for (int sl = I.slot_lo[i]; sl <= I.slot_hi[i]; ++sl) q += slots[sl * lda + col];
+    I.r[o] = I.rho_l * static_cast<double>(q) + I.rho_c * (zv - un) - I.c0 * xv;
+    a[0] = dv * dv;
+    a[1] = xv * xv;
+  }
+  block_sum<2>(a, red);
+  if (threadIdx.x == 0) {
+    I.dual_part[(static_cast<int64_t>(i) * nch + it.chunk) * 2 + 0] = a[0];
+    I.dual_part[(static_cast<int64_t>(i) * nch + it.chunk) * 2 + 1] = a[1];
+    __threadfence();
+    last = atomicAdd(&I.gs->ticket, 1u) == static_cast<unsigned>(N * nch) - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    double pr = 0.0, nx = 0.0;
+    for (int ii = lane; ii < N; ii += 32) {
+      double s0 = 0.0, s1 = 0.0;
+      for (int cidx = 0; cidx < nch; ++cidx) {
+        s0 += I.dual_part[(static_cast<int64_t>(ii) * nch + cidx) * 2 + 0];
+        s1 += I.dual_part[(static_cast<int64_t>(ii) * nch + cidx) * 2 + 1];
+      }
+      pr += sqrt(s0);
+      nx += sqrt(s1);
+    }
+    pr = warp_sum(pr);
+    nx = warp_sum(nx);
+    double q0 = 0.0, q1 = 0.0, q2 = 0.0;
+    for (int g = lane; g < I.G_inst; g += 32) {
+      q0 += I.cta_stats[g * 4 + 0];
+      q1 += I.cta_stats[g * 4 + 1];
+      q2 += I.cta_stats[g * 4 + 2];
+    }
+    q0 = warp_sum(q0);
+    q1 = warp_sum(q1);
+    q2 = warp_sum(q2);
+    if (lane == 0) {
+      GlobalState* gs = I.gs;
+      Resid& rec = I.trace[gs->iter % kTraceCapacity];
+      rec.p_r = pr;
+      rec.p_rel = pr / fmax(fmax(nx, N * rec.znorm), 1e-30);
+      rec.i_r = sqrt(q0);
+      rec.i_rel = sqrt(q0) / fmax(fmax(sqrt(q1), sqrt(q2)), 1e-30);
+      const double chk = rec.p_r + rec.d_r + rec.b_r + rec.i_r + rec.t + rec.v;
+      if (!isfinite(chk)) set_err(I.err, DEV_NONFINITE);
+      gs->iter += 1;
+      gs->ticket = 0;
+    }
+  }
+  (void)n;
+}
+
+}  // namespace bic

@@ -21,6 +21,7 @@
 #include "bicadmm.h"
 #include "common.cuh"
 #include "nspace.cuh"
+#include "batch.cuh"
 #include "pass.cuh"
 #include "polish.cuh"
 #include "setup.cuh"
@@ -34,7 +35,7 @@ constexpr int kDualThreads = 256;
 constexpr int kXupdThreads = 256;
 constexpr int kXupdRows = 32;
 constexpr int kCholThreads = 256;
-constexpr int kTraceCap = 4096;
+constexpr int kTraceCap = kTraceCapacity;
 constexpr int64_t kMaxN = 32768;                 // single-CTA global step limit
 constexpr size_t kPassSmemBudget = 200 * 1024;   // dynamic smem for A-pass stages
 constexpr size_t kPassCtaTarget = 100 * 1024;    // auto sizing aims at two CTAs per SM
@@ -733,6 +734,289 @@ int run_polish(bicadmm_ctx* h, std::vector<double>& xs_out) {
 
 }  // namespace
 
+// ============================================================================ batches
+
+struct bicadmm_batch_ctx {
+  std::vector<bicadmm_t> hs;
+  cudaStream_t stream = nullptr;
+  int esz = 8;
+  int R = 0, S = 0, VPT = 0, G = 0, nseg = 0, n_xitems = 0, n_ditems = 0, max_ldp = 0;
+  int stage_kb = 0;
+  int64_t P = 0;
+  size_t stage_bytes = 0, smem = 0;
+  std::vector<void*> allocs;       // batch-owned device memory (tables, slots, stats)
+  std::vector<void*> table_allocs; // tables rebuilt on retiling
+  BatchInst* d_inst = nullptr;
+  BatchSeg* d_seg = nullptr;
+  XItem* d_xitems = nullptr;
+  DItem* d_ditems = nullptr;
+  ConsensusArgs* d_cons = nullptr;
+  std::vector<std::pair<int, int>> candidates;  // (R, S) tilings still to try
+  std::vector<std::pair<double, std::pair<int, int>>> timings;
+  int tune_iters = 0;
+  bool use_graph = false;
+  bool profile = false;                 // events around each kernel kind (eager launches)
+  std::vector<cudaEvent_t> ev;          // pairs
+  std::vector<int> ev_kind;
+  double kind_ms[4] = {0, 0, 0, 0};
+  int64_t kind_n[4] = {0, 0, 0, 0};
+  cudaGraphExec_t graph = nullptr;
+  int64_t launches = 0, iters = 0;
+  std::string err;
+};
+
+namespace {
+
+int bfail(bicadmm_batch_ctx* b, int code, const std::string& msg) {
+  if (b) b->err = msg;
+  return code;
+}
+
+#define BCK(call)                                                                                 \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess)                                                                        \
+      return bfail(b, BICADMM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));      \
+  } while (0)
+
+template <typename T>
+int bdev_alloc(bicadmm_batch_ctx* b, T** ptr, size_t bytes, bool table) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return bfail(b, BICADMM_ERR_OOM, "batch allocation failed");
+  }
+  (table ? b->table_allocs : b->allocs).push_back(p);
+  *ptr = static_cast<T*>(p);
+  return BICADMM_OK;
+}
+
+template <typename TA, typename TM, int R, int VPT>
+int launch_pass_batch_rv(bicadmm_batch_ctx* b) {
+  auto kern = k_fused_pass_batch<TA, TM, R, VPT, kPassThreads>;
+  BCK(allow_max_dynamic_smem(kern));
+  kern<<<b->G, kPassThreads, b->smem, b->stream>>>(b->d_inst, b->d_seg, b->nseg, b->P, b->S,
+                                                   b->stage_bytes, kWaitLimitCycles);
+  BCK(cudaGetLastError());
+  return BICADMM_OK;
+}
+
+template <typename TA, typename TM, int R, int VPT>
+int occupancy_batch_rv(bicadmm_batch_ctx* b, int* blocks) {
+  auto kern = k_fused_pass_batch<TA, TM, R, VPT, kPassThreads>;
+  BCK(allow_max_dynamic_smem(kern));
+  BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, kPassThreads, b->smem));
+  return BICADMM_OK;
+}
+
+// dispatch on (R, VPT); op 0 = launch, 1 = occupancy
+template <typename TA, typename TM>
+int batch_pass_dispatch(bicadmm_batch_ctx* b, int op, int* blocks) {
+#define BP_CASE(RR, VV)                                                                \
+  if (b->R == RR && b->VPT == VV)                                                      \
+    return op == 0 ? launch_pass_batch_rv<TA, TM, RR, VV>(b) : occupancy_batch_rv<TA, TM, RR, VV>(b, blocks);
+#define BP_R(RR) BP_CASE(RR, 1) BP_CASE(RR, 2) BP_CASE(RR, 3) BP_CASE(RR, 4) BP_CASE(RR, 5) \
+  BP_CASE(RR, 6) BP_CASE(RR, 8) BP_CASE(RR, 12) BP_CASE(RR, 16)
+  BP_R(8)
+#undef BP_R
+#undef BP_CASE
+  return bfail(b, BICADMM_ERR_UNSUPPORTED, "no batched A-pass variant for this tiling");
+}
+
+constexpr int kBatchMaxRows = 8;  // rows per panel at most (the batched kernel's R)
+
+// Build the panel partition and every table for a tiling: stages of `stage_kb` KB, S of
+// them; each instance's panels take as many rows (<= 8) as fit in a stage.
+int batch_build(bicadmm_batch_ctx* b, int stage_kb, int S) {
+  for (void* p : b->table_allocs) cudaFree(p);
+  b->table_allocs.clear();
+  const int B = static_cast<int>(b->hs.size());
+  int64_t max_lda = 0;
+  int max_ldp = 0;
+  for (bicadmm_t h : b->hs) {
+    max_lda = std::max(max_lda, h->lda);
+    max_ldp = std::max(max_ldp, h->max_ldp);
+  }
+  const int R = kBatchMaxRows;
+  b->R = R;
+  b->stage_kb = stage_kb;
+  b->S = S;
+  b->max_ldp = max_ldp;
+  b->stage_bytes = static_cast<size_t>(stage_kb) * 1024;
+  if (b->stage_bytes < static_cast<size_t>(max_lda) * b->esz)
+    return bfail(b, BICADMM_ERR_UNSUPPORTED, "stage smaller than the widest row");
+  b->smem = S * b->stage_bytes + S * sizeof(uint64_t) +
+            static_cast<size_t>(R) * (kPassThreads / 32 + 1) * b->esz + 16;
+  b->VPT = pick_vpt(max_lda / (b->esz == 8 ? 2 : 4));
+  if (b->VPT < 0) return bfail(b, BICADMM_ERR_UNSUPPORTED, "instance rows too wide for the batched pass");
+  // segments
+  std::vector<BatchSeg> seg;
+  int64_t P = 0;
+  for (int q = 0; q < B; ++q) {
+    bicadmm_t h = b->hs[q];
+    const int rpp = static_cast<int>(std::min<int64_t>(
+        R, static_cast<int64_t>(b->stage_bytes / (static_cast<size_t>(h->lda) * b->esz))));
+    for (int i = 0; i < h->N; ++i) {
+      const int64_t rows = h->shard_row0[i + 1] - h->shard_row0[i];
+      seg.push_back(BatchSeg{q, i, P, h->shard_row0[i], rows, rpp, 0});
+      P += (rows + rpp - 1) / rpp;
+    }
+  }
+  b->P = P;
+  b->nseg = static_cast<int>(seg.size());
+  int occ = 0;
+  int rc = b->esz == 8 ? batch_pass_dispatch<double, double>(b, 1, &occ)
+                       : batch_pass_dispatch<float, float>(b, 1, &occ);
+  if (rc != BICADMM_OK) return rc;
+  if (occ < 1) return bfail(b, BICADMM_ERR_UNSUPPORTED, "batched A-pass cannot be resident");
+  b->G = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(occ) * b->hs[0]->num_sms, P));
+  auto owner = [&](int64_t panel) {
+    int64_t c = panel * b->G / P;
+    while (c > 0 && c * P / b->G > panel) --c;
+    while ((c + 1) * P / b->G <= panel) ++c;
+    return static_cast<int>(c);
+  };
+  // per-instance tables
+  std::vector<BatchInst> inst(B);
+  std::vector<ConsensusArgs> cons(B);
+  std::vector<XItem> xitems;
+  std::vector<DItem> ditems;
+  size_t si = 0;
+  for (int q = 0; q < B; ++q) {
+    bicadmm_t h = b->hs[q];
+    const BatchSeg& s0 = seg[si];
+    const BatchSeg& s1 = seg[si + h->N - 1];
+    const int c_lo = owner(s0.first_panel);
+    const int c_hi = owner(s1.first_panel + (s1.rows + s1.rpp - 1) / s1.rpp - 1);
+    std::vector<int> lo(h->N), hi(h->N);
+    for (int i = 0; i < h->N; ++i) {
+      const BatchSeg& g = seg[si + i];
+      lo[i] = owner(g.first_panel) - c_lo + i;
+      hi[i] = owner(g.first_panel + (g.rows + g.rpp - 1) / g.rpp - 1) - c_lo + i;
+    }
+    si += h->N;
+    const int G_inst = c_hi - c_lo + 1;
+    void* slots = nullptr;
+    double* stats = nullptr;
+    int* d_lo = nullptr;
+    int* d_hi = nullptr;
+    if ((rc = bdev_alloc(b, &slots, static_cast<size_t>(G_inst + h->N) * h->lda * b->esz, true)) != BICADMM_OK) return rc;
+    if ((rc = bdev_alloc(b, &stats, static_cast<size_t>(G_inst) * 4 * sizeof(double), true)) != BICADMM_OK) return rc;
+    if ((rc = bdev_alloc(b, &d_lo, h->N * sizeof(int), true)) != BICADMM_OK) return rc;
+    if ((rc = bdev_alloc(b, &d_hi, h->N * sizeof(int), true)) != BICADMM_OK) return rc;
+    BCK(cudaMemcpyAsync(d_lo, lo.data(), h->N * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaMemcpyAsync(d_hi, hi.data(), h->N * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    BatchInst& I = inst[q];
+    I.A = h->A; I.lda = h->lda; I.xlo = h->xlo; I.b = h->b; I.omega = h->omega; I.nu = h->nu;
+    I.slots = slots; I.cta_stats = stats; I.c_lo = c_lo; I.G_inst = G_inst;
+    I.loss = h->p.loss; I.newton_iters = h->p.newton_iters; I.M = h->M; I.rho_l = h->p.rho_l;
+    I.P = h->Pm; I.P_off = h->d_P_off; I.blk_col0 = h->d_blk_col0; I.blk_ldp = h->d_blk_ldp;
+    I.M_blocks = h->M; I.N = h->N; I.x = h->x; I.u = h->u; I.r = h->r; I.z = h->z;
+    I.rho_c = h->p.rho_c; I.c0 = h->c0; I.slot_lo = d_lo; I.slot_hi = d_hi;
+    I.dual_part = h->dual_part; I.dual_chunks = h->dual_chunks; I.n = h->p.n; I.gs = h->gs;
+    I.trace = h->trace; I.err = h->d_err;
+    cons[q] = consensus_args(h, true);
+    for (int i = 0; i < h->N; ++i)
+      for (int j = 0; j < h->M; ++j) {
+        const int nj = h->blk_col0[j + 1] - h->blk_col0[j];
+        for (int r0 = 0; r0 < nj; r0 += kXupdRows) xitems.push_back(XItem{q, i, j, r0});
+      }
+    for (int i = 0; i < h->N; ++i)
+      for (int cidx = 0; cidx < h->dual_chunks; ++cidx) ditems.push_back(DItem{q, i, cidx});
+  }
+  b->n_xitems = static_cast<int>(xitems.size());
+  b->n_ditems = static_cast<int>(ditems.size());
+  if ((rc = bdev_alloc(b, &b->d_inst, B * sizeof(BatchInst), true)) != BICADMM_OK) return rc;
+  if ((rc = bdev_alloc(b, &b->d_seg, seg.size() * sizeof(BatchSeg), true)) != BICADMM_OK) return rc;
+  if ((rc = bdev_alloc(b, &b->d_xitems, xitems.size() * sizeof(XItem), true)) != BICADMM_OK) return rc;
+  if ((rc = bdev_alloc(b, &b->d_ditems, ditems.size() * sizeof(DItem), true)) != BICADMM_OK) return rc;
+  if ((rc = bdev_alloc(b, &b->d_cons, B * sizeof(ConsensusArgs), true)) != BICADMM_OK) return rc;
+  BCK(cudaMemcpyAsync(b->d_inst, inst.data(), B * sizeof(BatchInst), cudaMemcpyHostToDevice, b->stream));
+  BCK(cudaMemcpyAsync(b->d_seg, seg.data(), seg.size() * sizeof(BatchSeg), cudaMemcpyHostToDevice, b->stream));
+  BCK(cudaMemcpyAsync(b->d_xitems, xitems.data(), xitems.size() * sizeof(XItem), cudaMemcpyHostToDevice, b->stream));
+  BCK(cudaMemcpyAsync(b->d_ditems, ditems.data(), ditems.size() * sizeof(DItem), cudaMemcpyHostToDevice, b->stream));
+  BCK(cudaMemcpyAsync(b->d_cons, cons.data(), B * sizeof(ConsensusArgs), cudaMemcpyHostToDevice, b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  return BICADMM_OK;
+}
+
+int bprof(bicadmm_batch_ctx* b, int kind, bool end) {
+  if (!b->profile) return BICADMM_OK;
+  if (!end) {
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    b->ev.push_back(e0);
+    b->ev.push_back(e1);
+    b->ev_kind.push_back(kind);
+    BCK(cudaEventRecord(e0, b->stream));
+  } else {
+    BCK(cudaEventRecord(b->ev.back(), b->stream));
+  }
+  return BICADMM_OK;
+}
+
+// One outer iteration of every instance: 4 launches (kinds: 1 x-update, 0 pass,
+// 3 consensus, 2 dual).
+template <typename TM>
+int batch_iteration(bicadmm_batch_ctx* b) {
+  int rc;
+  auto kx = k_xupd_batch<TM, kXupdThreads, kXupdRows>;
+  const size_t xsm = static_cast<size_t>(b->max_ldp) * sizeof(TM);
+  if (xsm > 48 * 1024) BCK(cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(xsm)));
+  if ((rc = bprof(b, 1, false)) != BICADMM_OK) return rc;
+  kx<<<b->n_xitems, kXupdThreads, xsm, b->stream>>>(b->d_inst, b->d_xitems);
+  BCK(cudaGetLastError());
+  if ((rc = bprof(b, 1, true)) != BICADMM_OK) return rc;
+  if ((rc = bprof(b, 0, false)) != BICADMM_OK) return rc;
+  rc = b->esz == 8 ? batch_pass_dispatch<double, double>(b, 0, nullptr)
+                   : batch_pass_dispatch<float, float>(b, 0, nullptr);
+  if (rc != BICADMM_OK) return rc;
+  if ((rc = bprof(b, 0, true)) != BICADMM_OK) return rc;
+  if ((rc = bprof(b, 3, false)) != BICADMM_OK) return rc;
+  k_global_batch<512, 2><<<static_cast<unsigned>(b->hs.size()), 512, 0, b->stream>>>(b->d_cons);
+  if ((rc = bprof(b, 3, true)) != BICADMM_OK) return rc;
+  if ((rc = bprof(b, 2, false)) != BICADMM_OK) return rc;
+  k_dual_batch<TM, kDualThreads><<<b->n_ditems, kDualThreads, 0, b->stream>>>(b->d_inst, b->d_ditems);
+  BCK(cudaGetLastError());
+  if ((rc = bprof(b, 2, true)) != BICADMM_OK) return rc;
+  b->launches += 4;
+  return BICADMM_OK;
+}
+
+int batch_run(bicadmm_batch_ctx* b, int n) {
+  for (int it = 0; it < n; ++it) {
+    int rc = b->esz == 8 ? batch_iteration<double>(b) : batch_iteration<float>(b);
+    if (rc != BICADMM_OK) return rc;
+  }
+  return BICADMM_OK;
+}
+
+int batch_capture(bicadmm_batch_ctx* b) {
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  if (!b->use_graph) return BICADMM_OK;
+  // attributes are set by an eager launch before capture
+  cudaGraph_t g = nullptr;
+  BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  const int64_t before = b->launches;
+  int rc = b->esz == 8 ? batch_iteration<double>(b) : batch_iteration<float>(b);
+  cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+  b->launches = before;
+  if (rc != BICADMM_OK) return rc;
+  if (e != cudaSuccess) return bfail(b, BICADMM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return bfail(b, BICADMM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  return BICADMM_OK;
+}
+
+}  // namespace
+
 // =============================================================================== C ABI
 
 extern "C" {
@@ -988,6 +1272,156 @@ int bicadmm_get_pass_time(bicadmm_t h, double* ms_out, int64_t* launches_out) {
   if (ms_out) *ms_out = ms[KIND_PASS];
   if (launches_out) *launches_out = cnt[KIND_PASS];
   return BICADMM_OK;
+}
+
+int bicadmm_batch_create(bicadmm_t* handles, int32_t count, void* stream, int32_t flags,
+                         bicadmm_batch_t* out) {
+  g_create_error.clear();
+  if (!out || !handles || count < 1) { g_create_error = "handles, count >= 1 and out are required"; return BICADMM_ERR_ARG; }
+  *out = nullptr;
+  for (int q = 0; q < count; ++q) {
+    bicadmm_t h = handles[q];
+    if (!h || !h->ready) { g_create_error = "every handle must be set up"; return BICADMM_ERR_STATE; }
+    if (h->esz != handles[0]->esz || h->device != handles[0]->device) { g_create_error = "handles must share precision and device"; return BICADMM_ERR_ARG; }
+    if (h->p.inner_iters != 1) { g_create_error = "batched handles must use inner_iters = 1"; return BICADMM_ERR_UNSUPPORTED; }
+    for (int q2 = 0; q2 < q; ++q2)
+      if (handles[q2] == h) { g_create_error = "a handle appears twice"; return BICADMM_ERR_ARG; }
+  }
+  bicadmm_batch_ctx* b = new bicadmm_batch_ctx();
+  b->hs.assign(handles, handles + count);
+  b->stream = static_cast<cudaStream_t>(stream);
+  b->esz = static_cast<int>(handles[0]->esz);
+  b->use_graph = (flags & BICADMM_BATCH_GRAPH) != 0;
+  b->profile = (flags & BICADMM_BATCH_PROFILE) != 0;
+  if (b->use_graph && b->profile) { g_create_error = "profiling needs eager launches (no graph)"; delete b; return BICADMM_ERR_ARG; }
+  if (b->use_graph && !stream) { g_create_error = "graph capture needs a non-default stream"; delete b; return BICADMM_ERR_ARG; }
+  int64_t max_lda = 0;
+  for (bicadmm_t h : b->hs) max_lda = std::max(max_lda, h->lda);
+  const size_t row_bytes = static_cast<size_t>(max_lda) * b->esz;
+  // tilings (stage KB, S stages) that hold the widest row and fit the shared memory
+  for (int kb : {16, 24, 32, 40, 48, 64})
+    for (int S : {2, 3, 4}) {
+      const size_t st = static_cast<size_t>(kb) * 1024;
+      if (st >= row_bytes && S * st <= kPassSmemBudget) b->candidates.push_back({kb, S});
+    }
+  if (b->candidates.empty()) { g_create_error = "rows too wide for the batched pass"; delete b; return BICADMM_ERR_UNSUPPORTED; }
+  // default: 40 KB stages (or one widest row), two stages: two CTAs per SM
+  const int kb0 = static_cast<int>(std::max<size_t>(40, (row_bytes + 1023) / 1024));
+  const int S0 = 2;
+  if (!(flags & BICADMM_BATCH_AUTOTUNE)) b->candidates.clear();
+  int rc = batch_build(b, kb0, S0);
+  if (rc != BICADMM_OK) {
+    g_create_error = b->err;
+    for (void* p : b->allocs) cudaFree(p);
+    for (void* p : b->table_allocs) cudaFree(p);
+    delete b;
+    return rc;
+  }
+  b->tune_iters = 2;
+  *out = b;
+  return BICADMM_OK;
+}
+
+int bicadmm_batch_step(bicadmm_batch_t b, int32_t n_iters, int64_t* launches_out) {
+  if (!b) return BICADMM_ERR_ARG;
+  if (n_iters < 0) return bfail(b, BICADMM_ERR_ARG, "n_iters must be >= 0");
+  int done = 0;
+  int rc = BICADMM_OK;
+  // Autotuning: the first iterations run each candidate tiling for tune_iters iterations
+  // (each is an ordinary iteration of every instance), timed with CUDA events; the fastest
+  // tiling is kept.
+  while (!b->candidates.empty() && done < n_iters) {
+    const auto cand = b->candidates.back();
+    b->candidates.pop_back();
+    if ((rc = batch_build(b, cand.first, cand.second)) != BICADMM_OK) {
+      if (rc == BICADMM_ERR_UNSUPPORTED) continue;
+      return rc;
+    }
+    const int k = std::min(b->tune_iters, n_iters - done);
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    BCK(cudaEventRecord(e0, b->stream));
+    rc = batch_run(b, k);
+    BCK(cudaEventRecord(e1, b->stream));
+    BCK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    BCK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != BICADMM_OK) return rc;
+    b->timings.push_back({ms / k, cand});
+    done += k;
+    b->iters += k;
+    if (b->candidates.empty()) {
+      auto best = *std::min_element(b->timings.begin(), b->timings.end());
+      if ((rc = batch_build(b, best.second.first, best.second.second)) != BICADMM_OK) return rc;
+    }
+  }
+  if (done < n_iters && b->use_graph && !b->graph) {
+    // one eager iteration sets kernel attributes, then one iteration is captured
+    if ((rc = batch_run(b, 1)) != BICADMM_OK) return rc;
+    ++done;
+    ++b->iters;
+    if ((rc = batch_capture(b)) != BICADMM_OK) return rc;
+  }
+  for (; done < n_iters; ++done) {
+    if (b->graph) {
+      BCK(cudaGraphLaunch(b->graph, b->stream));
+      b->launches += 4;
+    } else if ((rc = batch_run(b, 1)) != BICADMM_OK) {
+      return rc;
+    }
+    ++b->iters;
+  }
+  for (bicadmm_t h : b->hs) h->iters_done += n_iters;
+  if (launches_out) *launches_out = b->launches;
+  return BICADMM_OK;
+}
+
+int bicadmm_batch_tiling(bicadmm_batch_t b, int32_t* rows_out, int32_t* stages_out) {
+  if (!b) return BICADMM_ERR_ARG;
+  if (rows_out) *rows_out = b->stage_kb;
+  if (stages_out) *stages_out = b->S;
+  return BICADMM_OK;
+}
+
+int bicadmm_batch_kernel_times(bicadmm_batch_t b, double* ms_out, int64_t* launches_out) {
+  if (!b) return BICADMM_ERR_ARG;
+  BCK(cudaStreamSynchronize(b->stream));
+  double ms[4] = {0, 0, 0, 0};
+  int64_t cnt[4] = {0, 0, 0, 0};
+  for (size_t q = 0; q + 1 < b->ev.size(); q += 2) {
+    float t = 0.f;
+    BCK(cudaEventElapsedTime(&t, b->ev[q], b->ev[q + 1]));
+    ms[b->ev_kind[q / 2]] += t;
+    cnt[b->ev_kind[q / 2]] += 1;
+  }
+  for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+  b->ev.clear();
+  b->ev_kind.clear();
+  for (int k = 0; k < 4; ++k) {
+    if (ms_out) ms_out[k] = ms[k];
+    if (launches_out) launches_out[k] = cnt[k];
+  }
+  return BICADMM_OK;
+}
+
+int bicadmm_batch_destroy(bicadmm_batch_t b) {
+  if (!b) return BICADMM_OK;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  else cudaDeviceSynchronize();
+  for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (void* p : b->allocs) cudaFree(p);
+  for (void* p : b->table_allocs) cudaFree(p);
+  delete b;
+  return BICADMM_OK;
+}
+
+const char* bicadmm_batch_last_error(bicadmm_batch_t b) {
+  if (!b) return g_create_error.c_str();
+  return b->err.c_str();
 }
 
 int bicadmm_destroy(bicadmm_t h) {

@@ -13,6 +13,9 @@
 
 namespace bic {
 
+// Records kept in a handle's residual trace ring.
+constexpr int kTraceCapacity = 4096;
+
 // Per-iteration residual record (mirrored by the host).
 struct Resid {
   double p_r, d_r, b_r, i_r;

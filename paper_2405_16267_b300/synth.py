@@ -230,6 +230,37 @@ def small_problem(loss: int, m: int, n: int, nnz: int, N: int, M: int, kappa: in
                    gamma, 0)
 
 
+def batch_instance_specs(count=256, seed=0, m_range=(1000, 50000), n_range=(100, 4000),
+                         block_cols=512):
+    """Shapes of a batch of uneven instances: m and n log-uniform in their ranges, kappa
+    uniform in 1..5 % of n (at least 1), N uniform in 4..16 shards (at most m), M such that
+    blocks have at most `block_cols` columns, loss alternating squared / squared hinge."""
+    g = _rng(seed, 7)
+    specs = []
+    for k in range(count):
+        m = int(round(math.exp(g.uniform(math.log(m_range[0]), math.log(m_range[1])))))
+        n = int(round(math.exp(g.uniform(math.log(n_range[0]), math.log(n_range[1])))))
+        kappa = max(1, int(round(n * g.uniform(0.01, 0.05))))
+        N = min(m, int(g.integers(4, 17)))
+        M = max(1, -(-n // block_cols))
+        loss = LOSS_SQUARED if k % 2 == 0 else LOSS_SQHINGE
+        specs.append(dict(m=m, n=n, kappa=kappa, N=N, M=M, loss=loss, seed=seed * 100003 + k))
+    return specs
+
+
+def batch_instance(spec, noise=0.1, dtype=np.float32) -> Problem:
+    """One instance of a batch: A i.i.d. N(0,1), x* +/-U[1,2] on kappa random indices,
+    b = A x* + N(0, noise^2) (squared) or its sign (squared hinge)."""
+    m, n, kappa, seed = spec["m"], spec["n"], spec["kappa"], spec["seed"]
+    A = gaussian_rows(m, n, seed)
+    x_star = planted_support(n, kappa, seed, "pm_uniform12")
+    supp = np.flatnonzero(x_star)
+    lin = A[:, supp] @ x_star[supp] + noise * _noise(m, seed)
+    b = lin if spec["loss"] == LOSS_SQUARED else _sign_pm1(lin)
+    return Problem("batch_%d_%dx%d" % (spec["loss"], m, n), A.astype(dtype), b, x_star,
+                   spec["loss"], spec["N"], spec["M"], kappa, 1.0, 10.0, 0)
+
+
 def round_to_f32(A: np.ndarray) -> np.ndarray:
     """FP32-rounded copy of A upcast back to FP64 (the exact values an FP32 run sees)."""
     return A.astype(np.float32).astype(np.float64)

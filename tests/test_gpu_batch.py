@@ -1,0 +1,125 @@
+"""Batched execution: uneven instances advanced together by one launch per kernel kind per
+iteration must give each instance the iterates it gets alone (same handle API), up to the
+rounding of the regrouped A'd partial sums, and the oracle's iterates."""
+import numpy as np
+import pytest
+
+from oracle import bicadmm_ref as ref
+from paper_2405_16267_b300 import bicadmm as bc
+from paper_2405_16267_b300 import synth
+
+from gpu_util import compare_state, rel_err, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-9
+
+
+def _instances(seed=0):
+    rng = np.random.default_rng(seed)
+    probs = []
+    specs = [(bc.LOSS_SQUARED, 1500, 90, 3, 2, 6), (bc.LOSS_SQHINGE, 2300, 150, 4, 3, 7),
+             (bc.LOSS_LOGISTIC, 900, 61, 2, 2, 4), (bc.LOSS_SQUARED, 4100, 333, 5, 4, 12),
+             (bc.LOSS_SQHINGE, 700, 40, 1, 1, 3), (bc.LOSS_LOGISTIC, 3000, 210, 6, 3, 9)]
+    for k, (loss, m, n, N, M, kappa) in enumerate(specs):
+        probs.append(synth.small_problem(loss, m=m, n=n, nnz=kappa, N=N, M=M, kappa=kappa,
+                                         seed=100 + k + seed))
+    return probs
+
+
+def _solvers(probs, precision=bc.PREC_FP64):
+    import torch
+    out = []
+    for P in probs:
+        A = P.A if precision == bc.PREC_FP64 else P.A.astype(np.float32)
+        out.append(bc.Solver(A, P.b, loss=P.loss, N=P.N, M=P.M, kappa=P.kappa, gamma=P.gamma,
+                             rho_c=P.rho, precision=precision, stream=torch.cuda.current_stream()))
+    return out
+
+
+@pytest.mark.parametrize("flags", [0, 1, 2, 3])
+def test_batch_equals_alone(flags):
+    import torch
+    probs = _instances()
+    iters = 25
+    alone = []
+    for s in _solvers(probs):
+        s.step(iters)
+        alone.append(s.state())
+        s.close()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sol = _solvers(probs)
+        b = bc.batch_create(sol, stream=stream, flags=flags)
+        try:
+            launches = bc.batch_step(b, 10)
+            launches = bc.batch_step(b, iters - 10)
+            rows, stages = bc.batch_tiling(b)
+        finally:
+            stream.synchronize()
+            bc.batch_destroy(b)
+        states = [s.state() for s in sol]
+        for s in sol:
+            s.close()
+    assert 16 <= rows <= 64 and stages >= 2  # stage KB, stage count
+    assert launches == 4 * iters or (flags & 1)  # graph replays count one iteration's 4
+    for st, want, P in zip(states, alone, probs):
+        for k in ("z", "x", "u", "s", "omega", "nu"):
+            assert rel_err(st[k], want[k]) <= TOL64, (P.name, k)
+        assert abs(st["t"] - want["t"]) <= TOL64 * max(1.0, abs(want["t"]))
+        assert list(ref.top_kappa(st["z"], P.kappa)) == list(ref.top_kappa(want["z"], P.kappa))
+
+
+def test_batch_matches_oracle():
+    import torch
+    probs = _instances(seed=7)[:3]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sol = _solvers(probs)
+        b = bc.batch_create(sol, stream=stream, flags=bc.BATCH_GRAPH)
+        bc.batch_step(b, 20)
+        stream.synchronize()
+        bc.batch_destroy(b)
+        states = [s.state() for s in sol]
+        for s in sol:
+            s.close()
+    for st, P in zip(states, probs):
+        o = run_oracle(P, 20)
+        compare_state(st, o, TOL64)
+
+
+def test_batch_fp32_close_to_alone():
+    import torch
+    probs = _instances(seed=3)
+    alone = []
+    for s in _solvers(probs, bc.PREC_FP32):
+        s.step(15)
+        alone.append(s.state())
+        s.close()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sol = _solvers(probs, bc.PREC_FP32)
+        b = bc.batch_create(sol, stream=stream, flags=0)
+        bc.batch_step(b, 15)
+        stream.synchronize()
+        bc.batch_destroy(b)
+        states = [s.state() for s in sol]
+        for s in sol:
+            s.close()
+    for st, want in zip(states, alone):
+        for k in ("z", "x", "omega", "nu"):
+            assert rel_err(st[k], want[k]) <= 1e-4, k
+
+
+def test_batch_rejects_bad_requests():
+    import torch
+    probs = _instances()[:2]
+    sol = _solvers(probs)
+    try:
+        with pytest.raises(bc.BicadmmError):
+            bc.batch_create([sol[0], sol[0]])
+        with pytest.raises(bc.BicadmmError):
+            bc.batch_create(sol, stream=None, flags=bc.BATCH_GRAPH)
+    finally:
+        for s in sol:
+            s.close()
