@@ -396,6 +396,7 @@ def run_time_to_tol(stream, tol=1e-6):
     from paper_2405_16267_b300 import bicadmm as bc
     P = synth.table1_sls(**TABLE1)
     A64 = torch.from_numpy(P.A).cuda()
+    A32 = A64.float()
     b64 = torch.from_numpy(P.b).cuda()
     truth = set(np.flatnonzero(P.x_star).tolist())
     out = {"workload": P.name, "tol_rel": tol, "N_shards": P.N, "M_blocks": P.M, "kappa": P.kappa,
@@ -403,7 +404,7 @@ def run_time_to_tol(stream, tol=1e-6):
     for name, prec in (("fp64", bc.PREC_FP64), ("fp32", bc.PREC_FP32)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s = bc.Solver(A64 if prec == bc.PREC_FP64 else A64.float(), b64, loss=P.loss, N=P.N, M=P.M,
+        s = bc.Solver(A64 if prec == bc.PREC_FP64 else A32, b64, loss=P.loss, N=P.N, M=P.M,
                       kappa=P.kappa, gamma=P.gamma, rho_c=P.rho, precision=prec, tol_rel=tol,
                       check_every=5, max_iters=5000, stream=stream)
         torch.cuda.synchronize()

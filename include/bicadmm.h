@@ -228,6 +228,54 @@ int bicadmm_batch_kernel_times(bicadmm_batch_t b, double* ms_out, int64_t* launc
 int bicadmm_batch_destroy(bicadmm_batch_t b);
 const char* bicadmm_batch_last_error(bicadmm_batch_t b);
 
+/* Device bytes a handle with these parameters allocates (including one polished get_x),
+ * and the extra bytes its setup holds temporarily.  Needs a current CUDA device. */
+int bicadmm_estimate_bytes(const bicadmm_params* params, int64_t* device_bytes,
+                           int64_t* setup_extra_bytes);
+
+/* Serving (not part of the paper): a request loop with continuous batching.  Requests are
+ * complete solves (A, b and parameters) submitted with an arrival time on the server's
+ * clock (seconds since bicadmm_server_create, bicadmm_server_clock).  bicadmm_server_run
+ * works in rounds until every submitted request is finished (or, with no request active,
+ * the next arrival is later than `until`):
+ *   - admit: arrived requests, in arrival order, get a handle (device copy of A and b,
+ *     factors, iteration state) while the estimated device bytes stay within
+ *     hbm_budget_bytes and at most max_active are active; a request that can never fit
+ *     finishes with BICADMM_ERR_OOM;
+ *   - one batched round (bicadmm_batch_step over every active request, CUDA graph when
+ *     use_graph) of up to iters_per_round iterations, cut short so no request passes its
+ *     max_iters; requests arriving meanwhile are admitted while the round runs;
+ *   - retire: a request whose residuals meet its tol_rel (checked at round ends) or that
+ *     reached max_iters is polished (when `polish`), copied to host and its memory freed.
+ * Each request's iterates are those of solving it alone up to rounding (the batch only
+ * regroups partial sums).  The caller keeps A and b of a request valid until it finishes.
+ * All requests use the server's precision and inner_iters = 1.  Single host thread. */
+typedef struct bicadmm_server_ctx* bicadmm_server_t;
+typedef struct {
+  int64_t hbm_budget_bytes;  /* device bytes the active requests may hold              */
+  int32_t max_active;        /* requests in flight at most                             */
+  int32_t iters_per_round;   /* iterations per batched round                           */
+  int32_t precision;         /* BICADMM_PREC_* of every request                        */
+  int32_t use_graph;         /* replay rounds from a captured CUDA graph               */
+  int32_t polish;            /* results are polished (kappa <= 1024)                   */
+  int32_t pad;
+} bicadmm_server_params;
+int bicadmm_server_create(const bicadmm_server_params* sp, bicadmm_server_t* out);
+double bicadmm_server_clock(bicadmm_server_t s);
+int bicadmm_server_submit(bicadmm_server_t s, const bicadmm_params* p, const void* A,
+                          int32_t A_dtype, int64_t lda, int32_t A_on_device, const void* b,
+                          int32_t b_dtype, int32_t b_on_device, double arrival, int64_t* id_out);
+int bicadmm_server_run(bicadmm_server_t s, double until, int64_t* completed_out);
+/* Result of a finished request: x (n doubles; polished if the server polishes), support
+ * (kappa indices), info, and times_out[3] = arrival, admission, completion.  Returns the
+ * request's own status when it failed. */
+int bicadmm_server_result(bicadmm_server_t s, int64_t id, double* x_host, int64_t len,
+                          int64_t* support_out, bicadmm_info* info, double* times_out);
+/* counters_out[5]: submitted, finished, rounds, peak estimated device bytes, launches. */
+int bicadmm_server_stats(bicadmm_server_t s, int64_t* counters_out);
+int bicadmm_server_destroy(bicadmm_server_t s);
+const char* bicadmm_server_last_error(bicadmm_server_t s);
+
 /* Free every device buffer of the handle (synchronises its stream).  NULL is accepted. */
 int bicadmm_destroy(bicadmm_t h);
 

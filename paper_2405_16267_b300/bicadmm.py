@@ -49,6 +49,12 @@ class Info(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class ServerParams(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_active", ctypes.c_int32),
+                ("iters_per_round", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("polish", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
 class BicadmmError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("%s (%d): %s" % (STATUS.get(code, "?"), code, msg))
@@ -89,6 +95,21 @@ SIGNATURES = [
                                                   ctypes.POINTER(ctypes.c_int64)]),
     ("bicadmm_batch_destroy", ctypes.c_int, [_VP]),
     ("bicadmm_batch_last_error", ctypes.c_char_p, [_VP]),
+    ("bicadmm_estimate_bytes", ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_int64),
+                                              ctypes.POINTER(ctypes.c_int64)]),
+    ("bicadmm_server_create", ctypes.c_int, [ctypes.POINTER(ServerParams), ctypes.POINTER(_VP)]),
+    ("bicadmm_server_clock", ctypes.c_double, [_VP]),
+    ("bicadmm_server_submit", ctypes.c_int, [_VP, ctypes.POINTER(Params), _VP, ctypes.c_int32,
+                                             ctypes.c_int64, ctypes.c_int32, _VP, ctypes.c_int32,
+                                             ctypes.c_int32, ctypes.c_double,
+                                             ctypes.POINTER(ctypes.c_int64)]),
+    ("bicadmm_server_run", ctypes.c_int, [_VP, ctypes.c_double, ctypes.POINTER(ctypes.c_int64)]),
+    ("bicadmm_server_result", ctypes.c_int, [_VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                                             ctypes.POINTER(Info), ctypes.POINTER(ctypes.c_double)]),
+    ("bicadmm_server_stats", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
+    ("bicadmm_server_destroy", ctypes.c_int, [_VP]),
+    ("bicadmm_server_last_error", ctypes.c_char_p, [_VP]),
     ("bicadmm_destroy", ctypes.c_int, [_VP]),
     ("bicadmm_last_error", ctypes.c_char_p, [_VP]),
 ]
@@ -290,6 +311,82 @@ def batch_kernel_times(b):
 def batch_destroy(b):
     if b:
         _bcheck(lib().bicadmm_batch_destroy(b))
+
+
+def estimate_bytes(params):
+    dev = ctypes.c_int64()
+    extra = ctypes.c_int64()
+    _check(lib().bicadmm_estimate_bytes(ctypes.byref(params), ctypes.byref(dev), ctypes.byref(extra)))
+    return dev.value, extra.value
+
+
+def _scheck(code, s=None):
+    if code != 0:
+        msg = lib().bicadmm_server_last_error(s)
+        raise BicadmmError(code, msg.decode() if msg else "")
+
+
+class Server:
+    """Serving loop with continuous batching (include/bicadmm.h, bicadmm_server_*)."""
+
+    def __init__(self, hbm_budget_bytes, max_active=64, iters_per_round=10,
+                 precision=PREC_FP32, use_graph=True, polish=True):
+        sp = ServerParams(int(hbm_budget_bytes), int(max_active), int(iters_per_round),
+                          int(precision), int(bool(use_graph)), int(bool(polish)), 0)
+        self.s = _VP()
+        _scheck(lib().bicadmm_server_create(ctypes.byref(sp), ctypes.byref(self.s)))
+        self._keep = {}
+        self._n = {}
+
+    def clock(self):
+        return lib().bicadmm_server_clock(self.s)
+
+    def submit(self, A, b, arrival, **params):
+        """A, b: numpy arrays (host) or torch tensors (host or device); kept alive here
+        until the request's result is taken."""
+        pa, ca, da, ka = _buffer(A)
+        pb, cb, db, kb = _buffer(b)
+        m, n = ka.shape
+        p = default_params(m=m, n=n, **params)
+        rid = ctypes.c_int64()
+        _scheck(lib().bicadmm_server_submit(self.s, ctypes.byref(p), pa, ca, n, da, pb, cb, db,
+                                            float(arrival), ctypes.byref(rid)), self.s)
+        self._keep[rid.value] = (ka, kb)
+        self._n[rid.value] = (n, p.kappa)
+        return rid.value
+
+    def run(self, until=1e30):
+        done = ctypes.c_int64()
+        _scheck(lib().bicadmm_server_run(self.s, float(until), ctypes.byref(done)), self.s)
+        return done.value
+
+    def result(self, rid):
+        n, kappa = self._n[rid]
+        x = np.zeros(n)
+        sup = np.zeros(kappa, dtype=np.int64)
+        inf = Info()
+        t = (ctypes.c_double * 3)()
+        code = lib().bicadmm_server_result(self.s, int(rid), x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          n, sup.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                          ctypes.byref(inf), t)
+        self._keep.pop(rid, None)
+        return dict(status=code, x=x, support=sup, info=inf, arrival=t[0], admitted=t[1], done=t[2])
+
+    def stats(self):
+        c = (ctypes.c_int64 * 5)()
+        _scheck(lib().bicadmm_server_stats(self.s, c), self.s)
+        return dict(submitted=c[0], finished=c[1], rounds=c[2], peak_bytes=c[3], launches=c[4])
+
+    def close(self):
+        if self.s:
+            lib().bicadmm_server_destroy(self.s)
+            self.s = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def destroy(h):

@@ -12,7 +12,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <deque>
+#include <thread>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -39,6 +42,9 @@ constexpr int kTraceCap = kTraceCapacity;
 constexpr int64_t kMaxN = 32768;                 // single-CTA global step limit
 constexpr size_t kPassSmemBudget = 200 * 1024;   // dynamic smem for A-pass stages
 constexpr size_t kPassCtaTarget = 100 * 1024;    // auto sizing aims at two CTAs per SM
+constexpr int kPolishRowBlocks = 592;
+constexpr int kPolishChunks = 64;
+constexpr int kMaxPolishKappa = 1024;
 
 int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
@@ -472,6 +478,24 @@ int build_geometry(bicadmm_ctx* h) {
   return BICADMM_OK;
 }
 
+// Device bytes a handle allocates (including the polish buffers of one polished get_x),
+// and the extra bytes its setup holds temporarily.
+void handle_bytes(const bicadmm_ctx* h, int64_t* persistent, int64_t* setup_extra) {
+  const int64_t m = h->p.m, lda = h->lda, N = h->N, kappa = h->p.kappa;
+  const int64_t es = static_cast<int64_t>(h->esz);
+  int64_t b = 0;
+  b += m * lda * es + 3 * m * es;                        // A, b, omega, nu
+  b += static_cast<int64_t>(h->nslots) * lda * es;       // slots
+  b += N * lda * es + h->P_total * es;                   // xlo, P
+  b += 3 * N * lda * 8 + 7 * lda * 8;                    // x, u, r; z, s, w, tau_r, c, e, key
+  b += static_cast<int64_t>(h->G) * 32 + N * h->dual_chunks * 16 + 4096 * 112 + 4096;
+  // polish: supp, A_S, q, d1, d2, p, x_S, step, partials, H
+  b += kappa * 8 + kappa * m * 8 + 4 * m * 8 + 2 * kappa * 8 + kPolishRowBlocks * 8 +
+       static_cast<int64_t>(kPolishChunks) * kappa * 8 + (kPolishChunks + 1) * kappa * kappa * 8;
+  if (persistent) *persistent = b;
+  if (setup_extra) *setup_extra = std::min<int64_t>(256ll << 20, m * lda * 8) + h->G_total * 8;
+}
+
 int allocate(bicadmm_ctx* h) {
   const int64_t m = h->p.m, lda = h->lda, N = h->N;
   const size_t es = h->esz;
@@ -590,11 +614,10 @@ int load_matrix(bicadmm_ctx* h, const void* src, int dtype, int64_t lda_src, int
 
 template <typename TA>
 int build_factors(bicadmm_ctx* h) {
-  double *G = nullptr, *W = nullptr;
+  double* G = nullptr;
   cudaError_t e = cudaMalloc(&G, std::max<int64_t>(h->G_total, 1) * sizeof(double));
   if (e != cudaSuccess) { cudaGetLastError(); return fail(h, BICADMM_ERR_OOM, "Gram buffer allocation failed"); }
-  e = cudaMalloc(&W, std::max<int64_t>(h->G_total, 1) * sizeof(double));
-  if (e != cudaSuccess) { cudaGetLastError(); cudaFree(G); return fail(h, BICADMM_ERR_OOM, "factor scratch allocation failed"); }
+
   int rc = BICADMM_OK;
   const int T = (h->max_nj + 63) / 64;
   const dim3 ggrid(T * (T + 1) / 2, h->M, h->N);
@@ -603,13 +626,26 @@ int build_factors(bicadmm_ctx* h) {
   h->launches += 1;
   e = cudaGetLastError();
   if (e == cudaSuccess) {
-    auto kc = k_chol_inv<TA, kCholThreads>;
+    auto kc = k_chol<kCholThreads>;
     const size_t sm = static_cast<size_t>(h->max_nj) * sizeof(double);
     if (sm > 48 * 1024) e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
     if (e == cudaSuccess) {
-      kc<<<h->N * h->M, kCholThreads, sm, h->stream>>>(G, h->d_G_off, W, h->d_blk_col0, h->d_blk_ldp, h->M,
-                                                    h->p.rho_l, h->c0, static_cast<TA*>(h->Pm),
-                                                    h->d_P_off, h->d_err);
+      kc<<<h->N * h->M, kCholThreads, sm, h->stream>>>(G, h->d_G_off, h->d_blk_col0, h->M,
+                                                    h->p.rho_l, h->c0, h->d_err);
+      h->launches += 1;
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) {
+    // one warp per column; as many warps as fit 200 KB of column vectors (at most 8)
+    const int warps = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(8, (200 << 10) / (8 * h->max_nj))));
+    const size_t sm = static_cast<size_t>(warps) * h->max_nj * sizeof(double);
+    auto ki = k_inv_cols<TA>;
+    if (sm > 48 * 1024) e = cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
+    if (e == cudaSuccess) {
+      const dim3 grid(h->N * h->M, (h->max_nj + warps - 1) / warps);
+      ki<<<grid, 32 * warps, sm, h->stream>>>(G, h->d_G_off, h->d_blk_col0, h->d_blk_ldp, h->M,
+                                              static_cast<TA*>(h->Pm), h->d_P_off);
       h->launches += 1;
       e = cudaGetLastError();
     }
@@ -618,15 +654,11 @@ int build_factors(bicadmm_ctx* h) {
   cudaError_t e2 = cudaStreamSynchronize(h->stream);
   if (rc == BICADMM_OK && e2 != cudaSuccess) rc = fail(h, BICADMM_ERR_CUDA, std::string("factor sync: ") + cudaGetErrorString(e2));
   cudaFree(G);
-  cudaFree(W);
   if (rc != BICADMM_OK) return rc;
   return check_device_error(h);
 }
 
 // ---------------------------------------------------------------- support and polish
-constexpr int kPolishRowBlocks = 592;
-constexpr int kPolishChunks = 64;
-constexpr int kMaxPolishKappa = 1024;
 
 int compute_support(bicadmm_ctx* h) {
   if (!h->supp) {
@@ -1041,6 +1073,24 @@ int bicadmm_default_params(bicadmm_params* p) {
   return BICADMM_OK;
 }
 
+int bicadmm_estimate_bytes(const bicadmm_params* params, int64_t* device_bytes,
+                           int64_t* setup_extra_bytes) {
+  std::string why;
+  int rc = validate(params, why);
+  if (rc != BICADMM_OK) { g_create_error = why; return rc; }
+  bicadmm_ctx tmp;
+  tmp.p = *params;
+  if (tmp.p.rho_b == 0.0) tmp.p.rho_b = 0.5 * tmp.p.rho_c;
+  if (tmp.p.rho_l == 0.0) tmp.p.rho_l = tmp.p.rho_c;
+  cudaError_t e = cudaGetDevice(&tmp.device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&tmp.num_sms, cudaDevAttrMultiProcessorCount, tmp.device);
+  if (e != cudaSuccess) { cudaGetLastError(); g_create_error = "no usable CUDA device"; return BICADMM_ERR_CUDA; }
+  rc = build_geometry(&tmp);
+  if (rc != BICADMM_OK) { g_create_error = tmp.err; return rc; }
+  handle_bytes(&tmp, device_bytes, setup_extra_bytes);
+  return BICADMM_OK;
+}
+
 int bicadmm_create(const bicadmm_params* params, void* stream, bicadmm_t* out) {
   g_create_error.clear();
   if (!out) { g_create_error = "out is NULL"; return BICADMM_ERR_ARG; }
@@ -1422,6 +1472,292 @@ int bicadmm_batch_destroy(bicadmm_batch_t b) {
 const char* bicadmm_batch_last_error(bicadmm_batch_t b) {
   if (!b) return g_create_error.c_str();
   return b->err.c_str();
+}
+
+// ============================================================================ serving
+
+struct ServerReq {
+  bicadmm_params p{};
+  const void* A = nullptr;
+  const void* b = nullptr;
+  int32_t A_dtype = 0, b_dtype = 0, A_dev = 0, b_dev = 0;
+  int64_t lda = 0;
+  double arrival = 0.0, admitted = -1.0, done = -1.0;
+  bicadmm_t h = nullptr;
+  int64_t bytes = 0;
+  int iters = 0;
+  int status = BICADMM_OK;
+  std::vector<double> x;
+  std::vector<int64_t> support;
+  bicadmm_info info{};
+};
+
+struct bicadmm_server_ctx {
+  bicadmm_server_params sp{};
+  cudaStream_t round_stream = nullptr, setup_stream = nullptr;
+  std::vector<ServerReq> reqs;
+  std::deque<int64_t> waiting;   // FIFO of submitted, not yet admitted requests
+  std::vector<int64_t> active;
+  bicadmm_batch_t batch = nullptr;
+  bool dirty = true;
+  int64_t bytes_in_use = 0, peak_bytes = 0;
+  int64_t rounds = 0, completed = 0, launches = 0;
+  std::chrono::steady_clock::time_point t0;
+  std::string err;
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+namespace {
+
+int sfail(bicadmm_server_ctx* s, int code, const std::string& msg) {
+  if (s) s->err = msg;
+  return code;
+}
+
+void server_drop_batch(bicadmm_server_ctx* s) {
+  if (s->batch) {
+    bicadmm_batch_destroy(s->batch);
+    s->batch = nullptr;
+  }
+  s->dirty = true;
+}
+
+// Admit arrived requests in FIFO order while the device-memory budget and slot count allow.
+int server_admit(bicadmm_server_ctx* s) {
+  const double t = s->now();
+  while (!s->waiting.empty() && static_cast<int>(s->active.size()) < s->sp.max_active) {
+    ServerReq& r = s->reqs[s->waiting.front()];
+    if (r.arrival > t) break;
+    int64_t need = 0, extra = 0;
+    int rc = bicadmm_estimate_bytes(&r.p, &need, &extra);
+    if (rc != BICADMM_OK) {  // an invalid request fails alone
+      r.status = rc;
+      r.done = t;
+      s->waiting.pop_front();
+      ++s->completed;
+      continue;
+    }
+    if (need + extra > s->sp.hbm_budget_bytes) {
+      r.status = BICADMM_ERR_OOM;
+      r.done = t;
+      s->waiting.pop_front();
+      ++s->completed;
+      continue;
+    }
+    if (s->bytes_in_use + need + extra > s->sp.hbm_budget_bytes) break;  // wait for memory
+    bicadmm_t h = nullptr;
+    rc = bicadmm_create(&r.p, s->setup_stream, &h);
+    if (rc == BICADMM_OK) {
+      rc = bicadmm_setup(h, r.A, r.A_dtype, r.lda, r.A_dev, r.b, r.b_dtype, r.b_dev);
+      if (rc != BICADMM_OK) {
+        s->err = h->err;
+        bicadmm_destroy(h);
+        h = nullptr;
+      }
+    } else {
+      s->err = g_create_error;
+    }
+    s->waiting.pop_front();
+    if (rc != BICADMM_OK) {
+      r.status = rc;
+      r.done = s->now();
+      ++s->completed;
+      continue;
+    }
+    r.h = h;
+    r.bytes = need;
+    r.admitted = t;
+    s->bytes_in_use += need;
+    s->peak_bytes = std::max(s->peak_bytes, s->bytes_in_use + extra);
+    s->active.push_back(static_cast<int64_t>(&r - s->reqs.data()));
+    s->dirty = true;
+  }
+  return BICADMM_OK;
+}
+
+// Residual check of every active request after a round; retire the finished ones.
+int server_retire(bicadmm_server_ctx* s) {
+  std::vector<int64_t> still, finished;
+  for (int64_t id : s->active) {
+    ServerReq& r = s->reqs[id];
+    bicadmm_info inf;
+    int rc = fill_info(r.h, &inf);
+    const double mx = std::max(std::max(inf.p_rel, inf.d_rel), std::max(inf.b_rel, inf.i_rel));
+    const bool conv = r.iters > 1 && mx <= r.p.tol_rel;
+    if (rc != BICADMM_OK || conv || r.iters >= r.p.max_iters) {
+      r.status = rc;
+      r.info = inf;
+      r.info.converged = conv ? 1 : 0;
+      finished.push_back(id);
+    } else {
+      still.push_back(id);
+    }
+  }
+  if (finished.empty()) return BICADMM_OK;
+  server_drop_batch(s);  // the batch references the handles
+  for (int64_t id : finished) {
+    ServerReq& r = s->reqs[id];
+    if (r.status == BICADMM_OK) {
+      r.x.assign(r.p.n, 0.0);
+      r.support.assign(r.p.kappa, 0);
+      const int pol = s->sp.polish && r.p.kappa <= kMaxPolishKappa ? 1 : 0;
+      r.status = bicadmm_get_x(r.h, r.x.data(), r.p.n, pol, r.support.data());
+    }
+    bicadmm_destroy(r.h);
+    r.h = nullptr;
+    s->bytes_in_use -= r.bytes;
+    r.done = s->now();
+    ++s->completed;
+  }
+  s->active = still;
+  return BICADMM_OK;
+}
+
+}  // namespace
+
+int bicadmm_server_create(const bicadmm_server_params* sp, bicadmm_server_t* out) {
+  g_create_error.clear();
+  if (!sp || !out) { g_create_error = "params and out are required"; return BICADMM_ERR_ARG; }
+  *out = nullptr;
+  if (sp->hbm_budget_bytes <= 0 || sp->max_active < 1 || sp->iters_per_round < 1) {
+    g_create_error = "need hbm_budget_bytes > 0, max_active >= 1, iters_per_round >= 1";
+    return BICADMM_ERR_ARG;
+  }
+  bicadmm_server_ctx* s = new bicadmm_server_ctx();
+  s->sp = *sp;
+  if (cudaStreamCreateWithFlags(&s->round_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->setup_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    g_create_error = "stream creation failed";
+    delete s;
+    return BICADMM_ERR_CUDA;
+  }
+  s->t0 = std::chrono::steady_clock::now();
+  *out = s;
+  return BICADMM_OK;
+}
+
+double bicadmm_server_clock(bicadmm_server_t s) { return s ? s->now() : 0.0; }
+
+int bicadmm_server_submit(bicadmm_server_t s, const bicadmm_params* p, const void* A,
+                          int32_t A_dtype, int64_t lda, int32_t A_on_device, const void* b,
+                          int32_t b_dtype, int32_t b_on_device, double arrival, int64_t* id_out) {
+  if (!s) return BICADMM_ERR_ARG;
+  if (!p || !A || !b || !id_out) return sfail(s, BICADMM_ERR_ARG, "p, A, b and id_out are required");
+  if (p->precision != s->sp.precision) return sfail(s, BICADMM_ERR_ARG, "request precision differs from the server's");
+  if (p->inner_iters != 1) return sfail(s, BICADMM_ERR_UNSUPPORTED, "served requests use inner_iters = 1");
+  ServerReq r;
+  r.p = *p;
+  r.A = A;
+  r.b = b;
+  r.A_dtype = A_dtype;
+  r.b_dtype = b_dtype;
+  r.A_dev = A_on_device;
+  r.b_dev = b_on_device;
+  r.lda = lda;
+  r.arrival = arrival;
+  s->reqs.push_back(std::move(r));
+  const int64_t id = static_cast<int64_t>(s->reqs.size()) - 1;
+  // keep the waiting list ordered by arrival (stable for equal times)
+  auto it = s->waiting.end();
+  while (it != s->waiting.begin() && s->reqs[*(it - 1)].arrival > arrival) --it;
+  s->waiting.insert(it, id);
+  *id_out = id;
+  return BICADMM_OK;
+}
+
+int bicadmm_server_run(bicadmm_server_t s, double until, int64_t* completed_out) {
+  if (!s) return BICADMM_ERR_ARG;
+  int rc;
+  for (;;) {
+    if ((rc = server_admit(s)) != BICADMM_OK) return rc;
+    if (s->active.empty()) {
+      if (s->waiting.empty()) break;
+      const double next = s->reqs[s->waiting.front()].arrival;
+      if (next > until) break;
+      const double wait = next - s->now();
+      if (wait > 0) std::this_thread::sleep_for(std::chrono::duration<double>(std::min(wait, 0.001)));
+      continue;
+    }
+    if (s->dirty || !s->batch) {
+      server_drop_batch(s);
+      std::vector<bicadmm_t> hs;
+      for (int64_t id : s->active) hs.push_back(s->reqs[id].h);
+      rc = bicadmm_batch_create(hs.data(), static_cast<int32_t>(hs.size()), s->round_stream,
+                                s->sp.use_graph ? BICADMM_BATCH_GRAPH : 0, &s->batch);
+      if (rc != BICADMM_OK) return sfail(s, rc, std::string("batch: ") + g_create_error);
+      s->dirty = false;
+    }
+    // a round: as many iterations as the closest request to its cap still needs (<= the
+    // round length), so every request stops exactly at its iteration cap
+    int k = s->sp.iters_per_round;
+    for (int64_t id : s->active) k = std::min(k, s->reqs[id].p.max_iters - s->reqs[id].iters);
+    k = std::max(k, 1);
+    int64_t launches = 0;
+    if ((rc = bicadmm_batch_step(s->batch, k, &launches)) != BICADMM_OK) return sfail(s, rc, s->batch->err);
+    s->launches += 4 * k;
+    for (int64_t id : s->active) s->reqs[id].iters += k;
+    ++s->rounds;
+    // new arrivals are set up (setup stream) while the round runs on the device
+    if ((rc = server_admit(s)) != BICADMM_OK) return rc;
+    if (cudaStreamSynchronize(s->round_stream) != cudaSuccess) return sfail(s, BICADMM_ERR_CUDA, "round failed");
+    if ((rc = server_retire(s)) != BICADMM_OK) return rc;
+    if (s->active.empty() && s->waiting.empty()) break;
+    if (s->now() > until && s->active.empty()) break;
+  }
+  if (completed_out) *completed_out = s->completed;
+  return BICADMM_OK;
+}
+
+int bicadmm_server_result(bicadmm_server_t s, int64_t id, double* x_host, int64_t len,
+                          int64_t* support_out, bicadmm_info* info, double* times_out) {
+  if (!s) return BICADMM_ERR_ARG;
+  if (id < 0 || id >= static_cast<int64_t>(s->reqs.size())) return sfail(s, BICADMM_ERR_ARG, "unknown request id");
+  const ServerReq& r = s->reqs[id];
+  if (r.done < 0) return sfail(s, BICADMM_ERR_STATE, "request not finished");
+  if (times_out) {
+    times_out[0] = r.arrival;
+    times_out[1] = r.admitted;
+    times_out[2] = r.done;
+  }
+  if (info) *info = r.info;
+  if (r.status != BICADMM_OK) return r.status;
+  if (x_host) {
+    if (len != r.p.n) return sfail(s, BICADMM_ERR_ARG, "x_host must hold n doubles");
+    std::copy(r.x.begin(), r.x.end(), x_host);
+  }
+  if (support_out) std::copy(r.support.begin(), r.support.end(), support_out);
+  return BICADMM_OK;
+}
+
+int bicadmm_server_stats(bicadmm_server_t s, int64_t* counters_out) {
+  if (!s) return BICADMM_ERR_ARG;
+  if (counters_out) {
+    counters_out[0] = static_cast<int64_t>(s->reqs.size());
+    counters_out[1] = s->completed;
+    counters_out[2] = s->rounds;
+    counters_out[3] = s->peak_bytes;
+    counters_out[4] = s->launches;
+  }
+  return BICADMM_OK;
+}
+
+int bicadmm_server_destroy(bicadmm_server_t s) {
+  if (!s) return BICADMM_OK;
+  server_drop_batch(s);
+  for (ServerReq& r : s->reqs)
+    if (r.h) bicadmm_destroy(r.h);
+  cudaStreamDestroy(s->round_stream);
+  cudaStreamDestroy(s->setup_stream);
+  delete s;
+  return BICADMM_OK;
+}
+
+const char* bicadmm_server_last_error(bicadmm_server_t s) {
+  if (!s) return g_create_error.c_str();
+  return s->err.c_str();
 }
 
 int bicadmm_destroy(bicadmm_t h) {

@@ -88,20 +88,17 @@ k_gram(const TA* __restrict__ A, int64_t lda, const int64_t* __restrict__ shard_
     }
 }
 
-// One CTA per block (i, j): K = rho_l G + c0 I (in place in G, lower triangle), Cholesky
-// K = L L' in place, then P = K^-1 by forward and back substitution, one column per
-// thread, in FP64 scratch W; finally P is written in TP with row stride ldp (zero padded).
-template <typename TP, int CT>
+// One CTA per block (i, j): K = rho_l G + c0 I (in place in G), Cholesky K = L L' in place in
+// the lower triangle (right-looking, column k cached in shared memory), then L' is copied
+// into the strict upper triangle so that both triangular solves read rows.
+template <int CT>
 __global__ void __launch_bounds__(CT)
-k_chol_inv(double* __restrict__ G, const int64_t* __restrict__ G_off, double* __restrict__ W,
-           const int* __restrict__ blk_col0, const int* __restrict__ blk_ldp, int M,
-           double rho_l, double c0, TP* __restrict__ P, const int64_t* __restrict__ P_off,
-           int* __restrict__ err) {
+k_chol(double* __restrict__ G, const int64_t* __restrict__ G_off, const int* __restrict__ blk_col0,
+       int M, double rho_l, double c0, int* __restrict__ err) {
   extern __shared__ double colk[];
-  const int blk = blockIdx.x, i = blk / M, j = blk - i * M;
-  const int nj = blk_col0[j + 1] - blk_col0[j], ldp = blk_ldp[j];
+  const int blk = blockIdx.x, j = blk % M;
+  const int nj = blk_col0[j + 1] - blk_col0[j];
   double* K = G + G_off[blk];
-  double* Wb = W + G_off[blk];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NWP = CT / 32;
   for (int64_t e = tid; e < static_cast<int64_t>(nj) * nj; e += CT) {
@@ -109,13 +106,10 @@ k_chol_inv(double* __restrict__ G, const int64_t* __restrict__ G_off, double* __
     K[e] = rho_l * K[e] + (a == bq ? c0 : 0.0);
   }
   __syncthreads();
-  __shared__ int bad;
-  if (tid == 0) bad = 0;
-  __syncthreads();
   for (int k = 0; k < nj; ++k) {
     if (tid == 0) {
       const double dkk = K[static_cast<int64_t>(k) * nj + k];
-      if (!(dkk > 0.0)) { bad = 1; set_err(err, DEV_NONPOS_PIVOT); }
+      if (!(dkk > 0.0)) set_err(err, DEV_NONPOS_PIVOT);
       K[static_cast<int64_t>(k) * nj + k] = dkk > 0.0 ? sqrt(dkk) : 1.0;
     }
     __syncthreads();
@@ -133,28 +127,51 @@ k_chol_inv(double* __restrict__ G, const int64_t* __restrict__ G_off, double* __
     }
     __syncthreads();
   }
-  if (bad) return;
-  // Columns of K^-1: L y = e_c, then L' p = y.
-  for (int cidx = tid; cidx < nj; cidx += CT) {
-    for (int a = 0; a < nj; ++a) {
-      double sacc = (a == cidx) ? 1.0 : 0.0;
-      const double* La = K + static_cast<int64_t>(a) * nj;
-      for (int bq = 0; bq < a; ++bq) sacc -= La[bq] * Wb[static_cast<int64_t>(bq) * nj + cidx];
-      Wb[static_cast<int64_t>(a) * nj + cidx] = sacc / La[a];
-    }
-    for (int a = nj - 1; a >= 0; --a) {
-      double sacc = Wb[static_cast<int64_t>(a) * nj + cidx];
-      for (int bq = a + 1; bq < nj; ++bq)
-        sacc -= K[static_cast<int64_t>(bq) * nj + a] * Wb[static_cast<int64_t>(bq) * nj + cidx];
-      Wb[static_cast<int64_t>(a) * nj + cidx] = sacc / K[static_cast<int64_t>(a) * nj + a];
-    }
+  // upper triangle <- L'
+  for (int64_t e = tid; e < static_cast<int64_t>(nj) * nj; e += CT) {
+    const int a = static_cast<int>(e / nj), bq = static_cast<int>(e - static_cast<int64_t>(a) * nj);
+    if (bq > a) K[e] = K[static_cast<int64_t>(bq) * nj + a];
   }
-  __syncthreads();
-  TP* Pb = P + P_off[blk];
-  for (int64_t e = tid; e < static_cast<int64_t>(nj) * ldp; e += CT) {
-    const int a = static_cast<int>(e / ldp), bq = static_cast<int>(e - static_cast<int64_t>(a) * ldp);
-    Pb[e] = bq < nj ? static_cast<TP>(Wb[static_cast<int64_t>(a) * nj + bq]) : TP(0);
+}
+
+// Columns of K^-1 = L^-T L^-1: grid (blocks, column groups), one warp per column c:
+// forward L y = e_c then back L' p = y, the column held in shared memory; P is written in
+// TP with row stride ldp (P is symmetric, so column c is written as row c, its padding
+// entries zeroed).
+template <typename TP>
+__global__ void k_inv_cols(const double* __restrict__ G, const int64_t* __restrict__ G_off,
+                           const int* __restrict__ blk_col0, const int* __restrict__ blk_ldp,
+                           int M, TP* __restrict__ P, const int64_t* __restrict__ P_off) {
+  extern __shared__ double ycol[];  // [warps][nj]
+  const int blk = blockIdx.x, j = blk % M;
+  const int nj = blk_col0[j + 1] - blk_col0[j], ldp = blk_ldp[j];
+  const int nw = blockDim.x >> 5, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.y * nw + warp;
+  if (c >= nj) return;
+  const double* K = G + G_off[blk];
+  double* y = ycol + static_cast<int64_t>(warp) * nj;
+  for (int a = lane; a < nj; a += 32) y[a] = 0.0;
+  __syncwarp();
+  // forward: y_a = (delta_ac - sum_{b<a} L[a,b] y_b) / L[a,a], zero for a < c
+  for (int a = c; a < nj; ++a) {
+    const double* La = K + static_cast<int64_t>(a) * nj;
+    double part = 0.0;
+    for (int bq = c + lane; bq < a; bq += 32) part = fma(La[bq], y[bq], part);
+    part = warp_sum(part);
+    if (lane == 0) y[a] = ((a == c ? 1.0 : 0.0) - part) / La[a];
+    __syncwarp();
   }
+  // back: p_a = (y_a - sum_{b>a} L[b,a] p_b) / L[a,a]; row a of the upper triangle is L[., a]
+  for (int a = nj - 1; a >= 0; --a) {
+    const double* Ua = K + static_cast<int64_t>(a) * nj;
+    double part = 0.0;
+    for (int bq = a + 1 + lane; bq < nj; bq += 32) part = fma(Ua[bq], y[bq], part);
+    part = warp_sum(part);
+    if (lane == 0) y[a] = (y[a] - part) / Ua[a];
+    __syncwarp();
+  }
+  TP* Pr = P + P_off[blk] + static_cast<int64_t>(c) * ldp;
+  for (int a = lane; a < ldp; a += 32) Pr[a] = a < nj ? static_cast<TP>(y[a]) : TP(0);
 }
 
 }  // namespace bic
