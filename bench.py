@@ -51,8 +51,12 @@ def parse():
     ap.add_argument("--pass-stages", type=int, default=0)
     ap.add_argument("--inner", type=int, default=1, help="inner sharing sweeps J per iteration")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance leg")
-    ap.add_argument("--workload", default="logistic", choices=["logistic", "batch"],
-                    help="batch: 256 uneven instances advanced by batched launches")
+    ap.add_argument("--workload", default="logistic", choices=["logistic", "batch", "serve"],
+                    help="batch: 256 uneven instances advanced by batched launches; "
+                         "serve: a Poisson stream of solves through the serving loop")
+    ap.add_argument("--requests", type=int, default=64, help="requests in the serve workload")
+    ap.add_argument("--rate", type=float, default=200.0, help="mean arrivals/s (serve)")
+    ap.add_argument("--serve-iters", type=int, default=100, help="iteration cap per request")
     ap.add_argument("--batch", type=int, default=256, help="instances in the batch workload")
     return ap.parse_args()
 
@@ -383,6 +387,60 @@ def run_batch(args, rank, world):
     }
 
 
+# ----------------------------------------------------------------------------- serve
+
+def run_serve(args, rank, world):
+    """Serving: a Poisson stream (args.rate per second) of args.requests solves of mixed
+    loss and size (m log-uniform [1e3, 2e5], n log-uniform [100, 1e4], kappa 1-5 % of n,
+    FP32), inputs drawn on the device beforehand; the serving loop admits them under a
+    150 GB budget with continuous batching.  Latency = completion - arrival."""
+    import torch
+    from paper_2405_16267_b300 import bicadmm as bc
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    specs = synth.serve_request_specs(count=args.requests, rate=args.rate)
+    t_gen = time.perf_counter()
+    data = [synth.device_request(sp) for sp in specs]
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    a_bytes = sum(sp["m"] * sp["n"] * 4 for sp in specs)
+    clocks = ClockSampler(local)
+    with bc.Server(hbm_budget_bytes=150 << 30, max_active=64, iters_per_round=10,
+                   precision=bc.PREC_FP32, use_graph=True, polish=True) as srv:
+        t0 = srv.clock() + 0.05
+        ids = [srv.submit(A, b, arrival=t0 + sp["arrival"], loss=sp["loss"],
+                          precision=bc.PREC_FP32, N_shards=sp["N"], M_blocks=sp["M"],
+                          kappa=sp["kappa"], gamma=10.0, rho_c=1.0, max_iters=args.serve_iters,
+                          tol_rel=1e-6)
+               for sp, (A, b) in zip(specs, data)]
+        srv.run()
+        res = [srv.result(i) for i in ids]
+        st = srv.stats()
+    clk = clocks.stop()
+    ok = [r for r in res if r["status"] == 0]
+    lat = np.array([r["done"] - r["arrival"] for r in ok])
+    wait = np.array([r["admitted"] - r["arrival"] for r in ok])
+    span = max(r["done"] for r in res) - min(r["arrival"] for r in res)
+    return {
+        "metric": "solves/s (serving, continuous batching)", "value": len(ok) / span,
+        "unit": "solves/s", "n_gpus": world, "steps": len(res), "warmup": 0,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded, drawn on the device)",
+        "config": {"workload": "serve_poisson%d_mixed_fp32" % int(args.rate),
+                   "requests": len(res), "arrival_rate_per_s": args.rate,
+                   "offered_A_bytes": a_bytes, "hbm_budget_bytes": 150 << 30,
+                   "iters_per_request_cap": args.serve_iters, "tol_rel": 1e-6,
+                   "iters_per_round": 10},
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "mean": float(lat.mean()), "max": float(lat.max())},
+        "queue_wait_s": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
+        "completed": len(ok), "failed": len(res) - len(ok),
+        "converged": int(sum(r["info"].converged for r in ok)),
+        "server": st, "input_generation_s": t_gen, "clocks": clk,
+        "gpu_launches": int(st["launches"]),
+    }
+
+
 # ----------------------------------------------------------------------------- time to tol
 
 TABLE1 = dict(m=100000, n=2000, sparsity=0.9, noise=0.01, N=4, M=4, rho=1.0, gamma=10.0, seed=0)
@@ -487,6 +545,8 @@ def main():
         res = run_reference(args, rank, world)
     elif args.workload == "batch":
         res = run_batch(args, rank, world)
+    elif args.workload == "serve":
+        res = run_serve(args, rank, world)
     else:
         res = run_gpu(args, rank, world)
         if rank == 0 and not args.no_ttt:

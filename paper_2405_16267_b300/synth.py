@@ -261,6 +261,41 @@ def batch_instance(spec, noise=0.1, dtype=np.float32) -> Problem:
                    spec["loss"], spec["N"], spec["M"], kappa, 1.0, 10.0, 0)
 
 
+def serve_request_specs(count=64, seed=0, rate=200.0, m_range=(1000, 200000),
+                        n_range=(100, 10000), block_cols=512):
+    """A Poisson stream of solve requests: gaps Exp(rate); m and n log-uniform in their
+    ranges; kappa uniform in 1..5 % of n; N uniform in 4..16 shards; M such that blocks have
+    at most `block_cols` columns; loss cycling squared / logistic / squared hinge."""
+    g = _rng(seed, 8)
+    t, specs = 0.0, []
+    losses = (LOSS_SQUARED, LOSS_LOGISTIC, LOSS_SQHINGE)
+    for k in range(count):
+        t += float(g.exponential(1.0 / rate))
+        m = int(round(math.exp(g.uniform(math.log(m_range[0]), math.log(m_range[1])))))
+        n = int(round(math.exp(g.uniform(math.log(n_range[0]), math.log(n_range[1])))))
+        kappa = max(1, int(round(n * g.uniform(0.01, 0.05))))
+        N = min(m, int(g.integers(4, 17)))
+        specs.append(dict(arrival=t, m=m, n=n, kappa=kappa, N=N, M=max(1, -(-n // block_cols)),
+                          loss=losses[k % 3], seed=seed * 1000003 + k))
+    return specs
+
+
+def device_request(spec, device="cuda", noise=0.1):
+    """A request's data drawn on the device (torch's seeded CUDA generator): A i.i.d. N(0,1)
+    FP32, x* with kappa entries +/-U[1,2], b = A x* + N(0, noise^2) or its sign."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(spec["seed"]))
+    m, n, kappa = spec["m"], spec["n"], spec["kappa"]
+    A = torch.randn(m, n, generator=g, device=device, dtype=torch.float32)
+    idx = torch.randperm(n, generator=g, device=device)[:kappa]
+    mag = 1.0 + torch.rand(kappa, generator=g, device=device, dtype=torch.float32)
+    sgn = torch.where(torch.rand(kappa, generator=g, device=device) < 0.5, -1.0, 1.0)
+    lin = A[:, idx] @ (mag * sgn) + noise * torch.randn(m, generator=g, device=device)
+    b = lin if spec["loss"] == LOSS_SQUARED else torch.where(lin >= 0, 1.0, -1.0)
+    return A, b.double()
+
+
 def round_to_f32(A: np.ndarray) -> np.ndarray:
     """FP32-rounded copy of A upcast back to FP64 (the exact values an FP32 run sees)."""
     return A.astype(np.float32).astype(np.float64)
