@@ -24,7 +24,14 @@ Readings where the paper is silent or inconsistent (each also pinned by a test):
     (eqs. x-min-step rewritten, p:x-subp, u-update); the sign of y_i in eq. eq:al is read
     the same way.
   * Losses take the label as a second argument: squared (q-b)^2 (no 1/2, as eq. p:sls),
-    logistic log(1+exp(-b q)), squared hinge max(0, 1-b q)^2, with b in {-1,+1}.
+    logistic log(1+exp(-b q)), squared hinge max(0, 1-b q)^2, with b in {-1,+1}; softmax
+    (Sec. 2's sparse softmax regression) is the cross-entropy logsumexp(q) - q_y of the
+    K-vector q = a_r W, label y in {0..K-1}.
+  * Softmax: the decision variable is the n x K matrix W; every n-space vector (x_i, u_i,
+    z, s) holds it flattened feature-major (entry (c, k) at c*K + k), so the sparsity
+    budget kappa, the (z,t) step, the s step and the lowest-index tie rule apply entrywise
+    to that vector.  The block solve of eq. (p:GPU;x) takes the K columns of W_ij at once
+    (the same block matrix for every class); omega, nu and the block products are m x K.
   * All state starts at zero; the inner count J is a parameter.
   * Uneven shards/blocks: contiguous ranges, the first (total mod parts) one longer.
   * The (z,t) problem is solved exactly: z = soft-threshold(w + tau s, tau) with tau the
@@ -64,8 +71,23 @@ def split_ranges(total, parts):
 
 # --------------------------------------------------------------------------- losses
 
+def logsumexp_rows(q):
+    """log sum_k exp(q_rk) per row, shifted by the row maximum."""
+    qm = q.max(axis=1)
+    return qm + np.log(np.exp(q - qm[:, None]).sum(axis=1))
+
+
+def softmax_rows(q):
+    e = np.exp(q - q.max(axis=1)[:, None])
+    return e / e.sum(axis=1)[:, None]
+
+
 def loss_rows(loss, q, b):
-    """Per-row loss l(q; b) of problem (p:SML) for each supported model (Sec. 2)."""
+    """Per-row loss l(q; b) of problem (p:SML) for each supported model (Sec. 2).
+    Softmax: q is m x K and b holds the class index of each row."""
+    if loss == LOSS_SOFTMAX:
+        y = np.asarray(b).astype(np.int64)
+        return logsumexp_rows(q) - q[np.arange(q.shape[0]), y]
     if loss == LOSS_SQUARED:
         return (q - b) ** 2
     if loss == LOSS_LOGISTIC:
@@ -75,9 +97,11 @@ def loss_rows(loss, q, b):
     raise ValueError("loss %r" % loss)
 
 
-def objective(loss, A, b, x, gamma):
-    """F(x) = sum_r l(a_r x; b_r) + ||x||^2 / (2 gamma)   (problem p:SML)."""
-    return float(np.sum(loss_rows(loss, A @ x, b)) + x @ x / (2.0 * gamma))
+def objective(loss, A, b, x, gamma, K=1):
+    """F(x) = sum_r l(a_r x; b_r) + ||x||^2 / (2 gamma)   (problem p:SML); for softmax x is
+    the flattened n x K matrix."""
+    X = np.asarray(x, dtype=np.float64).reshape(A.shape[1], K) if K > 1 else x
+    return float(np.sum(loss_rows(loss, A @ X, b)) + np.sum(X * X) / (2.0 * gamma))
 
 
 def omega_prox(loss, a, b, M, rho_l):
@@ -88,6 +112,8 @@ def omega_prox(loss, a, b, M, rho_l):
     with a = (mean of the block products) + nu.
     """
     a = np.asarray(a, dtype=np.float64)
+    if loss == LOSS_SOFTMAX:
+        return softmax_prox(a, b, M, rho_l)
     if loss == LOSS_SQUARED:
         # d/dw: 2M(Mw - b) + M rho_l (w - a) = 0
         return (2.0 * b + rho_l * a) / (2.0 * M + rho_l)
@@ -112,6 +138,51 @@ def omega_prox(loss, a, b, M, rho_l):
             lo = np.where(pos, lo, mid)
         return 0.5 * (lo + hi)
     raise ValueError("loss %r" % loss)
+
+
+def softmax_prox(a, y, M, rho_l, max_iters=200):
+    """Softmax omega-bar step of eq. (p:GPU;omega), one K-vector problem per row:
+
+        omega_r = argmin_w  CE(M w; y_r) + (M rho_l / 2) ||w - a_r||^2,
+        CE(q; y) = logsumexp(q) - q_y.
+
+    phi is strongly convex; gradient g = M (softmax(M w) - e_y) + M rho_l (w - a), Hessian
+    H = M^2 (diag p - p p') + M rho_l I.  Newton from w = a, all rows at once, damped by
+    backtracking on ||g|| (the Newton direction decreases ||g||^2 at rate 2||g||^2; unlike
+    phi itself, ||g|| has no cancellation near the minimum), until every row's step is
+    within a few ulps of w.
+    """
+    a = np.asarray(a, dtype=np.float64)
+    y = np.asarray(y).astype(np.int64)
+    m, K = a.shape
+    onehot = np.zeros((m, K))
+    onehot[np.arange(m), y] = 1.0
+    eye = np.eye(K)[None]
+
+    def grad(w):
+        return M * (softmax_rows(M * w) - onehot) + M * rho_l * (w - a)
+
+    eps = np.finfo(np.float64).eps
+    w = a.copy()
+    g = grad(w)
+    for _ in range(max_iters):
+        p = softmax_rows(M * w)
+        H = (M * M) * (p[:, :, None] * eye - p[:, :, None] * p[:, None, :]) + M * rho_l * eye
+        step = np.linalg.solve(H, g[:, :, None])[:, :, 0]
+        done = np.all(np.abs(step) <= 4.0 * eps * np.maximum(1.0, np.abs(w)), axis=1)
+        if done.all():
+            break
+        gn = np.linalg.norm(g, axis=1)
+        alpha = np.where(done, 0.0, 1.0)
+        for _ in range(60):
+            g_try = grad(w - alpha[:, None] * step)
+            bad = (np.linalg.norm(g_try, axis=1) > (1.0 - 1e-4 * alpha) * gn) & ~done
+            if not bad.any():
+                break
+            alpha = np.where(bad, 0.5 * alpha, alpha)
+        w = w - alpha[:, None] * step
+        g = grad(w)
+    return w
 
 
 # --------------------------------------------------------------------------- (z,t) step
@@ -193,15 +264,19 @@ def s_step(z, t, v, kappa):
 class BiCADMM:
     """Bi-cADMM over N sample shards, each with M feature blocks (Algorithms 1 and 2).
 
-    A: (m, n) FP64, b: (m,) targets (squared) or labels in {-1,+1}.
+    A: (m, n) FP64, b: (m,) targets (squared), labels in {-1,+1}, or class indices
+    0..K-1 (softmax, K classes).  n-space vectors have length n*K (feature-major).
     """
 
     def __init__(self, A, b, loss, N, M, kappa, gamma=10.0, rho_c=1.0, rho_b=None,
-                 rho_l=None, inner_iters=1, n_shards_total=None):
+                 rho_l=None, inner_iters=1, n_shards_total=None, K=1):
         self.A = np.asarray(A, dtype=np.float64)
         self.b = np.asarray(b, dtype=np.float64)
         self.m, self.n = self.A.shape
         self.loss, self.N, self.M, self.kappa = int(loss), int(N), int(M), int(kappa)
+        self.K = int(K)
+        if (self.loss == LOSS_SOFTMAX) != (self.K > 1):
+            raise ValueError("K > 1 exactly for the softmax loss")
         self.gamma, self.rho_c = float(gamma), float(rho_c)
         self.rho_b = 0.5 * self.rho_c if rho_b is None else float(rho_b)
         self.rho_l = self.rho_c if rho_l is None else float(rho_l)
@@ -223,18 +298,19 @@ class BiCADMM:
                 K = self.rho_l * (Aij.T @ Aij) + self.c0 * np.eye(c1_ - c0_)
                 row.append(scipy.linalg.cho_factor(K, lower=True))
             self.factors.append(row)
-        n, N = self.n, self.N
-        self.x = np.zeros((N, n))
-        self.u = np.zeros((N, n))
-        self.z = np.zeros(n)
-        self.s = np.zeros(n)
+        n, N, K = self.n, self.N, self.K
+        self.x = np.zeros((N, n * K))
+        self.u = np.zeros((N, n * K))
+        self.z = np.zeros(n * K)
+        self.s = np.zeros(n * K)
         self.t = 0.0
         self.v = 0.0
         self.tau = 0.0
-        self.omega = np.zeros(self.m)   # omega-bar, per shard row range
-        self.nu = np.zeros(self.m)
-        self.Axbar = np.zeros(self.m)   # (1/M) sum_j A_ij x_ij
-        self.p = [[np.zeros(r1 - r0) for _ in self.blocks] for (r0, r1) in self.shards]
+        mshape = (self.m,) if K == 1 else (self.m, K)
+        self.omega = np.zeros(mshape)   # omega-bar, per shard row range
+        self.nu = np.zeros(mshape)
+        self.Axbar = np.zeros(mshape)   # (1/M) sum_j A_ij x_ij
+        self.p = [[np.zeros((r1 - r0, K)) for _ in self.blocks] for (r0, r1) in self.shards]
         self.iters = 0
         self.history = []
 
@@ -242,23 +318,32 @@ class BiCADMM:
     def x_step_shard(self, i):
         r0, r1 = self.shards[i]
         b_i = self.b[r0:r1]
+        K = self.K
+        # (rows, K) views of the m-space state and (n, K) views of the n-space state
+        omega_v = self.omega.reshape(self.m, K)
+        nu_v = self.nu.reshape(self.m, K)
+        Axbar_v = self.Axbar.reshape(self.m, K)
+        X, U, Z = self.x[i].reshape(self.n, K), self.u[i].reshape(self.n, K), self.z.reshape(self.n, K)
         for _ in range(self.J):
-            omega, Axbar, nu = self.omega[r0:r1], self.Axbar[r0:r1], self.nu[r0:r1]
+            omega, Axbar, nu = omega_v[r0:r1], Axbar_v[r0:r1], nu_v[r0:r1]
             new_x = []
             for j, (c0_, c1_) in enumerate(self.blocks):
                 Aij = self.A[r0:r1, c0_:c1_]
                 # eq. (p:GPU;x): target A_ij x_ij ~ A_ij x_ij^k + omega^k - Axbar^k - nu^k
                 c_ij = self.p[i][j] + omega - Axbar - nu
-                rhs = self.rho_l * (Aij.T @ c_ij) + self.rho_c * (self.z[c0_:c1_] - self.u[i, c0_:c1_])
+                rhs = self.rho_l * (Aij.T @ c_ij) + self.rho_c * (Z[c0_:c1_] - U[c0_:c1_])
                 new_x.append(scipy.linalg.cho_solve(self.factors[i][j], rhs))
             for j, (c0_, c1_) in enumerate(self.blocks):
-                self.x[i, c0_:c1_] = new_x[j]
+                X[c0_:c1_] = new_x[j]
                 self.p[i][j] = self.A[r0:r1, c0_:c1_] @ new_x[j]
             Axbar_new = sum(self.p[i]) / self.M                      # "Allreduce", Alg. 2
-            omega_new = omega_prox(self.loss, Axbar_new + nu, b_i, self.M, self.rho_l)  # (p:GPU;omega)
-            self.nu[r0:r1] = nu + Axbar_new - omega_new              # (p:GPU;nu)
-            self.omega[r0:r1] = omega_new
-            self.Axbar[r0:r1] = Axbar_new
+            if K == 1:                                               # (p:GPU;omega)
+                omega_new = omega_prox(self.loss, (Axbar_new + nu)[:, 0], b_i, self.M, self.rho_l)[:, None]
+            else:
+                omega_new = omega_prox(self.loss, Axbar_new + nu, b_i, self.M, self.rho_l)
+            nu_v[r0:r1] = nu + Axbar_new - omega_new                 # (p:GPU;nu)
+            omega_v[r0:r1] = omega_new
+            Axbar_v[r0:r1] = Axbar_new
 
     # ---- one outer iteration (iterations block, scaled form)
     def iterate(self, n_iters=1):
@@ -304,17 +389,20 @@ class BiCADMM:
         return top_kappa(self.z, self.kappa)
 
     def polished(self):
-        return polish(self.A, self.b, self.loss, self.gamma, self.support())
+        return polish(self.A, self.b, self.loss, self.gamma, self.support(), K=self.K)
 
 
 # --------------------------------------------------------------------------- polish
 
-def polish(A, b, loss, gamma, S, tol=1e-13, max_newton=100):
+def polish(A, b, loss, gamma, S, tol=1e-13, max_newton=100, K=1):
     """Restricted problem on a fixed support S (not part of the paper's algorithm):
 
         min_{supp x in S}  sum_r l(a_r x; b_r) + ||x||^2 / (2 gamma),  solved in FP64.
+    Softmax: S indexes the flattened n x K matrix (entry (c, k) at c*K + k).
     """
     A = np.asarray(A, dtype=np.float64)
+    if loss == LOSS_SOFTMAX:
+        return _polish_softmax(A, b, gamma, S, K, tol, max_newton)
     n = A.shape[1]
     AS = A[:, S]
     x = np.zeros(n)
@@ -347,3 +435,42 @@ def polish(A, b, loss, gamma, S, tol=1e-13, max_newton=100):
             break
     x[S] = xs
     return x
+
+
+def _polish_softmax(A, b, gamma, S, K, tol, max_newton):
+    """Damped Newton on the entries in S of the n x K matrix W (the rest held at zero).
+    With Q = A W and P = softmax rows: gradient A'(P - Y) + W/gamma; Hessian of entries
+    (c, k), (c', k'): sum_r a_rc a_rc' p_rk (delta_kk' - p_rk') + delta / gamma."""
+    m, n = A.shape
+    y = np.asarray(b).astype(np.int64)
+    S = np.asarray(S, dtype=np.int64)
+    cols, cls = S // K, S % K
+    Y = np.zeros((m, K))
+    Y[np.arange(m), y] = 1.0
+    w = np.zeros(len(S))
+
+    def full(wv):
+        W = np.zeros(n * K)
+        W[S] = wv
+        return W.reshape(n, K)
+
+    def F(wv):
+        Q = A @ full(wv)
+        return float(np.sum(logsumexp_rows(Q) - Q[np.arange(m), y]) + wv @ wv / (2.0 * gamma))
+
+    AS = A[:, cols]                      # column of A for each support entry
+    for _ in range(max_newton):
+        P = softmax_rows(A @ full(w))
+        G = A.T @ (P - Y)
+        grad = G[cols, cls] + w / gamma
+        Pk = P[:, cls]                   # p_{r, k(e)} for each support entry e
+        same = (cls[:, None] == cls[None, :]).astype(np.float64)
+        H = (AS * Pk).T @ AS * same - (AS * Pk).T @ (AS * Pk) + np.eye(len(S)) / gamma
+        step = np.linalg.solve(H, grad)
+        f0, alpha = F(w), 1.0
+        while F(w - alpha * step) > f0 + 1e-16 * abs(f0) and alpha > 1e-12:
+            alpha *= 0.5
+        w = w - alpha * step
+        if np.linalg.norm(alpha * step) <= tol * max(1.0, np.linalg.norm(w)):
+            break
+    return full(w).reshape(-1)

@@ -45,7 +45,8 @@ def split_ranges(total: int, parts: int):
 
 @dataclasses.dataclass
 class Problem:
-    """One synthetic instance: A (m x n, row-major), labels/targets b (m,), planted x_star."""
+    """One synthetic instance: A (m x n, row-major), labels/targets b (m,), planted x_star
+    (n, or the flattened n x K matrix W* for softmax: entry (c, k) at c*K + k)."""
     name: str
     A: np.ndarray
     b: np.ndarray
@@ -57,6 +58,7 @@ class Problem:
     rho: float
     gamma: float = 10.0
     iters: int = 200
+    K: int = 1
 
     @property
     def m(self):
@@ -216,6 +218,55 @@ def sparse_sqhinge(m=4000, n=400, nnz=12, noise=0.1, N=4, M=2, kappa=12, rho=1.0
     b = _sign_pm1(A @ x_star + noise * _noise(m, seed))
     return Problem("sparse_sqhinge_%dx%d" % (m, n), A, b, x_star, LOSS_SQHINGE, N, M, kappa,
                    rho, gamma, iters)
+
+
+def _gumbel(m: int, K: int, seed: int, row0: int = 0, chunk_rows: int = 4096) -> np.ndarray:
+    """Standard Gumbel(0, 1) draws for rows [row0, row0+m), K per row (chunked like A)."""
+    out = np.empty((m, K))
+    r = row0
+    while r < row0 + m:
+        c = r // chunk_rows
+        c0, c1 = c * chunk_rows, (c + 1) * chunk_rows
+        u = _rng(seed, 4, c).random((chunk_rows, K))
+        lo, hi = max(r, c0), min(row0 + m, c1)
+        out[lo - row0:hi - row0] = -np.log(-np.log(u[lo - c0:hi - c0] + 1e-300))
+        r = hi
+    return out
+
+
+def planted_matrix(n: int, K: int, nnz: int, seed: int) -> np.ndarray:
+    """W* (n x K, returned flattened feature-major) with nnz N(0,1) entries at uniformly
+    random positions among the n*K entries."""
+    g = _rng(seed, 5)
+    w = np.zeros(n * K)
+    idx = g.choice(n * K, size=nnz, replace=False)
+    w[idx] = g.standard_normal(nnz)
+    return w
+
+
+def sparse_softmax(m=500000, n=2000, K=10, nnz=500, N=32, M=4, kappa=500, rho=1.0,
+                   gamma=10.0, iters=200, seed=0, dtype=np.float32, rows=None,
+                   scale=1.0) -> Problem:
+    """Sparse softmax regression: A i.i.d. N(0,1) (times ``scale``), W* (n x K) with nnz
+    N(0,1) entries at uniformly random positions, labels y_r = argmax_k (a_r W* + G_rk)
+    with G standard Gumbel noise (so y is a draw from softmax(a_r W*)).  Labels are class
+    indices 0..K-1 stored as floats.  Defaults are the 500000 x 2000, K = 10 workload
+    (N = 32 shards, M = 4 blocks, entrywise kappa = 500).  rows=(r0, r1) generates only that
+    row range of the same matrix; A is returned in ``dtype``."""
+    r0, r1 = (0, m) if rows is None else rows
+    W = planted_matrix(n, K, nnz, seed).reshape(n, K)
+    A = np.empty((r1 - r0, n), dtype=dtype)
+    b = np.empty(r1 - r0)
+    chunk = 4096
+    r = r0
+    while r < r1:
+        c = min(r1, (r // chunk + 1) * chunk)
+        blk = gaussian_rows(c - r, n, seed, row0=r, chunk_rows=chunk) * scale
+        b[r - r0:c - r0] = np.argmax(blk @ W + _gumbel(c - r, K, seed, row0=r, chunk_rows=chunk), axis=1)
+        A[r - r0:c - r0] = blk
+        r = c
+    return Problem("sparse_softmax_%dx%dx%d" % (m, n, K), A, b, W.reshape(-1), LOSS_SOFTMAX,
+                   N, M, kappa, rho, gamma, iters, K)
 
 
 def small_problem(loss: int, m: int, n: int, nnz: int, N: int, M: int, kappa: int,

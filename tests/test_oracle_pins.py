@@ -5,6 +5,7 @@ closed form, an independent numerical method (scipy's generic optimisers, brute-
 enumeration, bisection) or an optimality condition stated on the original problem.
 """
 import itertools
+import math
 import json
 import os
 
@@ -320,3 +321,131 @@ def test_split_ranges():
     assert ref.split_ranges(10, 3) == [(0, 4), (4, 7), (7, 10)]
     assert ref.split_ranges(5, 5) == [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5)]
     assert synth.split_ranges(10, 3) == ref.split_ranges(10, 3)
+
+
+# ----------------------------------------------------------------- softmax (K classes)
+
+def test_softmax_loss_closed_forms():
+    """Cross-entropy of Sec. 2's sparse softmax regression: logsumexp(q) - q_y."""
+    q = np.array([[0.0, 0.0, 0.0], [1.0, 2.0, 0.0], [-3.0, 5.0, 5.0]])
+    y = np.array([1, 0, 2])
+    want = [math.log(3.0), math.log(math.e + math.e ** 2 + 1.0) - 1.0,
+            math.log(math.exp(-3.0) + 2.0 * math.exp(5.0)) - 5.0]
+    np.testing.assert_allclose(ref.loss_rows(ref.LOSS_SOFTMAX, q, y), want, rtol=1e-15)
+
+
+def test_softmax_prox_two_classes_is_logistic_prox():
+    """K = 2: with delta = w_1 - w_0 and sigma = w_0 + w_1 the softmax prox separates into
+    sigma = a_0 + a_1 and a logistic prox of eq. (p:GPU;omega) for delta at a_1 - a_0 with
+    label +1 (class 1) or -1 (class 0) and penalty rho_l / 2 (||w - a||^2 is half the sum
+    of the squared sigma and delta offsets).  The logistic prox is a bisection."""
+    rng = np.random.default_rng(11)
+    for M, rho_l in [(1, 1.0), (4, 0.5), (8, 2.0), (2, 0.05)]:
+        a = rng.standard_normal((200, 2)) * 3
+        y = rng.integers(0, 2, 200)
+        w = ref.softmax_prox(a, y, M, rho_l)
+        delta = ref.omega_prox(ref.LOSS_LOGISTIC, a[:, 1] - a[:, 0], np.where(y == 1, 1.0, -1.0),
+                               M, rho_l / 2)
+        np.testing.assert_allclose(w[:, 1] - w[:, 0], delta, rtol=0, atol=1e-12 * (1 + np.abs(delta).max()))
+        np.testing.assert_allclose(w.sum(axis=1), a.sum(axis=1), rtol=0, atol=1e-12 * (1 + np.abs(a).max()))
+
+
+def test_softmax_prox_vs_generic_minimiser():
+    rng = np.random.default_rng(12)
+    K = 5
+    for _ in range(25):
+        M = int(rng.integers(1, 9))
+        rho_l = float(rng.uniform(0.05, 4))
+        a = rng.standard_normal(K) * 2
+        y = int(rng.integers(0, K))
+        phi = lambda w: float(ref.loss_rows(ref.LOSS_SOFTMAX, (M * w)[None], np.array([y]))[0]
+                              + 0.5 * M * rho_l * np.sum((w - a) ** 2))
+        res = scipy.optimize.minimize(phi, a, method="BFGS", options=dict(gtol=1e-12))
+        w = ref.softmax_prox(a[None], np.array([y]), M, rho_l)[0]
+        assert phi(w) <= res.fun + 1e-12 * (1 + abs(res.fun))
+        np.testing.assert_allclose(w, res.x, atol=1e-6)
+
+
+def test_inner_sharing_admm_reaches_exact_prox_softmax():
+    """Sec. 3.1 with K = 3 classes: J sweeps of the sharing ADMM give the exact local prox
+    argmin_W sum_r CE(a_r W; y_r) + ||W||^2/(2 N gamma) + rho_c/2 ||W - Z + U||^2."""
+    K, n, N, gamma, rho_c = 3, 8, 2, 3.0, 0.8
+    P = synth.sparse_softmax(m=160, n=n, K=K, nnz=5, N=N, M=2, kappa=5, seed=3, dtype=np.float64)
+    o = ref.BiCADMM(P.A, P.b, ref.LOSS_SOFTMAX, N, 2, 5, gamma=gamma, rho_c=rho_c, rho_l=1.5,
+                    inner_iters=4000, K=K)
+    rng = np.random.default_rng(2)
+    o.z = rng.standard_normal(n * K) * 0.5
+    o.u[1] = rng.standard_normal(n * K) * 0.2
+    o.x_step_shard(1)
+    r0, r1 = o.shards[1]
+    A1, b1 = P.A[r0:r1], P.b[r0:r1]
+
+    def f(x):
+        W = x.reshape(n, K)
+        return (np.sum(ref.loss_rows(ref.LOSS_SOFTMAX, A1 @ W, b1)) + x @ x / (2 * N * gamma)
+                + 0.5 * rho_c * np.sum((x - o.z + o.u[1]) ** 2))
+
+    res = scipy.optimize.minimize(f, np.zeros(n * K), method="BFGS", options=dict(gtol=1e-11, maxiter=20000))
+    np.testing.assert_allclose(o.x[1], res.x, atol=1e-6)
+
+
+def test_softmax_kappa_full_gives_ridge_softmax():
+    """kappa = n K: the l0 constraint is void and problem (p:SML) is ridge-regularised
+    multinomial logistic regression, whose minimiser a generic method finds."""
+    K, n = 3, 5
+    P = synth.sparse_softmax(m=150, n=n, K=K, nnz=6, N=3, M=2, kappa=n * K, seed=4, dtype=np.float64)
+    o = ref.BiCADMM(P.A, P.b, ref.LOSS_SOFTMAX, 3, 2, n * K, gamma=2.0, rho_c=1.0, inner_iters=2, K=K)
+    assert o.solve(tol_rel=1e-8, max_iters=3000)
+    f = lambda x: ref.objective(ref.LOSS_SOFTMAX, P.A, P.b, x, 2.0, K=K)
+    res = scipy.optimize.minimize(f, np.zeros(n * K), method="BFGS", options=dict(gtol=1e-11))
+    np.testing.assert_allclose(o.z, res.x, atol=1e-5 * np.abs(res.x).max())
+
+
+def _brute_force_softmax(A, b, K, kappa, gamma):
+    n = A.shape[1]
+    best = (np.inf, None)
+    for S in itertools.combinations(range(n * K), kappa):
+        S = np.array(S)
+
+        def f(ws):
+            x = np.zeros(n * K)
+            x[S] = ws
+            return ref.objective(ref.LOSS_SOFTMAX, A, b, x, gamma, K=K)
+
+        res = scipy.optimize.minimize(f, np.zeros(kappa), method="BFGS", options=dict(gtol=1e-10))
+        if res.fun < best[0]:
+            x = np.zeros(n * K)
+            x[S] = res.x
+            best = (res.fun, x)
+    return best
+
+
+def test_softmax_brute_force_support_clear_margin():
+    """n = 4 features, K = 3 classes, entrywise kappa = 2 on a planted W* with two large
+    entries: after 200 iterations the Bi-cADMM support (entries (c, k) at c*K + k) and its
+    polished solution equal the optimum over all C(12, 2) supports.  (Bi-cADMM on the
+    classification losses converges slowly in the residuals; the support settles early.)"""
+    K, n, kappa = 3, 4, 2
+    P = synth.sparse_softmax(m=600, n=n, K=K, nnz=kappa, N=2, M=2, kappa=kappa, seed=7,
+                             dtype=np.float64, scale=2.0)
+    o = ref.BiCADMM(P.A, P.b, ref.LOSS_SOFTMAX, 2, 2, kappa, gamma=10.0, rho_c=1.0, K=K)
+    o.iterate(200)
+    f_best, x_best = _brute_force_softmax(P.A, P.b, K, kappa, 10.0)
+    assert set(o.support()) == set(np.flatnonzero(x_best))
+    np.testing.assert_allclose(o.polished(), x_best, atol=1e-6)
+
+
+def test_polish_softmax_vs_generic():
+    K, n = 3, 8
+    P = synth.sparse_softmax(m=300, n=n, K=K, nnz=5, N=2, M=2, kappa=5, seed=9, dtype=np.float64)
+    S = np.flatnonzero(P.x_star)
+    x = ref.polish(P.A, P.b, ref.LOSS_SOFTMAX, 10.0, S, K=K)
+
+    def f(ws):
+        v = np.zeros(n * K)
+        v[S] = ws
+        return ref.objective(ref.LOSS_SOFTMAX, P.A, P.b, v, 10.0, K=K)
+
+    res = scipy.optimize.minimize(f, np.zeros(len(S)), method="BFGS", options=dict(gtol=1e-12))
+    np.testing.assert_allclose(x[S], res.x, atol=1e-6)
+    assert np.count_nonzero(x) <= len(S)
