@@ -36,7 +36,13 @@ typedef struct bicadmm_ctx* bicadmm_t;
 
 /* Loss l(q; b) of a row (Sec. 2 lists the models; squared as eq. p:sls, without 1/2).
  * SQUARED: (q - b)^2.  LOGISTIC: log(1 + exp(-b q)), b in {-1,+1}.
- * SQHINGE: max(0, 1 - b q)^2, b in {-1,+1}.  SOFTMAX is reserved (not yet supported). */
+ * SQHINGE: max(0, 1 - b q)^2, b in {-1,+1}.
+ * SOFTMAX (sparse softmax regression, K = 2..16 classes): the model is an n x K matrix W,
+ *   q = a_r W is a K-vector, l(q; y) = logsumexp(q) - q_y with y in {0, .., K-1} given as
+ *   b_r (an integral value).  Every n-space array (x_i, u_i, z, s, the model returned by
+ *   bicadmm_get_x) holds W flattened feature-major, entry (c, k) at c*K + k; kappa bounds
+ *   the number of nonzero entries of W (entrywise sparsity, ties to the lowest flat index).
+ *   omega and nu are m x K, row-major. */
 enum {
   BICADMM_LOSS_SQUARED = 0,
   BICADMM_LOSS_LOGISTIC = 1,
@@ -46,11 +52,13 @@ enum {
 
 /* Precision of the stored A and of the per-row arithmetic on the A products.
  * FP64: everything in FP64.  FP32: A, A x and A'd in FP32; the n-space state, the block
- * factors and all residuals stay in FP64. */
-enum { BICADMM_PREC_FP64 = 0, BICADMM_PREC_FP32 = 1 };
+ * factors and all residuals stay in FP64.  BF16: A stored in BF16 (rounded to nearest
+ * even at setup; half the bytes of FP32), its products accumulated in FP32, everything
+ * else as in FP32 mode.  The Gram matrices, factors and polish use the stored (rounded) A. */
+enum { BICADMM_PREC_FP64 = 0, BICADMM_PREC_FP32 = 1, BICADMM_PREC_BF16 = 2 };
 
 /* Element type of caller buffers passed to bicadmm_setup(). */
-enum { BICADMM_DTYPE_F64 = 0, BICADMM_DTYPE_F32 = 1 };
+enum { BICADMM_DTYPE_F64 = 0, BICADMM_DTYPE_F32 = 1, BICADMM_DTYPE_BF16 = 2 };
 
 enum {
   BICADMM_OK = 0,
@@ -65,12 +73,12 @@ enum {
 
 /* Fields readable with bicadmm_get_state(); lengths in doubles. */
 enum {
-  BICADMM_FIELD_X = 0,      /* N x n: local estimates x_i (row i = shard i)           */
-  BICADMM_FIELD_U = 1,      /* N x n: scaled consensus duals u_i (eq. u-update)       */
-  BICADMM_FIELD_Z = 2,      /* n: consensus variable z                                */
-  BICADMM_FIELD_S = 3,      /* n: bi-linear variable s in S^kappa                     */
-  BICADMM_FIELD_OMEGA = 4,  /* m: omega-bar of eq. (p:GPU;omega), shard-major rows    */
-  BICADMM_FIELD_NU = 5,     /* m: sharing duals nu of eq. (p:GPU;nu)                  */
+  BICADMM_FIELD_X = 0,      /* N x nK: local estimates x_i (row i = shard i)          */
+  BICADMM_FIELD_U = 1,      /* N x nK: scaled consensus duals u_i (eq. u-update)      */
+  BICADMM_FIELD_Z = 2,      /* nK: consensus variable z                               */
+  BICADMM_FIELD_S = 3,      /* nK: bi-linear variable s in S^kappa                    */
+  BICADMM_FIELD_OMEGA = 4,  /* m x K: omega-bar of eq. (p:GPU;omega), shard-major rows */
+  BICADMM_FIELD_NU = 5,     /* m x K: sharing duals nu of eq. (p:GPU;nu)              */
   BICADMM_FIELD_SCALARS = 6 /* 3: t, v (scaled bi-linear dual, eq. v-update), tau    */
 };
 
@@ -78,16 +86,16 @@ typedef struct {
   int32_t loss;          /* BICADMM_LOSS_*                                              */
   int32_t precision;     /* BICADMM_PREC_*                                              */
   int64_t m, n;          /* rows and columns of A                                       */
-  int64_t K;             /* classes (1 for every supported loss)                        */
+  int64_t K;             /* classes: 2..16 for SOFTMAX, 1 for every other loss          */
   int32_t N_shards;      /* N >= 1 sample shards (1 <= N <= m)                          */
   int32_t M_blocks;      /* M >= 1 feature blocks per shard (1 <= M <= n)               */
-  int64_t kappa;         /* sparsity level, 1 <= kappa <= n                             */
+  int64_t kappa;         /* sparsity level, 1 <= kappa <= n K                           */
   double gamma;          /* ridge weight, > 0                                           */
   double rho_c;          /* consensus penalty, > 0                                      */
   double rho_b;          /* bi-linear penalty, > 0 (0 selects 0.5 rho_c)                */
   double rho_l;          /* sharing (feature-split) penalty, > 0 (0 selects rho_c)      */
   int32_t inner_iters;   /* J: sharing-ADMM sweeps per outer iteration, >= 1            */
-  int32_t newton_iters;  /* cap on safeguarded Newton steps of the logistic omega prox  */
+  int32_t newton_iters;  /* cap on Newton steps of the logistic / softmax omega prox   */
   int32_t max_iters;     /* outer-iteration cap of bicadmm_solve()                      */
   int32_t check_every;   /* solve(): read residuals back every this many iterations     */
   double tol_rel;        /* solve(): stop when max(p_rel, d_rel, b_rel, i_rel) <= tol   */
@@ -110,7 +118,7 @@ typedef struct {
  * Sizes (m, n, N, M, kappa) are zero and must be set by the caller. */
 int bicadmm_default_params(bicadmm_params* p);
 
-/* Validate *params and allocate all device buffers for that problem size.
+/* Validate *params and allocate all device buffers for that problem size (n K <= 32768).
  * stream: a cudaStream_t (NULL = legacy default stream), not owned by the handle.
  * On success *out owns the buffers until bicadmm_destroy().  Errors: ERR_ARG for an
  * invalid size or penalty, ERR_OOM if the device buffers do not fit, ERR_UNSUPPORTED for
@@ -120,7 +128,8 @@ int bicadmm_create(const bicadmm_params* params, void* stream, bicadmm_t* out);
 /* Load the data and build the per-block factors; resets the iteration state to zero.
  * A: m rows of n values with row stride lda (elements, lda >= n), type A_dtype, in host
  *    memory (A_on_device = 0) or device memory (1).  b: m values of type b_dtype (targets
- *    for SQUARED, labels +/-1 otherwise), host or device.  Both are copied (and converted
+ *    for SQUARED, class indices 0..K-1 for SOFTMAX, labels +/-1 otherwise), host or device;
+ *    b_dtype BF16 is not accepted.  Invalid softmax labels give ERR_ARG.  Both are copied (and converted
  *    to the handle's precision); the caller keeps ownership and may free them on return.
  * Builds G_ij = A_ij' A_ij and the inverse of rho_l G_ij + (1/(N gamma) + rho_c) I, the
  * matrix of the x_ij solve of eq. (p:GPU;x), in FP64.  Errors: ERR_ARG, ERR_CUDA,
@@ -138,10 +147,11 @@ int bicadmm_step(bicadmm_t h, int32_t n_iters, bicadmm_info* info);
  * iterations have run in this call.  Not converging is not an error: info->converged = 0. */
 int bicadmm_solve(bicadmm_t h, bicadmm_info* info);
 
-/* Copy the model to host memory x_host[len], len = n.
+/* Copy the model to host memory x_host[len], len = n K (the flattened n x K W for SOFTMAX).
  * polished = 0: the consensus iterate z.  polished = 1: the solution of the problem
  * restricted to S = the kappa largest |z_r| (ties to the lowest index), solved in FP64 by
- * damped Newton on the device (not part of the paper's algorithm; kappa <= 1024, else
+ * damped Newton on the device (not part of the paper's algorithm; kappa <= 1024 and K = 1
+ * (a softmax model is returned unpolished: ERR_UNSUPPORTED), else
  * ERR_UNSUPPORTED; ERR_NUMERIC if the restricted Hessian is not positive definite).
  * support_out (kappa entries, ascending) receives S when non-NULL.  Synchronises the
  * stream; the first polished call allocates the polish buffers (kappa x m doubles). */
@@ -201,7 +211,7 @@ int bicadmm_consensus_step_noalloc(const double* w, double* z, double* s, double
  * persistent A pass over a panel list spanning every instance's shards, consensus step,
  * dual update).  Each instance's iterates are those of bicadmm_step up to rounding (the
  * A'd partial sums are grouped differently).  Requirements: every handle set up, all of
- * one precision and device, inner_iters = 1.  The batch references the handles (it does
+ * one precision (FP64 or FP32) and device, inner_iters = 1, K = 1.  The batch references the handles (it does
  * not own them); destroy the batch before any of its handles.  Handles may still be stepped
  * alone between batch steps.
  * flags: BICADMM_BATCH_GRAPH captures one iteration into a CUDA graph and replays it (needs

@@ -15,8 +15,8 @@ import numpy as np
 from .build_lib import LIB
 
 LOSS_SQUARED, LOSS_LOGISTIC, LOSS_SOFTMAX, LOSS_SQHINGE = 0, 1, 2, 3
-PREC_FP64, PREC_FP32 = 0, 1
-DTYPE_F64, DTYPE_F32 = 0, 1
+PREC_FP64, PREC_FP32, PREC_BF16 = 0, 1, 2
+DTYPE_F64, DTYPE_F32, DTYPE_BF16 = 0, 1, 2
 FIELD_X, FIELD_U, FIELD_Z, FIELD_S, FIELD_OMEGA, FIELD_NU, FIELD_SCALARS = range(7)
 
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_STATE",
@@ -161,12 +161,12 @@ def _buffer(arr):
     try:
         import torch
         if isinstance(arr, torch.Tensor):
-            if arr.dtype not in (torch.float64, torch.float32):
-                raise TypeError("A and b must be float64 or float32")
+            codes = {torch.float64: DTYPE_F64, torch.float32: DTYPE_F32, torch.bfloat16: DTYPE_BF16}
+            if arr.dtype not in codes:
+                raise TypeError("A and b must be float64, float32 or bfloat16")
             if not arr.is_contiguous():
                 arr = arr.contiguous()
-            code = DTYPE_F64 if arr.dtype == torch.float64 else DTYPE_F32
-            return arr.data_ptr(), code, int(arr.is_cuda), arr
+            return arr.data_ptr(), codes[arr.dtype], int(arr.is_cuda), arr
     except ImportError:  # pragma: no cover
         pass
     a = np.ascontiguousarray(arr)
@@ -403,12 +403,13 @@ class Solver:
     """Convenience owner of one handle: create + setup on construction, destroy on close."""
 
     def __init__(self, A, b, *, loss, N, M, kappa, gamma=10.0, rho_c=1.0, rho_b=0.0,
-                 rho_l=0.0, inner_iters=1, precision=PREC_FP64, stream=None, **extra):
+                 rho_l=0.0, inner_iters=1, precision=PREC_FP64, stream=None, K=1, **extra):
         m, n = A.shape
-        self.n, self.m, self.N, self.kappa = int(n), int(m), int(N), int(kappa)
+        self.n, self.m, self.N, self.kappa, self.K = int(n), int(m), int(N), int(kappa), int(K)
         self.params = default_params(loss=loss, precision=precision, m=m, n=n, N_shards=N,
                                      M_blocks=M, kappa=kappa, gamma=gamma, rho_c=rho_c,
-                                     rho_b=rho_b, rho_l=rho_l, inner_iters=inner_iters, **extra)
+                                     rho_b=rho_b, rho_l=rho_l, inner_iters=inner_iters, K=K,
+                                     **extra)
         self.h = create(self.params, stream)
         try:
             setup(self.h, A, b)
@@ -424,16 +425,22 @@ class Solver:
         return solve(self.h)
 
     def x(self, polished=False):
-        return get_x(self.h, self.n, polished)
+        """The model (n entries; n*K, feature-major, for softmax)."""
+        return get_x(self.h, self.n * self.K, polished)
 
     def state(self):
-        N, n, m = self.N, self.n, self.m
+        """Full iteration state; with K > 1, x/u rows, z and s hold n*K entries
+        (feature-major) and omega/nu are (m, K)."""
+        N, n, m, K = self.N, self.n * self.K, self.m, self.K
         sc = get_state(self.h, FIELD_SCALARS, 3)
+        om = get_state(self.h, FIELD_OMEGA, m * K)
+        nu = get_state(self.h, FIELD_NU, m * K)
+        if K > 1:
+            om, nu = om.reshape(m, K), nu.reshape(m, K)
         return dict(x=get_state(self.h, FIELD_X, N * n).reshape(N, n),
                     u=get_state(self.h, FIELD_U, N * n).reshape(N, n),
                     z=get_state(self.h, FIELD_Z, n), s=get_state(self.h, FIELD_S, n),
-                    omega=get_state(self.h, FIELD_OMEGA, m), nu=get_state(self.h, FIELD_NU, m),
-                    t=sc[0], v=sc[1], tau=sc[2])
+                    omega=om, nu=nu, t=sc[0], v=sc[1], tau=sc[2])
 
     def close(self):
         if self.h:

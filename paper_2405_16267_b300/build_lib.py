@@ -20,7 +20,7 @@ LIB = os.path.join(LIBDIR, "libbicadmm.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-cudart", "static",
-         "-Xptxas", "-O3"]
+         "-Xptxas", "-O3", "--split-compile=0"]
 
 
 def nvcc() -> str:

@@ -2,13 +2,14 @@
 // declared in include/bicadmm.h.
 //
 // Device layout (all row-major, all owned by the handle):
-//   A       m x lda   (TA = double | float), lda = n rounded up to 32, zero padding
-//   b, omega, nu      m (TM)
-//   x, u, r  N x lda  FP64;  xlo N x lda (TA copy of x read by the A pass)
-//   z, s, w           lda FP64;  tau_r, c_arr, e_arr lda FP64 and key lda uint64
+//   A       m x lda   (TA = double | float | bf16), lda = n rounded up to 32, zero padding
+//   b       m (TM);  omega, nu  m x K (TM)
+//   x, u, r  N x ldx  FP64, ldx = lda K (K = 1 except softmax: entry (c, k) at c K + k);
+//            xlo N x ldx (TM copy of x read by the A pass)
+//   z, s, w           ldx FP64;  tau_r, c_arr, e_arr ldx FP64 and key ldx uint64
 //                     (scratch of the consensus CTA)
 //   P       per block (i,j): n_j x ldp_j (TP = TM), ldp_j = n_j rounded up to 32
-//   slots   (G + N) x lda (TM): A'd partial sums, one row per (panel CTA, shard) pair
+//   slots   (G + N) x ldx (TM): A'd partial sums, one row per (panel CTA, shard) pair
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,6 +26,7 @@
 #include "common.cuh"
 #include "nspace.cuh"
 #include "batch.cuh"
+#include "multiclass.cuh"
 #include "pass.cuh"
 #include "polish.cuh"
 #include "setup.cuh"
@@ -65,8 +67,12 @@ struct bicadmm_ctx {
   // geometry
   int N = 0, M = 0;
   int64_t lda = 0;
+  int K = 1;          // classes (softmax), 1 otherwise
+  int KC = 1;         // compile-time class bucket of the K > 1 kernels
+  int64_t ldx = 0;    // n-space row stride, lda K
   double c0 = 0.0;
-  size_t esz = 8;  // bytes per A / m-space element
+  size_t esz = 8;  // bytes per m-space / n-space low-precision element (TM)
+  size_t asz = 8;  // bytes per stored A element (TA)
   std::vector<int64_t> shard_row0, panel_start, G_off, P_off;
   std::vector<int> blk_col0, blk_ldp, slot_lo, slot_hi;
   int R = 0, S = 0, VPT = 0, G = 0, nslots = 0, max_nj = 0, max_ldp = 0, dual_chunks = 0;
@@ -155,9 +161,9 @@ ConsensusArgs consensus_args(bicadmm_ctx* h, bool enabled) {
   a.trace = h->trace;
   a.trace_cap = kTraceCap;
   a.N = h->N;
-  a.n = h->p.n;
+  a.n = h->p.n * h->K;
   a.kappa = h->p.kappa;
-  a.lda = h->lda;
+  a.lda = h->ldx;
   a.rho_c = h->p.rho_c;
   a.rho_b = h->p.rho_b;
   a.err = h->d_err;
@@ -185,7 +191,7 @@ int launch_pass_rv(bicadmm_ctx* h, bool with_consensus) {
   }
   PassGeometry geo{h->d_shard_row0, h->d_panel_start, h->N, h->P_panels};
   kern<<<h->G + (with_consensus ? 1 : 0), kPassThreads, h->pass_smem, h->stream>>>(
-      static_cast<const TA*>(h->A), h->lda, static_cast<const TA*>(h->xlo),
+      static_cast<const TA*>(h->A), h->lda, static_cast<const TM*>(h->xlo),
       static_cast<const TM*>(h->b), static_cast<TM*>(h->omega), static_cast<TM*>(h->nu),
       static_cast<TM*>(h->slots), h->cta_stats, geo, h->S, h->p.loss, static_cast<TM>(h->M),
       static_cast<TM>(h->p.rho_l), h->p.newton_iters, h->d_err, kWaitLimitCycles,
@@ -221,6 +227,69 @@ int launch_pass(bicadmm_ctx* h, bool with_consensus) {
   return fail(h, BICADMM_ERR_UNSUPPORTED, "no A-pass variant for this panel height");
 }
 
+// K > 1 (softmax) pass: R is fixed at 8 rows per panel; (VPT, KC) chosen at geometry time.
+constexpr int kPassRowsK = 8;
+
+template <typename TA, typename TM, int VPT, int KC>
+constexpr bool pass_k_fits() {
+  // x and Q accumulators of VPT x VE columns x KC classes, twice, in registers
+  return VPT * Vec16<TA>::n * KC * (sizeof(TM) == 8 ? 2 : 1) <= 80;
+}
+
+template <typename TA, typename TM, int VPT, int KC>
+int launch_pass_k_v(bicadmm_ctx* h, bool with_consensus, int op, int* blocks) {
+  if constexpr (!pass_k_fits<TA, TM, VPT, KC>()) {
+    return fail(h, BICADMM_ERR_UNSUPPORTED, "softmax A-pass: n K too large for the register tiles");
+  } else {
+    auto kern = k_fused_pass_k<TA, TM, kPassRowsK, VPT, kPassThreads, KC>;
+    CK(allow_max_dynamic_smem(kern));
+    if (op == 1) {
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, kPassThreads, h->pass_smem));
+      return BICADMM_OK;
+    }
+    PassGeometry geo{h->d_shard_row0, h->d_panel_start, h->N, h->P_panels};
+    kern<<<h->G + (with_consensus ? 1 : 0), kPassThreads, h->pass_smem, h->stream>>>(
+        static_cast<const TA*>(h->A), h->lda, static_cast<const TM*>(h->xlo), h->ldx, h->K,
+        static_cast<const TM*>(h->b), static_cast<TM*>(h->omega), static_cast<TM*>(h->nu),
+        static_cast<TM*>(h->slots), h->cta_stats, geo, h->S, static_cast<TM>(h->M),
+        static_cast<TM>(h->p.rho_l), h->p.newton_iters, h->d_err, kWaitLimitCycles,
+        consensus_args(h, with_consensus));
+    CK(cudaGetLastError());
+    return BICADMM_OK;
+  }
+}
+
+template <typename TA, typename TM, int KC>
+int launch_pass_k_c(bicadmm_ctx* h, bool wc, int op, int* blocks) {
+  switch (h->VPT) {
+    case 1: return launch_pass_k_v<TA, TM, 1, KC>(h, wc, op, blocks);
+    case 2: return launch_pass_k_v<TA, TM, 2, KC>(h, wc, op, blocks);
+    case 4: return launch_pass_k_v<TA, TM, 4, KC>(h, wc, op, blocks);
+  }
+  return fail(h, BICADMM_ERR_UNSUPPORTED, "no softmax A-pass variant for this width");
+}
+
+// op 0 = launch, 1 = occupancy query
+template <typename TA, typename TM>
+int launch_pass_k(bicadmm_ctx* h, bool wc, int op = 0, int* blocks = nullptr) {
+  switch (h->KC) {
+    case 4: return launch_pass_k_c<TA, TM, 4>(h, wc, op, blocks);
+    case 10: return launch_pass_k_c<TA, TM, 10>(h, wc, op, blocks);
+    case 16: return launch_pass_k_c<TA, TM, 16>(h, wc, op, blocks);
+  }
+  return fail(h, BICADMM_ERR_UNSUPPORTED, "no softmax A-pass variant for this class count");
+}
+
+// Launch the A pass for the handle's precision and class count.
+int launch_pass_any(bicadmm_ctx* h, bool last) {
+  const bool mc = h->K > 1;
+  switch (h->p.precision) {
+    case BICADMM_PREC_FP64: return mc ? launch_pass_k<double, double>(h, last) : launch_pass<double, double>(h, last);
+    case BICADMM_PREC_FP32: return mc ? launch_pass_k<float, float>(h, last) : launch_pass<float, float>(h, last);
+    default: return mc ? launch_pass_k<__nv_bfloat16, float>(h, last) : launch_pass<__nv_bfloat16, float>(h, last);
+  }
+}
+
 template <typename TA, typename TM, int R, int VPT>
 int occupancy_rv(bicadmm_ctx* h, int* blocks) {
   auto kern = k_fused_pass<TA, TM, R, VPT, kPassThreads>;
@@ -246,6 +315,16 @@ int pick_vpt(int64_t nvec) {
   static const int opts[] = {1, 2, 3, 4, 5, 6, 8, 12, 16};
   for (int v : opts)
     if (static_cast<int64_t>(v) * kPassThreads >= nvec) return v;
+  return -1;
+}
+
+// Softmax pass: the smallest of {1, 2, 4} vectors per thread covering the row, if its
+// register tiles (VPT x VE columns x KC classes, x and Q, doubled for FP64) fit.
+int pick_vpt_k(int64_t nvec, int ve, int kc, size_t tm_bytes) {
+  static const int opts[] = {1, 2, 4};
+  for (int v : opts)
+    if (static_cast<int64_t>(v) * kPassThreads >= nvec)
+      return v * ve * kc * (tm_bytes == 8 ? 2 : 1) <= 80 ? v : -1;
   return -1;
 }
 
@@ -281,7 +360,7 @@ int prof_end(bicadmm_ctx* h, int kind) {
 template <typename TM>
 int run_iterations(bicadmm_ctx* h, int n_iters) {
   const int N = h->N, M = h->M;
-  const int64_t lda = h->lda, n = h->p.n;
+  const int64_t lda = h->ldx, n = h->p.n * h->K;
   const dim3 rhs_grid(static_cast<unsigned>((lda + 255) / 256), N);
   const dim3 xupd_grid(static_cast<unsigned>((h->max_nj + kXupdRows - 1) / kXupdRows), M, N);
   const size_t xupd_smem = static_cast<size_t>(h->max_ldp) * sizeof(TM);
@@ -300,15 +379,25 @@ int run_iterations(bicadmm_ctx* h, int n_iters) {
         h->launches += 1;
       }
       if ((rc = prof_begin(h, KIND_XUPD)) != BICADMM_OK) return rc;
-      k_xupd<TM, TM, kXupdThreads, kXupdRows><<<xupd_grid, kXupdThreads, xupd_smem, h->stream>>>(
-          static_cast<const TM*>(h->Pm), h->d_P_off, h->d_blk_col0, h->d_blk_ldp, h->r, h->x,
-          static_cast<TM*>(h->xlo), M, lda);
+      if (h->K == 1) {
+        k_xupd<TM, TM, kXupdThreads, kXupdRows><<<xupd_grid, kXupdThreads, xupd_smem, h->stream>>>(
+            static_cast<const TM*>(h->Pm), h->d_P_off, h->d_blk_col0, h->d_blk_ldp, h->r, h->x,
+            static_cast<TM*>(h->xlo), M, lda);
+      } else {
+        const size_t sm = static_cast<size_t>(h->max_ldp) * h->KC * sizeof(TM);
+#define XUPD_K(KCV)                                                                                 \
+  k_xupd_k<TM, KCV, kXupdThreads, kXupdRows><<<xupd_grid, kXupdThreads, sm, h->stream>>>(          \
+      static_cast<const TM*>(h->Pm), h->d_P_off, h->d_blk_col0, h->d_blk_ldp, h->r, h->x,         \
+      static_cast<TM*>(h->xlo), M, lda, h->K)
+        if (h->KC == 4) XUPD_K(4); else if (h->KC == 10) XUPD_K(10); else XUPD_K(16);
+#undef XUPD_K
+      }
+      CK(cudaGetLastError());
       if ((rc = prof_end(h, KIND_XUPD)) != BICADMM_OK) return rc;
       if ((rc = prof_begin(h, KIND_PASS)) != BICADMM_OK) return rc;
       // The last sweep's pass also runs the global step in its spare CTA.
       const bool last = jj == h->p.inner_iters - 1;
-      rc = (h->p.precision == BICADMM_PREC_FP64) ? launch_pass<double, double>(h, last)
-                                                  : launch_pass<float, float>(h, last);
+      rc = launch_pass_any(h, last);
       if (rc != BICADMM_OK) return rc;
       if ((rc = prof_end(h, KIND_PASS)) != BICADMM_OK) return rc;
       h->launches += 2;
@@ -337,6 +426,7 @@ int check_device_error(bicadmm_ctx* h) {
     case DEV_NONPOS_PIVOT: return fail(h, BICADMM_ERR_NUMERIC, "non-positive pivot in a block factorisation");
     case DEV_NONFINITE: return fail(h, BICADMM_ERR_NUMERIC, "non-finite residual (NaN/Inf in the iterates)");
     case DEV_ZT_NOCONV: return fail(h, BICADMM_ERR_NUMERIC, "(z,t) root iteration did not terminate");
+    case DEV_BAD_LABEL: return fail(h, BICADMM_ERR_ARG, "softmax labels must be integers in [0, K)");
   }
   return fail(h, BICADMM_ERR_CUDA, "unknown device error " + std::to_string(e));
 }
@@ -366,18 +456,17 @@ int fill_info(bicadmm_ctx* h, bicadmm_info* info) {
 
 int validate(const bicadmm_params* p, std::string& why) {
   if (!p) { why = "params is NULL"; return BICADMM_ERR_ARG; }
-  if (p->loss == BICADMM_LOSS_SOFTMAX) { why = "softmax loss is not supported by this build"; return BICADMM_ERR_UNSUPPORTED; }
-  if (p->loss != BICADMM_LOSS_SQUARED && p->loss != BICADMM_LOSS_LOGISTIC && p->loss != BICADMM_LOSS_SQHINGE) { why = "unknown loss"; return BICADMM_ERR_ARG; }
-  if (p->precision != BICADMM_PREC_FP64 && p->precision != BICADMM_PREC_FP32) { why = "unknown precision"; return BICADMM_ERR_ARG; }
+  if (p->loss != BICADMM_LOSS_SQUARED && p->loss != BICADMM_LOSS_LOGISTIC && p->loss != BICADMM_LOSS_SQHINGE && p->loss != BICADMM_LOSS_SOFTMAX) { why = "unknown loss"; return BICADMM_ERR_ARG; }
+  if (p->precision != BICADMM_PREC_FP64 && p->precision != BICADMM_PREC_FP32 && p->precision != BICADMM_PREC_BF16) { why = "unknown precision"; return BICADMM_ERR_ARG; }
   if (p->m < 1 || p->n < 1) { why = "m and n must be >= 1"; return BICADMM_ERR_ARG; }
-  if (p->K != 1) { why = "K must be 1 for the supported losses"; return BICADMM_ERR_ARG; }
+  if (p->loss == BICADMM_LOSS_SOFTMAX ? (p->K < 2 || p->K > 16) : p->K != 1) { why = "K must be 2..16 for softmax and 1 otherwise"; return BICADMM_ERR_ARG; }
   if (p->N_shards < 1 || p->N_shards > p->m) { why = "need 1 <= N_shards <= m"; return BICADMM_ERR_ARG; }
   if (p->M_blocks < 1 || p->M_blocks > p->n) { why = "need 1 <= M_blocks <= n"; return BICADMM_ERR_ARG; }
-  if (p->kappa < 1 || p->kappa > p->n) { why = "need 1 <= kappa <= n"; return BICADMM_ERR_ARG; }
+  if (p->kappa < 1 || p->kappa > p->n * p->K) { why = "need 1 <= kappa <= n K"; return BICADMM_ERR_ARG; }
   if (!(p->gamma > 0) || !(p->rho_c > 0) || !(p->rho_b >= 0) || !(p->rho_l >= 0)) { why = "gamma, rho_c must be > 0 and rho_b, rho_l >= 0"; return BICADMM_ERR_ARG; }
   if (p->inner_iters < 1 || p->newton_iters < 1) { why = "inner_iters and newton_iters must be >= 1"; return BICADMM_ERR_ARG; }
   if (p->max_iters < 0 || p->check_every < 1) { why = "max_iters >= 0 and check_every >= 1 required"; return BICADMM_ERR_ARG; }
-  if (p->n > kMaxN) { why = "n > 32768 is not supported by this build"; return BICADMM_ERR_UNSUPPORTED; }
+  if (p->n * p->K > kMaxN) { why = "n K > 32768 is not supported by this build"; return BICADMM_ERR_UNSUPPORTED; }
   if (p->pass_rows != 0 && p->pass_rows != 1 && p->pass_rows != 2 && p->pass_rows != 4 && p->pass_rows != 8) { why = "pass_rows must be 0, 1, 2, 4 or 8"; return BICADMM_ERR_ARG; }
   if (p->pass_stages < 0 || p->pass_stages > 8) { why = "pass_stages must be in [0, 8]"; return BICADMM_ERR_ARG; }
   return BICADMM_OK;
@@ -388,7 +477,11 @@ int build_geometry(bicadmm_ctx* h) {
   h->N = p.N_shards;
   h->M = p.M_blocks;
   h->esz = p.precision == BICADMM_PREC_FP64 ? 8 : 4;
+  h->asz = p.precision == BICADMM_PREC_FP64 ? 8 : (p.precision == BICADMM_PREC_BF16 ? 2 : 4);
   h->lda = round_up(p.n, 32);
+  h->K = static_cast<int>(p.K);
+  h->KC = h->K == 1 ? 1 : (h->K <= 4 ? 4 : (h->K <= 10 ? 10 : 16));
+  h->ldx = h->lda * h->K;
   h->c0 = 1.0 / (h->N * p.gamma) + p.rho_c;
   // shards / blocks: contiguous, first (total mod parts) one longer
   h->shard_row0.assign(h->N + 1, 0);
@@ -420,8 +513,14 @@ int build_geometry(bicadmm_ctx* h) {
   h->P_total = po;
 
   // A-pass panel geometry
-  const size_t row_bytes = static_cast<size_t>(h->lda) * h->esz;
+  const size_t row_bytes = static_cast<size_t>(h->lda) * h->asz;
   int R = p.pass_rows;
+  if (h->K > 1) {
+    // Softmax pass: one CTA per SM (register tiles), 8-row panels, up to 4 stages in the
+    // single-CTA budget.
+    if (R != 0 && R != kPassRowsK) return fail(h, BICADMM_ERR_UNSUPPORTED, "the softmax A pass uses 8-row panels (pass_rows 0 or 8)");
+    R = kPassRowsK;
+  }
   // Auto: the tallest panel (<= 48 KB) of which two stages fit a two-CTA-per-SM budget, and
   // up to four stages in that budget (one stage if a single row exceeds it).
   if (R == 0) {
@@ -432,7 +531,7 @@ int build_geometry(bicadmm_ctx* h) {
   }
   int S = p.pass_stages;
   if (S == 0) {
-    const size_t budget = 2 * R * row_bytes <= kPassCtaTarget ? kPassCtaTarget : kPassSmemBudget;
+    const size_t budget = h->K == 1 && 2 * R * row_bytes <= kPassCtaTarget ? kPassCtaTarget : kPassSmemBudget;
     S = static_cast<int>(std::min<size_t>(4, budget / (R * row_bytes)));
     if (S < 1) S = 1;
   }
@@ -440,11 +539,18 @@ int build_geometry(bicadmm_ctx* h) {
     return fail(h, BICADMM_ERR_UNSUPPORTED, "A-pass stages do not fit in shared memory (rows too wide)");
   h->R = R;
   h->S = S;
-  const int64_t nvec = h->lda / (h->esz == 8 ? 2 : 4);
-  h->VPT = pick_vpt(nvec);
+  const int ve = static_cast<int>(16 / h->asz);
+  const int64_t nvec = h->lda / ve;
+  h->VPT = h->K == 1 ? pick_vpt(nvec) : pick_vpt_k(nvec, ve, h->KC, h->esz);
   if (h->VPT < 0) return fail(h, BICADMM_ERR_UNSUPPORTED, "rows too wide for the register-resident A-pass accumulators");
-  h->pass_smem = h->esz == 8 ? fused_pass_smem<double, double>(R, S, h->lda, kPassThreads)
-                             : fused_pass_smem<float, float>(R, S, h->lda, kPassThreads);
+  if (h->K > 1) {
+    const int C = h->KC <= 4 ? 4 : 16;
+    h->pass_smem = static_cast<size_t>(S) * R * row_bytes + S * sizeof(uint64_t) +
+                   static_cast<size_t>(R) * (kPassThreads / 32 + 1) * C * h->esz + 16;
+  } else {
+    h->pass_smem = static_cast<size_t>(S) * R * row_bytes + S * sizeof(uint64_t) +
+                   static_cast<size_t>(R) * (kPassThreads / 32 + 1) * h->esz + 16;
+  }
   h->panel_start.assign(h->N + 1, 0);
   for (int i = 0; i < h->N; ++i) {
     const int64_t mi = h->shard_row0[i + 1] - h->shard_row0[i];
@@ -452,7 +558,20 @@ int build_geometry(bicadmm_ctx* h) {
   }
   h->P_panels = h->panel_start[h->N];
   int occ = 0;
-  int rc = h->esz == 8 ? pass_occupancy<double, double>(h, &occ) : pass_occupancy<float, float>(h, &occ);
+  int rc;
+  if (h->K > 1) {
+    switch (h->p.precision) {
+      case BICADMM_PREC_FP64: rc = launch_pass_k<double, double>(h, false, 1, &occ); break;
+      case BICADMM_PREC_FP32: rc = launch_pass_k<float, float>(h, false, 1, &occ); break;
+      default: rc = launch_pass_k<__nv_bfloat16, float>(h, false, 1, &occ); break;
+    }
+  } else {
+    switch (h->p.precision) {
+      case BICADMM_PREC_FP64: rc = pass_occupancy<double, double>(h, &occ); break;
+      case BICADMM_PREC_FP32: rc = pass_occupancy<float, float>(h, &occ); break;
+      default: rc = pass_occupancy<__nv_bfloat16, float>(h, &occ); break;
+    }
+  }
   if (rc != BICADMM_OK) return rc;
   if (occ < 1) return fail(h, BICADMM_ERR_UNSUPPORTED, "A-pass variant cannot be resident on an SM");
   // One resident slot is kept for the consensus CTA that rides on the last pass.
@@ -474,20 +593,20 @@ int build_geometry(bicadmm_ctx* h) {
     h->slot_hi[i] = owner(h->panel_start[i + 1] - 1) + i;
   }
   h->nslots = h->G + h->N;
-  h->dual_chunks = static_cast<int>((h->lda + kDualThreads - 1) / kDualThreads);
+  h->dual_chunks = static_cast<int>((h->ldx + kDualThreads - 1) / kDualThreads);
   return BICADMM_OK;
 }
 
 // Device bytes a handle allocates (including the polish buffers of one polished get_x),
 // and the extra bytes its setup holds temporarily.
 void handle_bytes(const bicadmm_ctx* h, int64_t* persistent, int64_t* setup_extra) {
-  const int64_t m = h->p.m, lda = h->lda, N = h->N, kappa = h->p.kappa;
-  const int64_t es = static_cast<int64_t>(h->esz);
+  const int64_t m = h->p.m, lda = h->lda, ldx = h->ldx, N = h->N, kappa = h->p.kappa;
+  const int64_t es = static_cast<int64_t>(h->esz), as = static_cast<int64_t>(h->asz);
   int64_t b = 0;
-  b += m * lda * es + 3 * m * es;                        // A, b, omega, nu
-  b += static_cast<int64_t>(h->nslots) * lda * es;       // slots
-  b += N * lda * es + h->P_total * es;                   // xlo, P
-  b += 3 * N * lda * 8 + 7 * lda * 8;                    // x, u, r; z, s, w, tau_r, c, e, key
+  b += m * lda * as + m * es + 2 * m * h->K * es;       // A, b, omega, nu
+  b += static_cast<int64_t>(h->nslots) * ldx * es;      // slots
+  b += N * ldx * es + h->P_total * es;                  // xlo, P
+  b += 3 * N * ldx * 8 + 7 * ldx * 8;                   // x, u, r; z, s, w, tau_r, c, e, key
   b += static_cast<int64_t>(h->G) * 32 + N * h->dual_chunks * 16 + 4096 * 112 + 4096;
   // polish: supp, A_S, q, d1, d2, p, x_S, step, partials, H
   b += kappa * 8 + kappa * m * 8 + 4 * m * 8 + 2 * kappa * 8 + kPolishRowBlocks * 8 +
@@ -497,14 +616,14 @@ void handle_bytes(const bicadmm_ctx* h, int64_t* persistent, int64_t* setup_extr
 }
 
 int allocate(bicadmm_ctx* h) {
-  const int64_t m = h->p.m, lda = h->lda, N = h->N;
+  const int64_t m = h->p.m, lda = h->ldx, N = h->N;  // n-space arrays use the stride lda K
   const size_t es = h->esz;
   int rc;
 #define AL(ptr, bytes) if ((rc = dev_alloc(h, &(ptr), (bytes))) != BICADMM_OK) return rc
-  AL(h->A, static_cast<size_t>(m) * lda * es);
+  AL(h->A, static_cast<size_t>(m) * h->lda * h->asz);
   AL(h->b, m * es);
-  AL(h->omega, m * es);
-  AL(h->nu, m * es);
+  AL(h->omega, m * h->K * es);
+  AL(h->nu, m * h->K * es);
   AL(h->slots, static_cast<size_t>(h->nslots) * lda * es);
   AL(h->xlo, static_cast<size_t>(N) * lda * es);
   AL(h->Pm, static_cast<size_t>(h->P_total) * es);
@@ -548,10 +667,10 @@ int allocate(bicadmm_ctx* h) {
 }
 
 int reset_state(bicadmm_ctx* h) {
-  const int64_t m = h->p.m, lda = h->lda, N = h->N;
+  const int64_t m = h->p.m, lda = h->ldx, N = h->N;
   const size_t es = h->esz;
-  CK(cudaMemsetAsync(h->omega, 0, m * es, h->stream));
-  CK(cudaMemsetAsync(h->nu, 0, m * es, h->stream));
+  CK(cudaMemsetAsync(h->omega, 0, m * h->K * es, h->stream));
+  CK(cudaMemsetAsync(h->nu, 0, m * h->K * es, h->stream));
   CK(cudaMemsetAsync(h->slots, 0, static_cast<size_t>(h->nslots) * lda * es, h->stream));
   CK(cudaMemsetAsync(h->xlo, 0, static_cast<size_t>(N) * lda * es, h->stream));
   CK(cudaMemsetAsync(h->x, 0, N * lda * sizeof(double), h->stream));
@@ -573,12 +692,14 @@ int reset_state(bicadmm_ctx* h) {
 template <typename TOUT>
 int load_matrix(bicadmm_ctx* h, const void* src, int dtype, int64_t lda_src, int on_device,
                 TOUT* dst, int64_t rows, int64_t cols, int64_t lda_dst) {
-  const size_t in_es = dtype == BICADMM_DTYPE_F64 ? 8 : 4;
+  const size_t in_es = dtype == BICADMM_DTYPE_F64 ? 8 : (dtype == BICADMM_DTYPE_BF16 ? 2 : 4);
   auto convert = [&](const void* s, TOUT* d, int64_t nr) -> int {
     const int64_t total = nr * lda_dst;
     const unsigned grid = static_cast<unsigned>(std::min<int64_t>((total + 255) / 256, 65535));
     if (dtype == BICADMM_DTYPE_F64)
       k_convert_rows<double, TOUT><<<grid, 256, 0, h->stream>>>(static_cast<const double*>(s), lda_src, d, lda_dst, nr, cols);
+    else if (dtype == BICADMM_DTYPE_BF16)
+      k_convert_rows<__nv_bfloat16, TOUT><<<grid, 256, 0, h->stream>>>(static_cast<const __nv_bfloat16*>(s), lda_src, d, lda_dst, nr, cols);
     else
       k_convert_rows<float, TOUT><<<grid, 256, 0, h->stream>>>(static_cast<const float*>(s), lda_src, d, lda_dst, nr, cols);
     CK(cudaGetLastError());
@@ -612,7 +733,18 @@ int load_matrix(bicadmm_ctx* h, const void* src, int dtype, int64_t lda_src, int
   return rc;
 }
 
-template <typename TA>
+// Softmax: every b_r must be an integral class index in [0, K).
+template <typename TM>
+int check_labels(bicadmm_ctx* h) {
+  if (h->K == 1) return BICADMM_OK;
+  const unsigned grid = static_cast<unsigned>(std::min<int64_t>((h->p.m + 255) / 256, 4096));
+  k_check_labels<TM><<<grid, 256, 0, h->stream>>>(static_cast<const TM*>(h->b), h->p.m, h->K, h->d_err);
+  CK(cudaGetLastError());
+  h->launches += 1;
+  return check_device_error(h);
+}
+
+template <typename TA, typename TM>
 int build_factors(bicadmm_ctx* h) {
   double* G = nullptr;
   cudaError_t e = cudaMalloc(&G, std::max<int64_t>(h->G_total, 1) * sizeof(double));
@@ -621,7 +753,7 @@ int build_factors(bicadmm_ctx* h) {
   int rc = BICADMM_OK;
   const int T = (h->max_nj + 63) / 64;
   const dim3 ggrid(T * (T + 1) / 2, h->M, h->N);
-  k_gram<TA, TA><<<ggrid, 256, 0, h->stream>>>(static_cast<const TA*>(h->A), h->lda, h->d_shard_row0,
+  k_gram<TA, TM><<<ggrid, 256, 0, h->stream>>>(static_cast<const TA*>(h->A), h->lda, h->d_shard_row0,
                                                h->d_blk_col0, G, h->d_G_off, h->M);
   h->launches += 1;
   e = cudaGetLastError();
@@ -640,12 +772,12 @@ int build_factors(bicadmm_ctx* h) {
     // one warp per column; as many warps as fit 200 KB of column vectors (at most 8)
     const int warps = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(8, (200 << 10) / (8 * h->max_nj))));
     const size_t sm = static_cast<size_t>(warps) * h->max_nj * sizeof(double);
-    auto ki = k_inv_cols<TA>;
+    auto ki = k_inv_cols<TM>;
     if (sm > 48 * 1024) e = cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
     if (e == cudaSuccess) {
       const dim3 grid(h->N * h->M, (h->max_nj + warps - 1) / warps);
       ki<<<grid, 32 * warps, sm, h->stream>>>(G, h->d_G_off, h->d_blk_col0, h->d_blk_ldp, h->M,
-                                              static_cast<TA*>(h->Pm), h->d_P_off);
+                                              static_cast<TM*>(h->Pm), h->d_P_off);
       h->launches += 1;
       e = cudaGetLastError();
     }
@@ -665,7 +797,7 @@ int compute_support(bicadmm_ctx* h) {
     int rc = dev_alloc(h, &h->supp, h->p.kappa * sizeof(int64_t));
     if (rc != BICADMM_OK) return rc;
   }
-  k_support<1024, 1><<<1, 1024, 0, h->stream>>>(h->z, h->key, h->p.n, h->p.kappa, h->supp);
+  k_support<1024, 1><<<1, 1024, 0, h->stream>>>(h->z, h->key, h->p.n * h->K, h->p.kappa, h->supp);
   CK(cudaGetLastError());
   h->launches += 1;
   return BICADMM_OK;
@@ -1127,21 +1259,28 @@ int bicadmm_setup(bicadmm_t h, const void* A, int32_t A_dtype, int64_t lda, int3
                   const void* b, int32_t b_dtype, int32_t b_on_device) {
   if (!h) return BICADMM_ERR_ARG;
   if (!A || !b) return fail(h, BICADMM_ERR_ARG, "A and b must be non-NULL");
-  if (A_dtype != BICADMM_DTYPE_F64 && A_dtype != BICADMM_DTYPE_F32) return fail(h, BICADMM_ERR_ARG, "A_dtype must be F64 or F32");
+  if (A_dtype != BICADMM_DTYPE_F64 && A_dtype != BICADMM_DTYPE_F32 && A_dtype != BICADMM_DTYPE_BF16) return fail(h, BICADMM_ERR_ARG, "A_dtype must be F64, F32 or BF16");
   if (b_dtype != BICADMM_DTYPE_F64 && b_dtype != BICADMM_DTYPE_F32) return fail(h, BICADMM_ERR_ARG, "b_dtype must be F64 or F32");
   if (lda < h->p.n) return fail(h, BICADMM_ERR_ARG, "lda must be >= n");
   h->ready = false;
   h->err.clear();
   int rc = reset_state(h);
   if (rc != BICADMM_OK) return rc;
-  if (h->esz == 8) {
+  if (h->p.precision == BICADMM_PREC_FP64) {
     rc = load_matrix<double>(h, A, A_dtype, lda, A_on_device, static_cast<double*>(h->A), h->p.m, h->p.n, h->lda);
     if (rc == BICADMM_OK) rc = load_matrix<double>(h, b, b_dtype, 1, b_on_device, static_cast<double*>(h->b), h->p.m, 1, 1);
-    if (rc == BICADMM_OK) rc = build_factors<double>(h);
-  } else {
+    if (rc == BICADMM_OK) rc = check_labels<double>(h);
+    if (rc == BICADMM_OK) rc = build_factors<double, double>(h);
+  } else if (h->p.precision == BICADMM_PREC_FP32) {
     rc = load_matrix<float>(h, A, A_dtype, lda, A_on_device, static_cast<float*>(h->A), h->p.m, h->p.n, h->lda);
     if (rc == BICADMM_OK) rc = load_matrix<float>(h, b, b_dtype, 1, b_on_device, static_cast<float*>(h->b), h->p.m, 1, 1);
-    if (rc == BICADMM_OK) rc = build_factors<float>(h);
+    if (rc == BICADMM_OK) rc = check_labels<float>(h);
+    if (rc == BICADMM_OK) rc = build_factors<float, float>(h);
+  } else {
+    rc = load_matrix<__nv_bfloat16>(h, A, A_dtype, lda, A_on_device, static_cast<__nv_bfloat16*>(h->A), h->p.m, h->p.n, h->lda);
+    if (rc == BICADMM_OK) rc = load_matrix<float>(h, b, b_dtype, 1, b_on_device, static_cast<float*>(h->b), h->p.m, 1, 1);
+    if (rc == BICADMM_OK) rc = check_labels<float>(h);
+    if (rc == BICADMM_OK) rc = build_factors<__nv_bfloat16, float>(h);
   }
   if (rc != BICADMM_OK) return rc;
   h->ready = true;
@@ -1183,18 +1322,23 @@ int bicadmm_solve(bicadmm_t h, bicadmm_info* info) {
 int bicadmm_get_x(bicadmm_t h, double* x_host, int64_t len, int32_t polished, int64_t* support_out) {
   if (!h) return BICADMM_ERR_ARG;
   if (!h->ready) return fail(h, BICADMM_ERR_STATE, "bicadmm_get_x before setup");
-  if (!x_host || len != h->p.n) return fail(h, BICADMM_ERR_ARG, "x_host must hold n doubles");
+  const int64_t nK = h->p.n * h->K;
+  if (!x_host || len != nK) return fail(h, BICADMM_ERR_ARG, "x_host must hold n K doubles");
   if (polished && h->p.kappa > kMaxPolishKappa)
     return fail(h, BICADMM_ERR_UNSUPPORTED, "polish supports kappa <= 1024");
+  if (polished && h->K > 1)
+    return fail(h, BICADMM_ERR_UNSUPPORTED, "polish is not implemented for the softmax loss");
   if (!polished) {
-    CK(cudaMemcpyAsync(x_host, h->z, h->p.n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(x_host, h->z, nK * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     if (support_out) {
       int rc = compute_support(h);
       if (rc != BICADMM_OK) return rc;
     }
   } else {
     std::vector<double> xs;
-    int rc = h->esz == 8 ? run_polish<double, double>(h, xs) : run_polish<float, float>(h, xs);
+    int rc = h->p.precision == BICADMM_PREC_FP64 ? run_polish<double, double>(h, xs)
+             : h->p.precision == BICADMM_PREC_FP32 ? run_polish<float, float>(h, xs)
+                                                   : run_polish<__nv_bfloat16, float>(h, xs);
     if (rc != BICADMM_OK) return rc;
     std::vector<int64_t> sp(h->p.kappa);
     CK(cudaMemcpyAsync(sp.data(), h->supp, h->p.kappa * sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
@@ -1211,26 +1355,26 @@ int bicadmm_get_x(bicadmm_t h, double* x_host, int64_t len, int32_t polished, in
 int bicadmm_get_state(bicadmm_t h, int32_t field, double* out_host, int64_t len) {
   if (!h) return BICADMM_ERR_ARG;
   if (!out_host) return fail(h, BICADMM_ERR_ARG, "out_host is NULL");
-  const int64_t n = h->p.n, m = h->p.m, N = h->N;
+  const int64_t n = h->p.n * h->K, m = h->p.m * h->K, N = h->N;  // n K and m K entries
   auto need = [&](int64_t L) { return len == L; };
   switch (field) {
     case BICADMM_FIELD_X:
     case BICADMM_FIELD_U: {
-      if (!need(N * n)) return fail(h, BICADMM_ERR_ARG, "length must be N*n");
+      if (!need(N * n)) return fail(h, BICADMM_ERR_ARG, "length must be N*n*K");
       const double* src = field == BICADMM_FIELD_X ? h->x : h->u;
-      CK(cudaMemcpy2DAsync(out_host, n * sizeof(double), src, h->lda * sizeof(double), n * sizeof(double), N,
+      CK(cudaMemcpy2DAsync(out_host, n * sizeof(double), src, h->ldx * sizeof(double), n * sizeof(double), N,
                            cudaMemcpyDeviceToHost, h->stream));
       break;
     }
     case BICADMM_FIELD_Z:
     case BICADMM_FIELD_S:
-      if (!need(n)) return fail(h, BICADMM_ERR_ARG, "length must be n");
+      if (!need(n)) return fail(h, BICADMM_ERR_ARG, "length must be n*K");
       CK(cudaMemcpyAsync(out_host, field == BICADMM_FIELD_Z ? h->z : h->s, n * sizeof(double),
                          cudaMemcpyDeviceToHost, h->stream));
       break;
     case BICADMM_FIELD_OMEGA:
     case BICADMM_FIELD_NU: {
-      if (!need(m)) return fail(h, BICADMM_ERR_ARG, "length must be m");
+      if (!need(m)) return fail(h, BICADMM_ERR_ARG, "length must be m*K");
       const void* src = field == BICADMM_FIELD_OMEGA ? h->omega : h->nu;
       if (h->esz == 8) {
         CK(cudaMemcpyAsync(out_host, src, m * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -1333,6 +1477,7 @@ int bicadmm_batch_create(bicadmm_t* handles, int32_t count, void* stream, int32_
     bicadmm_t h = handles[q];
     if (!h || !h->ready) { g_create_error = "every handle must be set up"; return BICADMM_ERR_STATE; }
     if (h->esz != handles[0]->esz || h->device != handles[0]->device) { g_create_error = "handles must share precision and device"; return BICADMM_ERR_ARG; }
+    if (h->K != 1 || h->p.precision == BICADMM_PREC_BF16) { g_create_error = "batches take FP64 or FP32 handles with K = 1"; return BICADMM_ERR_UNSUPPORTED; }
     if (h->p.inner_iters != 1) { g_create_error = "batched handles must use inner_iters = 1"; return BICADMM_ERR_UNSUPPORTED; }
     for (int q2 = 0; q2 < q; ++q2)
       if (handles[q2] == h) { g_create_error = "a handle appears twice"; return BICADMM_ERR_ARG; }
@@ -1648,6 +1793,7 @@ int bicadmm_server_submit(bicadmm_server_t s, const bicadmm_params* p, const voi
   if (!p || !A || !b || !id_out) return sfail(s, BICADMM_ERR_ARG, "p, A, b and id_out are required");
   if (p->precision != s->sp.precision) return sfail(s, BICADMM_ERR_ARG, "request precision differs from the server's");
   if (p->inner_iters != 1) return sfail(s, BICADMM_ERR_UNSUPPORTED, "served requests use inner_iters = 1");
+  if (p->K != 1 || p->precision == BICADMM_PREC_BF16) return sfail(s, BICADMM_ERR_UNSUPPORTED, "served requests are FP64 or FP32 with K = 1");
   ServerReq r;
   r.p = *p;
   r.A = A;

@@ -2,6 +2,7 @@
 // reductions, and the PTX wrappers for mbarriers and bulk (TMA) copies.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -14,6 +15,7 @@ enum DevErr : int {
   DEV_NONPOS_PIVOT = 2,    // Cholesky met a non-positive pivot
   DEV_NONFINITE = 3,       // NaN/Inf in a residual
   DEV_ZT_NOCONV = 4,       // (z,t) root iteration exceeded its bound
+  DEV_BAD_LABEL = 5,       // a softmax label is not an integer in [0, K)
 };
 
 // Upper bound on any single spin-wait, in SM clock cycles (about 2 s at 2 GHz).
@@ -25,6 +27,37 @@ __device__ __forceinline__ void set_err(int* err, int code) { atomicCAS(err, 0, 
 template <typename T> struct Vec16;
 template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
 template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+template <> struct Vec16<__nv_bfloat16> { using type = uint4; static constexpr int n = 8; };
+
+// Element conversion between the stored A type and the arithmetic types (to BF16: round
+// to nearest even).
+template <typename TO, typename TI> __device__ __forceinline__ TO conv(TI v) { return static_cast<TO>(v); }
+template <> __device__ __forceinline__ float conv<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <> __device__ __forceinline__ double conv<double, __nv_bfloat16>(__nv_bfloat16 v) { return static_cast<double>(__bfloat162float(v)); }
+template <> __device__ __forceinline__ __nv_bfloat16 conv<__nv_bfloat16, double>(double v) { return __double2bfloat16(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 conv<__nv_bfloat16, float>(float v) { return __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 conv<__nv_bfloat16, __nv_bfloat16>(__nv_bfloat16 v) { return v; }
+
+// Reduce-scatter of C values (C a power of two <= 32) across a warp: on return lane l
+// holds the warp-wide sum of v[(l >> (5 - log2 C)) & (C - 1)] (v is clobbered).  Costs
+// C - 1 + 5 - log2 C shuffles instead of 5 C for C separate butterflies.
+template <int C, typename T>
+__device__ __forceinline__ T warp_reduce_scatter(T (&v)[C], int lane) {
+#pragma unroll
+  for (int c = C, o = 16; c > 1; c >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < c / 2; ++i) {
+      const T send = up ? v[i] : v[i + c / 2];
+      const T keep = up ? v[i + c / 2] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  T s = v[0];
+#pragma unroll
+  for (int o = 16 / C; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {

@@ -30,10 +30,12 @@ template <typename T> struct FpLim;
 template <> struct FpLim<float> {
   static constexpr float eps = 1.1920929e-7f;
   static constexpr float tiny = 1.17549435e-38f;
+  static constexpr float big = 3.4028234e38f;
 };
 template <> struct FpLim<double> {
   static constexpr double eps = 2.220446049250313e-16;
   static constexpr double tiny = 2.2250738585072014e-308;
+  static constexpr double big = 1.7976931348623157e308;
 };
 
 template <typename T> __device__ __forceinline__ T dev_exp(T x);
@@ -113,7 +115,7 @@ constexpr int kConsMW = 4;
 
 template <typename TA, typename TM, int R, int VPT, int NT>
 __global__ void __launch_bounds__(NT, 1)
-k_fused_pass(const TA* __restrict__ A, int64_t lda, const TA* __restrict__ xlo,
+k_fused_pass(const TA* __restrict__ A, int64_t lda, const TM* __restrict__ xlo,
              const TM* __restrict__ b, TM* __restrict__ omega, TM* __restrict__ nu,
              TM* __restrict__ slots, double* __restrict__ cta_stats, PassGeometry geo,
              int S, int loss, TM Mf, TM rho_l, int newton_iters, int* __restrict__ err,
@@ -164,7 +166,7 @@ k_fused_pass(const TA* __restrict__ A, int64_t lda, const TA* __restrict__ xlo,
     for (; n_issued < np && n_issued < S; ++n_issued) issue(n_issued);
   }
 
-  TA xr[VPT][VE];
+  TM xr[VPT][VE];
   TM acc[VPT][VE];
   int cur = -1, shard = 0;
 
@@ -189,15 +191,15 @@ k_fused_pass(const TA* __restrict__ A, int64_t lda, const TA* __restrict__ xlo,
     if (shard != cur) {
       if (cur >= 0) flush(cur);
       cur = shard;
-      const V* xv = reinterpret_cast<const V*>(xlo + static_cast<int64_t>(shard) * lda);
+      const TM* xs = xlo + static_cast<int64_t>(shard) * lda;
 #pragma unroll
       for (int kk = 0; kk < VPT; ++kk) {
         const int64_t v = tid + static_cast<int64_t>(kk) * NT;
-        V t;
-        if (v < nvec) t = xv[v]; else t = V{};
-        const TA* te = reinterpret_cast<const TA*>(&t);
 #pragma unroll
-        for (int e = 0; e < VE; ++e) { xr[kk][e] = te[e]; acc[kk][e] = TM(0); }
+        for (int e = 0; e < VE; ++e) {
+          xr[kk][e] = v < nvec ? xs[v * VE + e] : TM(0);
+          acc[kk][e] = TM(0);
+        }
       }
     }
     // Per-row scalars for the epilogue (the previous omega warm-starts the prox).
@@ -235,7 +237,7 @@ k_fused_pass(const TA* __restrict__ A, int64_t lda, const TA* __restrict__ xlo,
             const V a = sv[r * nvec + v];
             const TA* ae = reinterpret_cast<const TA*>(&a);
 #pragma unroll
-            for (int e = 0; e < VE; ++e) dot[r] = fma(TM(ae[e]), TM(xr[kk][e]), dot[r]);
+            for (int e = 0; e < VE; ++e) dot[r] = fma(conv<TM>(ae[e]), xr[kk][e], dot[r]);
           }
         }
       }
@@ -292,7 +294,7 @@ k_fused_pass(const TA* __restrict__ A, int64_t lda, const TA* __restrict__ xlo,
             const V a = sv[r * nvec + v];
             const TA* ae = reinterpret_cast<const TA*>(&a);
 #pragma unroll
-            for (int e = 0; e < VE; ++e) acc[kk][e] = fma(dr[r], TM(ae[e]), acc[kk][e]);
+            for (int e = 0; e < VE; ++e) acc[kk][e] = fma(dr[r], conv<TM>(ae[e]), acc[kk][e]);
           }
         }
       }

@@ -80,7 +80,7 @@ __global__ void k_gather_support(const TA* __restrict__ A, int64_t lda, const in
   const int64_t col = supp[k];
   for (int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < m;
        r += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    AS[k * m + r] = static_cast<double>(A[r * lda + col]);
+    AS[k * m + r] = conv<double>(A[r * lda + col]);
 }
 
 // Per row: q = a_S . x (x: kappa doubles), loss derivatives; per-CTA partial objective.

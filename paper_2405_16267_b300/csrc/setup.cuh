@@ -15,7 +15,7 @@ __global__ void k_convert_rows(const TIN* __restrict__ src, int64_t lda_src,
   for (int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
        idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t r = idx / lda_dst, c = idx - r * lda_dst;
-    dst[idx] = c < n ? static_cast<TOUT>(src[r * lda_src + c]) : TOUT(0);
+    dst[idx] = c < n ? conv<TOUT>(src[r * lda_src + c]) : conv<TOUT>(0.0f);
   }
 }
 
@@ -51,8 +51,8 @@ k_gram(const TA* __restrict__ A, int64_t lda, const int64_t* __restrict__ shard_
       const int k = e / TILE, cc = e - k * TILE;
       const int64_t row = r0 + k;
       const int ca = ti * TILE + cc, cb = tj * TILE + cc;
-      As[k][cc] = (row < r_end && ca < nj) ? static_cast<TC>(A[row * lda + col0 + ca]) : TC(0);
-      Bs[k][cc] = (row < r_end && cb < nj) ? static_cast<TC>(A[row * lda + col0 + cb]) : TC(0);
+      As[k][cc] = (row < r_end && ca < nj) ? conv<TC>(A[row * lda + col0 + ca]) : TC(0);
+      Bs[k][cc] = (row < r_end && cb < nj) ? conv<TC>(A[row * lda + col0 + cb]) : TC(0);
     }
     __syncthreads();
 #pragma unroll 8

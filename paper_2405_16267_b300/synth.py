@@ -350,3 +350,13 @@ def device_request(spec, device="cuda", noise=0.1):
 def round_to_f32(A: np.ndarray) -> np.ndarray:
     """FP32-rounded copy of A upcast back to FP64 (the exact values an FP32 run sees)."""
     return A.astype(np.float32).astype(np.float64)
+
+
+def round_to_bf16(A: np.ndarray) -> np.ndarray:
+    """BF16-rounded copy of A (round to nearest, ties to even, from the FP32 value) upcast
+    back to FP64: the exact values a BF16-storage run sees when given FP32 or FP64 input."""
+    f = np.ascontiguousarray(A, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    r = ((u + 0x7FFF + lsb) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)

@@ -10,12 +10,12 @@ def run_gpu(P, iters, precision=bc.PREC_FP64, J=1, A=None, b=None, rho_c=None, *
     import torch
     A = P.A if A is None else A
     b = P.b if b is None else b
-    if precision == bc.PREC_FP32:
+    if precision in (bc.PREC_FP32, bc.PREC_BF16) and not isinstance(A, torch.Tensor):
         A = np.asarray(A, dtype=np.float32)
     stream = torch.cuda.current_stream()
     with bc.Solver(A, b, loss=P.loss, N=P.N, M=P.M, kappa=P.kappa, gamma=P.gamma,
                    rho_c=P.rho if rho_c is None else rho_c, inner_iters=J, precision=precision,
-                   stream=stream, **extra) as s:
+                   stream=stream, K=P.K, **extra) as s:
         info = s.step(iters)
         st = s.state()
     return st, info
@@ -25,7 +25,7 @@ def run_oracle(P, iters, J=1, A=None, b=None, rho_c=None):
     A = P.A if A is None else A
     b = P.b if b is None else b
     o = ref.BiCADMM(A, b, P.loss, P.N, P.M, P.kappa, gamma=P.gamma,
-                    rho_c=P.rho if rho_c is None else rho_c, inner_iters=J)
+                    rho_c=P.rho if rho_c is None else rho_c, inner_iters=J, K=P.K)
     o.iterate(iters)
     return o
 

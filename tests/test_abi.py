@@ -54,7 +54,7 @@ def test_struct_layouts_match_header(lib):
 @pytest.mark.parametrize("field,value,code", [
     ("m", 0, -1), ("n", 0, -1), ("kappa", 0, -1), ("kappa", 101, -1), ("N_shards", 0, -1),
     ("N_shards", 51, -1), ("M_blocks", 101, -1), ("gamma", 0.0, -1), ("rho_c", -1.0, -1),
-    ("inner_iters", 0, -1), ("K", 2, -1), ("loss", 2, -7), ("loss", 9, -1), ("precision", 5, -1),
+    ("inner_iters", 0, -1), ("K", 2, -1), ("loss", 2, -1), ("loss", 9, -1), ("precision", 5, -1),
     ("pass_rows", 3, -1), ("n", 40000, -7),
 ])
 def test_create_rejects_bad_arguments_without_gpu(lib, field, value, code):
@@ -67,6 +67,15 @@ def test_create_rejects_bad_arguments_without_gpu(lib, field, value, code):
     assert rc == code
     assert not h.value
     assert len(bc.last_error(None)) > 0
+
+
+@pytest.mark.parametrize("K,n,kappa,code", [(17, 100, 5, -1), (10, 4000, 5, -7), (10, 100, 1001, -1)])
+def test_softmax_create_checks_without_gpu(lib, K, n, kappa, code):
+    """Softmax: 2 <= K <= 16, n K <= 32768, kappa <= n K (entrywise)."""
+    p = bc.default_params(m=50, n=n, N_shards=2, M_blocks=2, kappa=kappa, loss=bc.LOSS_SOFTMAX, K=K)
+    h = ctypes.c_void_p()
+    assert lib.bicadmm_create(ctypes.byref(p), None, ctypes.byref(h)) == code
+    assert not h.value
 
 
 def test_null_handle_calls_are_safe(lib):
