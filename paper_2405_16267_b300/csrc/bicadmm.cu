@@ -27,6 +27,7 @@
 #include "nspace.cuh"
 #include "batch.cuh"
 #include "multiclass.cuh"
+#include "mc_tc.cuh"
 #include "pass.cuh"
 #include "polish.cuh"
 #include "setup.cuh"
@@ -70,6 +71,8 @@ struct bicadmm_ctx {
   int K = 1;          // classes (softmax), 1 otherwise
   int KC = 1;         // compile-time class bucket of the K > 1 kernels
   int64_t ldx = 0;    // n-space row stride, lda K
+  bool use_tc = false;  // BF16 softmax: tensor-core A pass (k_fused_pass_tc)
+  CUtensorMap tmap;     // 2D map of A (BF16, 64 x 128 boxes, 128-byte swizzle) for it
   double c0 = 0.0;
   size_t esz = 8;  // bytes per m-space / n-space low-precision element (TM)
   size_t asz = 8;  // bytes per stored A element (TA)
@@ -280,8 +283,64 @@ int launch_pass_k(bicadmm_ctx* h, bool wc, int op = 0, int* blocks = nullptr) {
   return fail(h, BICADMM_ERR_UNSUPPORTED, "no softmax A-pass variant for this class count");
 }
 
+template <int KC>
+int launch_pass_tc_c(bicadmm_ctx* h, bool with_consensus, int op, int* blocks) {
+  auto kern = k_fused_pass_tc<KC>;
+  CK(allow_max_dynamic_smem(kern));
+  if (op == 1) {
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, kTcThreads, h->pass_smem));
+    return BICADMM_OK;
+  }
+  PassGeometry geo{h->d_shard_row0, h->d_panel_start, h->N, h->P_panels};
+  kern<<<h->G + (with_consensus ? 1 : 0), kTcThreads, h->pass_smem, h->stream>>>(
+      h->tmap, h->lda, static_cast<const float*>(h->xlo), h->ldx, h->K,
+      static_cast<const float*>(h->b), static_cast<float*>(h->omega), static_cast<float*>(h->nu),
+      static_cast<float*>(h->slots), h->cta_stats, geo, static_cast<float>(h->M),
+      static_cast<float>(h->p.rho_l), h->p.newton_iters, h->d_err, kWaitLimitCycles,
+      consensus_args(h, with_consensus));
+  CK(cudaGetLastError());
+  return BICADMM_OK;
+}
+
+int launch_pass_tc(bicadmm_ctx* h, bool wc, int op = 0, int* blocks = nullptr) {
+  switch (h->KC) {
+    case 4: return launch_pass_tc_c<4>(h, wc, op, blocks);
+    case 10: return launch_pass_tc_c<10>(h, wc, op, blocks);
+    case 16: return launch_pass_tc_c<16>(h, wc, op, blocks);
+  }
+  return fail(h, BICADMM_ERR_UNSUPPORTED, "no tensor-core A-pass variant for this class count");
+}
+
+// Encode the TMA map of the BF16 A for the tensor-core pass (driver entry point fetched
+// through the runtime, so the library does not link libcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int make_tmap(bicadmm_ctx* h) {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q));
+    if (!ptr || q != cudaDriverEntryPointSuccess) return fail(h, BICADMM_ERR_CUDA, "cuTensorMapEncodeTiled not available");
+    fn = reinterpret_cast<EncodeTiledFn>(ptr);
+  }
+  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(h->lda), static_cast<cuuint64_t>(h->p.m)};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(h->lda) * 2};
+  const cuuint32_t box[2] = {64, static_cast<cuuint32_t>(kTcRows)};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(&h->tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, h->A, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(h, BICADMM_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(static_cast<int>(r)));
+  return BICADMM_OK;
+}
+
 // Launch the A pass for the handle's precision and class count.
 int launch_pass_any(bicadmm_ctx* h, bool last) {
+  if (h->use_tc) return launch_pass_tc(h, last);
   const bool mc = h->K > 1;
   switch (h->p.precision) {
     case BICADMM_PREC_FP64: return mc ? launch_pass_k<double, double>(h, last) : launch_pass<double, double>(h, last);
@@ -467,7 +526,7 @@ int validate(const bicadmm_params* p, std::string& why) {
   if (p->inner_iters < 1 || p->newton_iters < 1) { why = "inner_iters and newton_iters must be >= 1"; return BICADMM_ERR_ARG; }
   if (p->max_iters < 0 || p->check_every < 1) { why = "max_iters >= 0 and check_every >= 1 required"; return BICADMM_ERR_ARG; }
   if (p->n * p->K > kMaxN) { why = "n K > 32768 is not supported by this build"; return BICADMM_ERR_UNSUPPORTED; }
-  if (p->pass_rows != 0 && p->pass_rows != 1 && p->pass_rows != 2 && p->pass_rows != 4 && p->pass_rows != 8) { why = "pass_rows must be 0, 1, 2, 4 or 8"; return BICADMM_ERR_ARG; }
+  if (p->pass_rows != 0 && p->pass_rows != 1 && p->pass_rows != 2 && p->pass_rows != 4 && p->pass_rows != 8 && p->pass_rows != 128) { why = "pass_rows must be 0, 1, 2, 4, 8 or 128"; return BICADMM_ERR_ARG; }
   if (p->pass_stages < 0 || p->pass_stages > 8) { why = "pass_stages must be in [0, 8]"; return BICADMM_ERR_ARG; }
   return BICADMM_OK;
 }
@@ -515,12 +574,18 @@ int build_geometry(bicadmm_ctx* h) {
   // A-pass panel geometry
   const size_t row_bytes = static_cast<size_t>(h->lda) * h->asz;
   int R = p.pass_rows;
-  if (h->K > 1) {
+  // BF16 softmax rows of <= 2048 columns: tensor-core pass (128-row panels) unless 8-row
+  // CUDA-core panels are asked for.
+  h->use_tc = h->K > 1 && p.precision == BICADMM_PREC_BF16 && h->lda <= 128 * kTcMaxSlabs &&
+              (R == 0 || R == kTcRows);
+  if (R == kTcRows && !h->use_tc) return fail(h, BICADMM_ERR_UNSUPPORTED, "128-row panels are the tensor-core pass (BF16 softmax, n <= 2048)");
+  if (h->K > 1 && !h->use_tc) {
     // Softmax pass: one CTA per SM (register tiles), 8-row panels, up to 4 stages in the
     // single-CTA budget.
     if (R != 0 && R != kPassRowsK) return fail(h, BICADMM_ERR_UNSUPPORTED, "the softmax A pass uses 8-row panels (pass_rows 0 or 8)");
     R = kPassRowsK;
   }
+  if (h->use_tc) R = kTcRows;
   // Auto: the tallest panel (<= 48 KB) of which two stages fit a two-CTA-per-SM budget, and
   // up to four stages in that budget (one stage if a single row exceeds it).
   if (R == 0) {
@@ -529,21 +594,23 @@ int build_geometry(bicadmm_ctx* h) {
       if (cand * row_bytes <= 48 * 1024 && 2 * cand * row_bytes <= kPassCtaTarget) { R = cand; break; }
     }
   }
-  int S = p.pass_stages;
+  int S = h->use_tc ? kTcStages : p.pass_stages;
   if (S == 0) {
     const size_t budget = h->K == 1 && 2 * R * row_bytes <= kPassCtaTarget ? kPassCtaTarget : kPassSmemBudget;
     S = static_cast<int>(std::min<size_t>(4, budget / (R * row_bytes)));
     if (S < 1) S = 1;
   }
-  if (static_cast<size_t>(S) * R * row_bytes > kPassSmemBudget)
+  if (!h->use_tc && static_cast<size_t>(S) * R * row_bytes > kPassSmemBudget)
     return fail(h, BICADMM_ERR_UNSUPPORTED, "A-pass stages do not fit in shared memory (rows too wide)");
   h->R = R;
   h->S = S;
   const int ve = static_cast<int>(16 / h->asz);
   const int64_t nvec = h->lda / ve;
-  h->VPT = h->K == 1 ? pick_vpt(nvec) : pick_vpt_k(nvec, ve, h->KC, h->esz);
+  h->VPT = h->use_tc ? 1 : (h->K == 1 ? pick_vpt(nvec) : pick_vpt_k(nvec, ve, h->KC, h->esz));
   if (h->VPT < 0) return fail(h, BICADMM_ERR_UNSUPPORTED, "rows too wide for the register-resident A-pass accumulators");
-  if (h->K > 1) {
+  if (h->use_tc) {
+    h->pass_smem = fused_pass_tc_smem();
+  } else if (h->K > 1) {
     const int C = h->KC <= 4 ? 4 : 16;
     h->pass_smem = static_cast<size_t>(S) * R * row_bytes + S * sizeof(uint64_t) +
                    static_cast<size_t>(R) * (kPassThreads / 32 + 1) * C * h->esz + 16;
@@ -559,7 +626,9 @@ int build_geometry(bicadmm_ctx* h) {
   h->P_panels = h->panel_start[h->N];
   int occ = 0;
   int rc;
-  if (h->K > 1) {
+  if (h->use_tc) {
+    rc = launch_pass_tc(h, false, 1, &occ);
+  } else if (h->K > 1) {
     switch (h->p.precision) {
       case BICADMM_PREC_FP64: rc = launch_pass_k<double, double>(h, false, 1, &occ); break;
       case BICADMM_PREC_FP32: rc = launch_pass_k<float, float>(h, false, 1, &occ); break;
@@ -1244,6 +1313,7 @@ int bicadmm_create(const bicadmm_params* params, void* stream, bicadmm_t* out) {
   }
   rc = build_geometry(h);
   if (rc == BICADMM_OK) rc = allocate(h);
+  if (rc == BICADMM_OK && h->use_tc) rc = make_tmap(h);
   if (rc == BICADMM_OK) rc = reset_state(h);
   if (rc != BICADMM_OK) {
     g_create_error = h->err;

@@ -52,11 +52,28 @@ def test_softmax_fp32_vs_oracle_on_rounded_A():
     compare_state(st, run_oracle(P, 25, A=A32), TOL32)
 
 
-def test_softmax_bf16_vs_oracle_on_rounded_A():
+@pytest.mark.parametrize("pass_rows", [8, 0])
+def test_softmax_bf16_vs_oracle_on_rounded_A(pass_rows):
+    """pass_rows 8: CUDA-core pass; 0: the tensor-core pass (128-row panels)."""
     P = synth.sparse_softmax(m=6000, n=200, K=10, nnz=40, N=4, M=4, kappa=40, seed=6)
     Ab = synth.round_to_bf16(P.A)
-    st, _ = run_gpu(P, 25, precision=bc.PREC_BF16, A=P.A)
+    st, _ = run_gpu(P, 25, precision=bc.PREC_BF16, A=P.A, pass_rows=pass_rows)
     compare_state(st, run_oracle(P, 25, A=Ab), TOL32)
+
+
+@pytest.mark.parametrize("case", [
+    # (m, n, K, N, M, kappa, iters)
+    (20000, 2000, 10, 4, 4, 100, 6),    # 16 slabs, the last 64-column box partly outside A
+    (60000, 300, 10, 16, 2, 40, 8),     # several shards per CTA, ragged panels
+    (9000, 2048, 3, 3, 4, 30, 6),       # full 2048-column rows, 4-class tiles
+    (5000, 130, 16, 5, 2, 50, 10),      # 16 classes, one partial slab
+])
+def test_softmax_bf16_tensor_core_pass(case):
+    m, n, K, N, M, kappa, iters = case
+    P = synth.sparse_softmax(m=m, n=n, K=K, nnz=kappa, N=N, M=M, kappa=kappa, seed=13)
+    Ab = synth.round_to_bf16(P.A)
+    st, _ = run_gpu(P, iters, precision=bc.PREC_BF16, A=P.A, pass_rows=128)
+    compare_state(st, run_oracle(P, iters, A=Ab), TOL32)
 
 
 @pytest.mark.parametrize("loss", [ref.LOSS_SQUARED, ref.LOSS_LOGISTIC, ref.LOSS_SQHINGE])
