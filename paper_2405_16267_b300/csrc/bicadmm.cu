@@ -85,6 +85,8 @@ struct bicadmm_ctx {
   // device buffers
   void *A = nullptr, *b = nullptr, *omega = nullptr, *nu = nullptr, *slots = nullptr,
        *xlo = nullptr, *Pm = nullptr;
+  unsigned char* wpk = nullptr;  // tensor-core pass: W_i as BF16 hi/lo MMA tiles per shard
+  int nslab = 0;                 // 128-column slabs of a row (tensor-core pass)
   double *x = nullptr, *u = nullptr, *r = nullptr, *z = nullptr, *s = nullptr, *w = nullptr,
          *tau_r = nullptr, *c_arr = nullptr, *e_arr = nullptr, *cta_stats = nullptr,
          *dual_part = nullptr;
@@ -293,7 +295,7 @@ int launch_pass_tc_c(bicadmm_ctx* h, bool with_consensus, int op, int* blocks) {
   }
   PassGeometry geo{h->d_shard_row0, h->d_panel_start, h->N, h->P_panels};
   kern<<<h->G + (with_consensus ? 1 : 0), kTcThreads, h->pass_smem, h->stream>>>(
-      h->tmap, h->lda, static_cast<const float*>(h->xlo), h->ldx, h->K,
+      h->tmap, h->lda, h->wpk, h->ldx, h->K,
       static_cast<const float*>(h->b), static_cast<float*>(h->omega), static_cast<float*>(h->nu),
       static_cast<float*>(h->slots), h->cta_stats, geo, static_cast<float>(h->M),
       static_cast<float>(h->p.rho_l), h->p.newton_iters, h->d_err, kWaitLimitCycles,
@@ -447,7 +449,7 @@ int run_iterations(bicadmm_ctx* h, int n_iters) {
 #define XUPD_K(KCV)                                                                                 \
   k_xupd_k<TM, KCV, kXupdThreads, kXupdRows><<<xupd_grid, kXupdThreads, sm, h->stream>>>(          \
       static_cast<const TM*>(h->Pm), h->d_P_off, h->d_blk_col0, h->d_blk_ldp, h->r, h->x,         \
-      static_cast<TM*>(h->xlo), M, lda, h->K)
+      static_cast<TM*>(h->xlo), M, lda, h->K, h->wpk, h->nslab)
         if (h->KC == 4) XUPD_K(4); else if (h->KC == 10) XUPD_K(10); else XUPD_K(16);
 #undef XUPD_K
       }
@@ -526,7 +528,7 @@ int validate(const bicadmm_params* p, std::string& why) {
   if (p->inner_iters < 1 || p->newton_iters < 1) { why = "inner_iters and newton_iters must be >= 1"; return BICADMM_ERR_ARG; }
   if (p->max_iters < 0 || p->check_every < 1) { why = "max_iters >= 0 and check_every >= 1 required"; return BICADMM_ERR_ARG; }
   if (p->n * p->K > kMaxN) { why = "n K > 32768 is not supported by this build"; return BICADMM_ERR_UNSUPPORTED; }
-  if (p->pass_rows != 0 && p->pass_rows != 1 && p->pass_rows != 2 && p->pass_rows != 4 && p->pass_rows != 8 && p->pass_rows != 128) { why = "pass_rows must be 0, 1, 2, 4, 8 or 128"; return BICADMM_ERR_ARG; }
+  if (p->pass_rows != 0 && p->pass_rows != 1 && p->pass_rows != 2 && p->pass_rows != 4 && p->pass_rows != 8 && p->pass_rows != 64) { why = "pass_rows must be 0, 1, 2, 4, 8 or 64"; return BICADMM_ERR_ARG; }
   if (p->pass_stages < 0 || p->pass_stages > 8) { why = "pass_stages must be in [0, 8]"; return BICADMM_ERR_ARG; }
   return BICADMM_OK;
 }
@@ -574,11 +576,11 @@ int build_geometry(bicadmm_ctx* h) {
   // A-pass panel geometry
   const size_t row_bytes = static_cast<size_t>(h->lda) * h->asz;
   int R = p.pass_rows;
-  // BF16 softmax rows of <= 2048 columns: tensor-core pass (128-row panels) unless 8-row
+  // BF16 softmax rows of <= 2048 columns: tensor-core pass (64-row panels) unless 8-row
   // CUDA-core panels are asked for.
   h->use_tc = h->K > 1 && p.precision == BICADMM_PREC_BF16 && h->lda <= 128 * kTcMaxSlabs &&
               (R == 0 || R == kTcRows);
-  if (R == kTcRows && !h->use_tc) return fail(h, BICADMM_ERR_UNSUPPORTED, "128-row panels are the tensor-core pass (BF16 softmax, n <= 2048)");
+  if (R == kTcRows && !h->use_tc) return fail(h, BICADMM_ERR_UNSUPPORTED, "64-row panels are the tensor-core pass (BF16 softmax, n <= 2048)");
   if (h->K > 1 && !h->use_tc) {
     // Softmax pass: one CTA per SM (register tiles), 8-row panels, up to 4 stages in the
     // single-CTA budget.
@@ -610,6 +612,7 @@ int build_geometry(bicadmm_ctx* h) {
   if (h->VPT < 0) return fail(h, BICADMM_ERR_UNSUPPORTED, "rows too wide for the register-resident A-pass accumulators");
   if (h->use_tc) {
     h->pass_smem = fused_pass_tc_smem();
+    h->nslab = 2 * static_cast<int>((h->lda + kTcStageCols - 1) / kTcStageCols);  // even
   } else if (h->K > 1) {
     const int C = h->KC <= 4 ? 4 : 16;
     h->pass_smem = static_cast<size_t>(S) * R * row_bytes + S * sizeof(uint64_t) +
@@ -675,6 +678,7 @@ void handle_bytes(const bicadmm_ctx* h, int64_t* persistent, int64_t* setup_extr
   b += m * lda * as + m * es + 2 * m * h->K * es;       // A, b, omega, nu
   b += static_cast<int64_t>(h->nslots) * ldx * es;      // slots
   b += N * ldx * es + h->P_total * es;                  // xlo, P
+  b += static_cast<int64_t>(N) * h->nslab * kTcWBytes;  // packed W (tensor-core pass)
   b += 3 * N * ldx * 8 + 7 * ldx * 8;                   // x, u, r; z, s, w, tau_r, c, e, key
   b += static_cast<int64_t>(h->G) * 32 + N * h->dual_chunks * 16 + 4096 * 112 + 4096;
   // polish: supp, A_S, q, d1, d2, p, x_S, step, partials, H
@@ -706,6 +710,7 @@ int allocate(bicadmm_ctx* h) {
   AL(h->c_arr, lda * sizeof(double));
   AL(h->e_arr, lda * sizeof(double));
   AL(h->key, lda * sizeof(uint64_t));
+  if (h->use_tc) AL(h->wpk, static_cast<size_t>(N) * h->nslab * kTcWBytes);
   AL(h->cta_stats, static_cast<size_t>(h->G) * 4 * sizeof(double));
   AL(h->dual_part, static_cast<size_t>(N) * h->dual_chunks * 2 * sizeof(double));
   AL(h->d_shard_row0, (N + 1) * sizeof(int64_t));
@@ -743,6 +748,7 @@ int reset_state(bicadmm_ctx* h) {
   CK(cudaMemsetAsync(h->slots, 0, static_cast<size_t>(h->nslots) * lda * es, h->stream));
   CK(cudaMemsetAsync(h->xlo, 0, static_cast<size_t>(N) * lda * es, h->stream));
   CK(cudaMemsetAsync(h->x, 0, N * lda * sizeof(double), h->stream));
+  if (h->wpk) CK(cudaMemsetAsync(h->wpk, 0, static_cast<size_t>(N) * h->nslab * kTcWBytes, h->stream));
   CK(cudaMemsetAsync(h->u, 0, N * lda * sizeof(double), h->stream));
   CK(cudaMemsetAsync(h->r, 0, N * lda * sizeof(double), h->stream));
   CK(cudaMemsetAsync(h->z, 0, lda * sizeof(double), h->stream));

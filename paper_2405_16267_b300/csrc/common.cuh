@@ -59,6 +59,12 @@ __device__ __forceinline__ T warp_reduce_scatter(T (&v)[C], int lane) {
   return s;
 }
 
+// Byte offset of element (row q, column c) inside a tile of rows of 64 BF16 (128 bytes)
+// with the 128-byte swizzle: the 16-byte chunk index is XORed with the row index mod 8.
+__host__ __device__ __forceinline__ uint32_t sw128_off(int q, int c) {
+  return static_cast<uint32_t>((q >> 3) * 1024 + (q & 7) * 128 + ((((c >> 3) ^ q) & 7) << 4) + (c & 7) * 2);
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -108,6 +114,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void fence_barrier_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {

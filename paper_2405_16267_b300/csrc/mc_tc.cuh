@@ -3,23 +3,21 @@
 // right-hand sides: eqs. p:GPU;x, p:GPU;omega, p:GPU;nu), with the two products on the
 // 5th-generation tensor cores:
 //
-//   forward   D1[128 x 16] = A_panel[128 x n] W_i[n x 16]            (row dots, FP32 in TMEM)
-//   backward  D2[n x 16]  += A_panel'[n x 128] d_panel[128 x 16]      (A'd, FP32 in TMEM)
+//   forward   D1[64 x 16] = A_panel[64 x n] W_i[n x 16]              (row dots, FP32 in TMEM)
+//   backward  D2[n x 16] += A_panel'[n x 64] d_panel[64 x 16]          (A'd, FP32 in TMEM)
 //
 // A stays BF16.  W_i and d are split into BF16 pairs hi + lo (hi = bf16(v), lo =
 // bf16(v - hi)) and both halves are accumulated into the same TMEM columns, so the
 // products carry about 16 bits of the FP32 operand instead of 8.
 //
-// Data movement: a panel is 128 rows; the row is cut into 128-column slabs, each moved by
-// two 2D TMA loads (64 x 128 boxes, 128-byte swizzle) into one 32 KB stage of an S-stage
-// mbarrier ring.  The same swizzled slab serves as the K-major A operand of the forward
-// (rows = M) and as the MN-major A operand of the backward (columns = M, two boxes LBO
-// apart).  The backward needs d, which needs the whole forward, so each slab is loaded twice
-// per panel: the second load normally hits L2 (one panel is 512 KB per SM).
+// Data movement: the row is cut into 128-column slabs, each moved by two 2D TMA loads
+// (64-column boxes, 128-byte swizzle) into one stage of an S-stage mbarrier ring.  The same
+// swizzled slab serves as the K-major A operand of the forward (rows = M) and as the
+// MN-major A operand of the backward (columns = M, the two boxes LBO apart).  The backward
+// needs d, which needs the whole forward, so each slab is loaded twice per panel: the
+// second load normally hits L2 (two panels, 512 KB, per SM are in flight).
 //
-// Roles: thread 0 issues TMA loads and tcgen05.mma; all four warps read TMEM (warp w owns
-// TMEM lanes 32w..32w+31 = panel rows / slab columns) and run the per-row softmax prox.
-// TMEM (512 columns): D1 at column 0, D2 slab c at column 32 + 16c.
+// Warp roles, panel size and the MMA order are described at k_fused_pass_tc.
 #pragma once
 
 #include <cuda.h>
@@ -65,6 +63,25 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a_desc, uint
       "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// The same, issued by one elected lane of a converged warp (the warp runs the issuing loop
+// uniformly, which keeps the operands in uniform registers; a loop in one thread of a
+// divergent branch issued MMAs at a fraction of the rate).
+__device__ __forceinline__ void umma_bf16_warp(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                               uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p, e;\n\tsetp.ne.b32 p, %4, 0;\n\telect.sync _|e, 0xffffffff;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit_warp(uint64_t* bar) {
+  asm volatile(
+      "{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+      "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(
+          smem_addr(bar))
+      : "memory");
+}
+
 // Arrive once on *bar when every tcgen05.mma issued so far by this thread has completed.
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -97,73 +114,73 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn_major,
          (static_cast<uint32_t>(M >> 4) << 24);
 }
 
-// Byte offset of element (row q, column c) inside a tile of rows of 64 BF16 (128 bytes)
-// with the 128-byte swizzle: the 16-byte chunk index is XORed with the row index mod 8.
-__device__ __forceinline__ uint32_t sw128_off(int q, int c) {
-  return static_cast<uint32_t>((q >> 3) * 1024 + (q & 7) * 128 + ((((c >> 3) ^ q) & 7) << 4) + (c & 7) * 2);
-}
-
 // ------------------------------------------------------------------ per-row softmax prox
 // omega-bar prox of eq. (p:GPU;omega) for one row held by one thread (K classes in
 // registers): argmin_w CE(M w; y) + (M rho_l / 2) ||w - a||^2.  Newton with the
 // Sherman-Morrison step of the Hessian diag(M^2 p + M rho_l) - M^2 p p', damped by halving
 // until ||g|| decreases, stopped once every step is within a few ulps of w.
-template <int KC, typename T>
-__device__ __forceinline__ void softmax_prox_row(T (&w)[KC], const T (&a)[KC], int y, int K, T M,
-                                                 T rho_l, int newton_iters) {
-  const T Mr = M * rho_l, M2 = M * M;
-  T p[KC], g[KC];
-  auto grad = [&](const T (&wv)[KC], T (&pk)[KC], T (&gk)[KC]) -> T {
-    T mx = -FpLim<T>::big;
+template <int KC>
+__device__ __forceinline__ void softmax_prox_row(float (&w)[KC], const float (&a)[KC], int y, int K,
+                                                 float M, float rho_l, int newton_iters) {
+  const float Mr = M * rho_l, M2 = M * M;
+  float p[KC], g[KC];
+  // gradient at wv (and p = softmax(M wv)); returns ||g||^2.  exp and the reciprocal use
+  // the fast hardware approximations (a few ulp); the minimiser is then that of phi up to
+  // that relative accuracy.
+  auto grad = [&](const float (&wv)[KC], float (&pk)[KC], float (&gk)[KC]) -> float {
+    float mx = -FpLim<float>::big;
 #pragma unroll
     for (int k = 0; k < KC; ++k)
-      if (k < K) mx = fmax(mx, M * wv[k]);
-    T S = T(0);
+      if (k < K) mx = fmaxf(mx, M * wv[k]);
+    float S = 0.f;
 #pragma unroll
     for (int k = 0; k < KC; ++k) {
-      pk[k] = k < K ? dev_exp<T>(M * wv[k] - mx) : T(0);
+      pk[k] = k < K ? __expf(M * wv[k] - mx) : 0.f;
       S += pk[k];
     }
-    const T inv = T(1) / S;
-    T gn = T(0);
+    const float inv = __fdividef(1.f, S);
+    float gn = 0.f;
 #pragma unroll
     for (int k = 0; k < KC; ++k) {
       pk[k] *= inv;
-      gk[k] = k < K ? M * (pk[k] - (k == y ? T(1) : T(0))) + Mr * (wv[k] - a[k]) : T(0);
-      gn = fma(gk[k], gk[k], gn);
+      gk[k] = k < K ? M * (pk[k] - (k == y ? 1.f : 0.f)) + Mr * (wv[k] - a[k]) : 0.f;
+      gn = fmaf(gk[k], gk[k], gn);
     }
     return gn;
   };
-  T gn2 = grad(w, p, g);
+  float gn2 = grad(w, p, g);
   for (int it = 0; it < newton_iters; ++it) {
-    T D[KC], t = T(0), sp = T(0);
+    float iD[KC], t = 0.f, sp = 0.f;
 #pragma unroll
     for (int k = 0; k < KC; ++k) {
-      D[k] = M2 * p[k] + Mr;
+      iD[k] = __fdividef(1.f, M2 * p[k] + Mr);
       if (k < K) {
-        t += p[k] * g[k] / D[k];
-        sp += p[k] / D[k];
+        t = fmaf(p[k] * g[k], iD[k], t);
+        sp = fmaf(p[k], iD[k], sp);
       }
     }
-    const T coef = M2 * t / (Mr * sp);
-    T delta[KC];
+    const float coef = __fdividef(M2 * t, Mr * sp);
+    float delta[KC];
     bool small = true;
 #pragma unroll
     for (int k = 0; k < KC; ++k) {
-      delta[k] = k < K ? (g[k] + coef * p[k]) / D[k] : T(0);
-      const T aw = fabs(w[k]);
-      small = small && fabs(delta[k]) <= T(4) * FpLim<T>::eps * (aw > T(1) ? aw : T(1));
+      delta[k] = k < K ? (g[k] + coef * p[k]) * iD[k] : 0.f;
+      small = small && fabsf(delta[k]) <= 4.f * FpLim<float>::eps * fmaxf(fabsf(w[k]), 1.f);
     }
     if (small) break;
-    T alpha = T(1), wt[KC], pt[KC], gt[KC], gt2 = gn2;
-    for (int bt = 0; bt < 40; ++bt) {
+    // damped step: halve until ||g|| decreases; no decrease within 8 halvings means g is
+    // at its rounding level, and w is kept
+    float alpha = 1.f, wt[KC], pt[KC], gt[KC], gt2 = gn2;
+    bool accepted = false;
+    for (int bt = 0; bt < 8; ++bt) {
 #pragma unroll
       for (int k = 0; k < KC; ++k) wt[k] = w[k] - alpha * delta[k];
       gt2 = grad(wt, pt, gt);
-      const T shrink = T(1) - T(1e-4) * alpha;
-      if (gt2 <= shrink * shrink * gn2) break;
-      alpha *= T(0.5);
+      const float shrink = 1.f - 1e-4f * alpha;
+      if (gt2 <= shrink * shrink * gn2) { accepted = true; break; }
+      alpha *= 0.5f;
     }
+    if (!accepted) break;
 #pragma unroll
     for (int k = 0; k < KC; ++k) {
       w[k] = wt[k];
@@ -175,63 +192,110 @@ __device__ __forceinline__ void softmax_prox_row(T (&w)[KC], const T (&a)[KC], i
 }
 
 // ------------------------------------------------------------------ k_fused_pass_tc
-constexpr int kTcRows = 128;                       // panel rows = MMA M
-constexpr int kTcThreads = 128;                    // 4 warps = the 128 TMEM lanes
-constexpr int kTcStages = 2;
-constexpr int kTcStageBytes = 2 * kTcRows * 128;   // two 64-column BF16 boxes
-constexpr int kTcMaxSlabs = 16;                    // 128-column slabs: lda <= 2048
-constexpr int kTcXBytes = kTcMaxSlabs * 2 * 2 * 2048;  // [box][split] 16 x 64 BF16 tiles
-constexpr int kTcDBytes = 2 * 2 * 2048;            // [split][row half] 16 x 64 BF16 tiles
-constexpr int kTcTmemCols = 512;
-constexpr int kTcConsMW = 8;                       // consensus masks: n K <= 32 * 8 * 128
+// Warp roles (256 threads): warps 0-3 own the 128 TMEM lanes (epilogue and slot flush),
+// warp 4 lane 0 issues the loads, warp 5 lane 0 issues tcgen05.mma, warps 6-7 idle.
+//
+// Panels are 64 rows.  The forward MMA has M = 128: for even panels its descriptor starts
+// at the box, so the panel rows land in TMEM lanes 0-63 (epilogue warps 0-1); for odd
+// panels it starts 8 KB (64 rows) earlier, so they land in lanes 64-127 (warps 2-3).  The
+// other 64 M-rows read neighbouring shared memory and give lanes that are never read.
+// The two warp pairs run the prox of alternate panels concurrently.
+//
+// W_i is read from global memory in its MMA layout (per 64-column box a 32 x 64 BF16 tile:
+// rows 0-15 the hi parts of the 16 classes, rows 16-31 the lo parts; written by
+// k_xupd_k): each forward stage brings the 8 KB W slab with the 16 KB A slab, so nothing
+// per shard stays resident and the ring can hold S stages of 24 KB.  The forward MMA has
+// N = 32 and produces A W_hi and A W_lo side by side; the epilogue adds the two halves.
+//
+// MMA order per CTA: F(0); then for each later panel k: F(k), B(k-1) inside a shard, or
+// B(k-1), F(k) when k starts a new shard; B(last) at the end.  The producer loads slabs in
+// exactly that order.  D1 and d are double-buffered by panel parity; the prox of panel k
+// overlaps the loads and forward MMAs of panel k+1.  At a shard end all four epilogue
+// warps wait for the shard's last backward and copy D2 to the shard's slot.
+constexpr int kTcRows = 64;                        // panel rows
+constexpr int kTcThreads = 256;
+constexpr int kTcStages = 4;
+constexpr int kTcBoxBytes = kTcRows * 128;         // one 64 x 64 BF16 box = 8 KB
+constexpr int kTcWBytes = 2 * 4096;                // W of a 128-column slab: [box] 32 x 64 BF16 (hi | lo)
+constexpr int kTcStageCols = 256;                  // columns per stage: two slabs, four boxes
+constexpr int kTcStageABytes = 4 * kTcBoxBytes;
+constexpr int kTcStageBytes = kTcStageABytes + 2 * kTcWBytes;  // A (256 columns) + its W
+constexpr int kTcMaxSlabs = 16;                    // lda <= 2048
+constexpr int kTcDBytes = 2 * 2 * 2048;            // [buffer][split] 16 x 64 BF16 tiles
+constexpr int kTcTmemCols = 512;                   // D1 x2 at 0 / 32, D2 slab s at 64 + 16 s
+constexpr int kTcD2Col = 64;
 
 inline size_t fused_pass_tc_smem() {
-  return 1024 + static_cast<size_t>(kTcStages) * kTcStageBytes + kTcXBytes + kTcDBytes + 256;
+  // alignment, a 64-row lead-in read by odd panels of stage 0, ring, d tiles, barriers
+  return 1024 + kTcBoxBytes + static_cast<size_t>(kTcStages) * kTcStageBytes + kTcDBytes + 256;
+}
+
+// Bounded wait that also gives up once another role has raised *abort.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, long long limit,
+                                                   volatile int* abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort || clock64() - t0 > limit) return false;
+  }
+  return true;
 }
 
 template <int KC>
 __global__ void __launch_bounds__(kTcThreads, 1)
-k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda, const float* __restrict__ xlo,
-                int64_t ldx, int K, const float* __restrict__ b, float* __restrict__ omega,
-                float* __restrict__ nu, float* __restrict__ slots, double* __restrict__ cta_stats,
-                PassGeometry geo, float Mf, float rho_l, int newton_iters, int* __restrict__ err,
+k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
+                const unsigned char* __restrict__ wpk, int64_t ldx, int K,
+                const float* __restrict__ b, float* __restrict__ omega, float* __restrict__ nu,
+                float* __restrict__ slots, double* __restrict__ cta_stats, PassGeometry geo,
+                float Mf, float rho_l, int newton_iters, int* __restrict__ err,
                 long long wait_limit, ConsensusArgs cons) {
   if (cons.enabled && blockIdx.x == gridDim.x - 1) {
-    consensus_block<kTcThreads, kTcConsMW>(cons);
+    consensus_block<kTcThreads, kConsMW>(cons);
     return;
   }
   constexpr int S = kTcStages;
-  constexpr uint32_t IDESC_FWD = idesc_bf16(128, 16, false, false);
+  constexpr uint32_t IDESC_FWD = idesc_bf16(128, 32, false, false);
   constexpr uint32_t IDESC_BWD = idesc_bf16(128, 16, true, false);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // 1024-byte alignment for the swizzled tiles
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  unsigned char* ring = base;
-  unsigned char* xs = ring + S * kTcStageBytes;
-  unsigned char* ds = xs + kTcXBytes;
+  unsigned char* ring = base + kTcBoxBytes;
+  unsigned char* ds = ring + S * kTcStageBytes;
   uint64_t* full = reinterpret_cast<uint64_t*>(ds + kTcDBytes);
   uint64_t* empty = full + S;
-  uint64_t* d1bar = empty + S;
-  uint64_t* bwdbar = d1bar + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bwdbar + 1);
-  float* red = reinterpret_cast<float*>(tmem_slot + 4);  // [4 warps][3]
+  uint64_t* d1full = empty + S;   // [2]
+  uint64_t* dready = d1full + 2;  // [2]
+  uint64_t* bwddone = dready + 2;
+  uint64_t* flushed = bwddone + 1;  // all 128 epilogue threads have copied D2 out
+  uint64_t* drainbar = flushed + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drainbar + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  long long* counts = reinterpret_cast<long long*>(tmem_slot + 2);  // [0] issued, [1] consumed
+  float* red = reinterpret_cast<float*>(counts + 2);               // [4 warps][3]
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int c = blockIdx.x, G = gridDim.x - (cons.enabled ? 1 : 0);
   const int64_t p_begin = static_cast<int64_t>(c) * geo.P / G;
   const int64_t p_end = static_cast<int64_t>(c + 1) * geo.P / G;
-  const int64_t np = p_end - p_begin;
-  const int nslab = static_cast<int>((lda + 127) / 128);
-  const int64_t nload = np * 2 * nslab;
+  const int np = static_cast<int>(p_end - p_begin);
+  const int nstage = static_cast<int>((lda + kTcStageCols - 1) / kTcStageCols);  // stages per phase
+  const int nslab = 2 * nstage;  // 128-column slabs (D2 tiles; W is stored for all of them)
+  volatile int* abort_v = abort_flag;
 
   if (tid == 0) {
     for (int st = 0; st < S; ++st) {
       mbar_init(&full[st], 1);
       mbar_init(&empty[st], 1);
     }
-    mbar_init(d1bar, 1);
-    mbar_init(bwdbar, 1);
+    mbar_init(&d1full[0], 1);
+    mbar_init(&d1full[1], 1);
+    mbar_init(&dready[0], 64);
+    mbar_init(&dready[1], 64);
+    mbar_init(bwddone, 1);
+    mbar_init(flushed, 128);
+    mbar_init(drainbar, 1);
+    *abort_flag = 0;
+    counts[0] = counts[1] = 0;
     fence_barrier_init();
   }
   if (warp == 0) {
@@ -242,208 +306,265 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda, const flo
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
 
-  // producer state (thread 0)
-  int64_t j_issue = 0, j_cons = 0;
-  int issue_shard = 0;
-  auto issue = [&](int64_t j) -> bool {
-    const int st = static_cast<int>(j % S);
-    if (j >= S && !mbar_wait_bounded(&empty[st], static_cast<uint32_t>(((j / S) - 1) & 1), wait_limit))
-      return false;
-    const int64_t k = j / (2 * nslab);
-    const int sl = static_cast<int>(j % nslab);
-    int64_t row0;
-    int nr;
-    locate_panel<kTcRows>(geo, p_begin + k, issue_shard, row0, nr);
-    unsigned char* dst = ring + st * kTcStageBytes;
-    mbar_arrive_expect_tx(&full[st], kTcStageBytes);
-    tma_load_2d(dst, &tmap, sl * 128, static_cast<int>(row0), &full[st]);
-    tma_load_2d(dst + kTcStageBytes / 2, &tmap, sl * 128 + 64, static_cast<int>(row0), &full[st]);
-    return true;
+  // Panel k -> (first row, rows, shard) with a forward-moving shard hint.
+  struct PanelWalk {
+    int hint = 0;
+    __device__ void at(const PassGeometry& g, int64_t p, int64_t& row0, int& nrows, int& shard) {
+      locate_panel<kTcRows>(g, p, hint, row0, nrows);
+      shard = hint;
+    }
+  };
+  // shard of panel k (k < np) or -1
+  auto shard_of = [&](int k) -> int {
+    if (k < 0 || k >= np) return -1;
+    PanelWalk t;
+    int64_t r0;
+    int nr, sh;
+    t.at(geo, p_begin + k, r0, nr, sh);
+    return sh;
+  };
+  // Step order shared by the producer and the MMA issuer: calls fn(is_forward, k).
+  auto schedule = [&](auto&& fn) {
+    PanelWalk pw;
+    int prev_shard = -1;
+    for (int k = 0; k < np; ++k) {
+      int64_t r0;
+      int nr, sh;
+      pw.at(geo, p_begin + k, r0, nr, sh);
+      const bool boundary = sh != prev_shard;
+      if (k > 0 && boundary && !fn(false, k - 1)) return;
+      if (!fn(true, k)) return;
+      if (k > 0 && !boundary && !fn(false, k - 1)) return;
+      prev_shard = sh;
+    }
+    if (np > 0) fn(false, np - 1);
   };
 
-  bool ok = true;
-  if (tid == 0) {
-    for (; j_issue < nload && j_issue < S; ++j_issue) ok = ok && issue(j_issue);
-  }
-
-  uint32_t d1_phase = 0, bwd_phase = 0;
-  int cur = -1, shard = 0;
-  bool first_bwd = true;
   float st_res = 0.f, st_om = 0.f, st_ax = 0.f;
 
-  // Wait until every issued MMA has completed, then copy the D2 accumulators of shard i to
-  // its slot (column col = 128 slab + TMEM lane, classes along TMEM columns).
-  auto flush = [&](int i) -> bool {
-    if (tid == 0) umma_commit(bwdbar);
-    const bool w_ok = mbar_wait_bounded(bwdbar, bwd_phase, wait_limit);
-    bwd_phase ^= 1u;
-    tc_fence_after();
-    float* dst = slots + static_cast<int64_t>(c + i) * ldx;
-    for (int sl = 0; sl < nslab; ++sl) {
-      uint32_t v[16];
-      tmem_ld16(tmem + lane_base + 32 + 16 * sl, v);
-      const int64_t col = static_cast<int64_t>(sl) * 128 + warp * 32 + lane;
-      if (col < lda) {
+  if (warp == 4) {
+    // ---------------------------------------------------------------- producer
+    if (lane == 0) {
+      long long j = 0;
+      PanelWalk pw;
+      schedule([&](bool fwd, int k) -> bool {
+        int64_t row0;
+        int nr, sh;
+        pw.at(geo, p_begin + k, row0, nr, sh);  // non-decreasing shard along the schedule
+        const unsigned char* wsrc = wpk + static_cast<int64_t>(sh) * nslab * kTcWBytes;
+        for (int sg = 0; sg < nstage; ++sg, ++j) {
+          const int st = static_cast<int>(j % S);
+          if (j >= S && !mbar_wait_or_abort(&empty[st], static_cast<uint32_t>(((j / S) - 1) & 1), wait_limit, abort_v)) {
+            *abort_v = 1;
+            counts[0] = j;
+            return false;
+          }
+          unsigned char* dst = ring + st * kTcStageBytes;
+          mbar_arrive_expect_tx(&full[st], kTcStageABytes + (fwd ? 2 * kTcWBytes : 0));
 #pragma unroll
-        for (int k = 0; k < KC; ++k)
-          if (k < K) dst[col * K + k] = __uint_as_float(v[k]);
-      }
+          for (int bx = 0; bx < 4; ++bx)
+            tma_load_2d(dst + bx * kTcBoxBytes, &tmap, sg * kTcStageCols + bx * 64, static_cast<int>(row0), &full[st]);
+          if (fwd) bulk_copy_g2s(dst + kTcStageABytes, wsrc + 2 * sg * kTcWBytes, 2 * kTcWBytes, &full[st]);
+        }
+        counts[0] = j;
+        return true;
+      });
     }
-    tc_fence_before();
-    return w_ok;
-  };
-
-  for (int64_t k = 0; k < np && ok; ++k) {
-    int64_t row0;
-    int nrows;
-    locate_panel<kTcRows>(geo, p_begin + k, shard, row0, nrows);
-    if (shard != cur) {
-      if (cur >= 0) ok = flush(cur) && ok;
-      // W_i of the new shard as BF16 hi/lo tiles [box][split][16 classes x 64 columns]
-      const float* xsrc = xlo + static_cast<int64_t>(shard) * ldx;
-      for (int e = tid; e < nslab * 128 * 16; e += kTcThreads) {
-        const int col = e >> 4, q = e & 15;
-        const float v = (col < lda && q < K) ? xsrc[static_cast<int64_t>(col) * K + q] : 0.f;
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-        const int bx = col >> 6;
-        const uint32_t off = sw128_off(q, col & 63);
-        *reinterpret_cast<__nv_bfloat16*>(xs + (bx * 2 + 0) * 2048 + off) = hi;
-        *reinterpret_cast<__nv_bfloat16*>(xs + (bx * 2 + 1) * 2048 + off) = lo;
-      }
-      fence_async_smem();
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-      cur = shard;
-      first_bwd = true;
-    }
-
-    // ---- forward: D1 = A_panel W_i (hi + lo)
-    if (tid == 0 && ok) {
-      for (int sl = 0; sl < nslab && ok; ++sl) {
-        const int st = static_cast<int>(j_cons % S);
-        if (!mbar_wait_bounded(&full[st], static_cast<uint32_t>((j_cons / S) & 1), wait_limit)) { ok = false; break; }
-        tc_fence_after();
-        const uint32_t sa = smem_addr(ring + st * kTcStageBytes);
-#pragma unroll
-        for (int bx = 0; bx < 2; ++bx)
-#pragma unroll
-          for (int sp = 0; sp < 2; ++sp)
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-              const uint64_t ad = sdesc_sw128(sa + bx * (kTcStageBytes / 2) + ks * 32, 16, 1024);
-              const uint64_t bd = sdesc_sw128(smem_addr(xs + ((sl * 2 + bx) * 2 + sp) * 2048) + ks * 32, 16, 1024);
-              umma_bf16(tmem, ad, bd, IDESC_FWD, (sl | bx | sp | ks) != 0 ? 1u : 0u);
-            }
-        umma_commit(&empty[st]);
-        ++j_cons;
-        if (j_issue < nload) { ok = issue(j_issue) && ok; ++j_issue; }
-      }
-      umma_commit(d1bar);
-    }
-    ok = __syncthreads_and(ok);
-    if (!ok) break;
-    ok = mbar_wait_bounded(d1bar, d1_phase, wait_limit);
-    d1_phase ^= 1u;
-    tc_fence_after();
-
-    // ---- epilogue: thread = panel row
+  } else if (warp == 5) {
+    // ---------------------------------------------------------------- MMA issuer (whole warp)
     {
-      uint32_t v[16];
-      tmem_ld16(tmem + lane_base, v);
-      const int r = tid;
-      const bool valid = r < nrows;
-      float Axb[KC], aa[KC], w[KC], nur[KC];
+      // descriptor templates: only the 14-bit start address field changes per MMA
+      const uint64_t tk = sdesc_sw128(0, 16, 1024);          // K-major operands
+      const uint64_t tm_ = sdesc_sw128(0, kTcBoxBytes, 1024);  // MN-major slab (backward A)
+      const uint32_t ring_a = smem_addr(ring), ds_a = smem_addr(ds);
+      auto dsc = [](uint64_t t, uint32_t addr) -> uint64_t { return t | ((addr >> 4) & 0x3FFFu); };
+      long long j = 0;
+      int bwd_shard = -1, fseg = 0;
+      auto consume = [&](bool fwd, int k) -> bool {
+        bool first_bwd = false;
+        if (!fwd) {
+          if (!mbar_wait_or_abort(&dready[k & 1], static_cast<uint32_t>((k >> 1) & 1), wait_limit, abort_v)) return false;
+          const int sh = shard_of(k);
+          first_bwd = sh != bwd_shard;
+          if (first_bwd && bwd_shard >= 0) {  // D2 of the previous shard has been copied out
+            if (!mbar_wait_or_abort(flushed, static_cast<uint32_t>(fseg & 1), wait_limit, abort_v)) return false;
+            ++fseg;
+          }
+          bwd_shard = sh;
+        }
+        tc_fence_after();
+        // odd panels: M-rows 64..127 are the panel rows (TMEM lanes 64..127)
+        const uint32_t lead = (k & 1) ? kTcBoxBytes : 0u;
+        for (int sg = 0; sg < nstage; ++sg, ++j) {
+          const int st = static_cast<int>(j % S);
+          // TMA completion on the stage barrier makes the data visible to the MMAs (both
+          // async proxy); no tcgen05 fence is needed here
+          if (!mbar_wait_or_abort(&full[st], static_cast<uint32_t>((j / S) & 1), wait_limit, abort_v)) return false;
+          const uint32_t sa = ring_a + st * kTcStageBytes;
+          if (fwd) {
+            const uint32_t d1 = tmem + 32 * (k & 1);
+#pragma unroll
+            for (int bx = 0; bx < 4; ++bx)
+#pragma unroll
+              for (int ks = 0; ks < 4; ++ks)
+                umma_bf16_warp(d1, dsc(tk, sa + bx * kTcBoxBytes - lead + ks * 32),
+                               dsc(tk, sa + kTcStageABytes + bx * 4096 + ks * 32), IDESC_FWD,
+                               (sg | bx | ks) != 0 ? 1u : 0u);
+          } else {
+            const uint32_t db = ds_a + (k & 1) * 4096;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int sl = 2 * sg + h;
+              {
+                const uint32_t d2 = tmem + kTcD2Col + 16 * sl;
+#pragma unroll
+                for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+                  for (int ks = 0; ks < 4; ++ks)
+                    umma_bf16_warp(d2, dsc(tm_, sa + h * 2 * kTcBoxBytes + ks * 2048),
+                                   dsc(tk, db + sp * 2048 + ks * 32), IDESC_BWD,
+                                   (first_bwd && sp == 0 && ks == 0) ? 0u : 1u);
+              }
+            }
+          }
+          umma_commit_warp(&empty[st]);
+        }
+        if (fwd) {
+          umma_commit_warp(&d1full[k & 1]);
+        } else if (k + 1 >= np || shard_of(k + 1) != bwd_shard) {
+          umma_commit_warp(bwddone);  // last backward of a shard
+        }
+        return true;
+      };
+      schedule([&](bool fwd, int k) -> bool {
+        const bool okk = consume(fwd, k);
+        counts[1] = j;
+        if (!okk) *abort_v = 1;
+        return okk;
+      });
+    }
+  } else if (warp < 4) {
+    // ---------------------------------------------------------------- epilogue warps
+    const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
+    const int pair = warp >> 1;  // panels of this parity
+    const int r = tid & 63;      // panel row of this thread
+    int seg = 0;
+    bool eok = true;
+    PanelWalk pw;
+    // prefetched row data of this pair's next panel
+    float nur[KC], wv[KC];
+    int y = 0;
+    auto prefetch = [&](int k) {
+      int64_t row0 = 0;
+      int nrows = 0, sh;
+      if (k < np) {
+        PanelWalk t;
+        t.at(geo, p_begin + k, row0, nrows, sh);
+      }
+      const bool valid = k < np && r < nrows;
 #pragma unroll
       for (int q = 0; q < KC; ++q) {
-        Axb[q] = __uint_as_float(v[q]) / Mf;
         nur[q] = (valid && q < K) ? nu[(row0 + r) * K + q] : 0.f;
-        w[q] = (valid && q < K) ? omega[(row0 + r) * K + q] : 0.f;
-        aa[q] = Axb[q] + nur[q];
+        wv[q] = (valid && q < K) ? omega[(row0 + r) * K + q] : 0.f;
       }
-      const int y = valid ? static_cast<int>(b[row0 + r]) : 0;
-      if (valid) softmax_prox_row<KC, float>(w, aa, y, K, Mf, rho_l, newton_iters);
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        float dv = 0.f;
-        if (q < KC && q < K && valid) {
-          const float nun = nur[q] + Axb[q] - w[q];
-          omega[(row0 + r) * K + q] = w[q];
-          nu[(row0 + r) * K + q] = nun;
-          dv = w[q] - Axb[q] - nun;
-          const float rr = Axb[q] - w[q];
-          st_res = fmaf(rr, rr, st_res);
-          st_om = fmaf(w[q], w[q], st_om);
-          st_ax = fmaf(Axb[q], Axb[q], st_ax);
-        }
-        const __nv_bfloat16 hi = __float2bfloat16_rn(dv);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(dv - __bfloat162float(hi));
-        // d tile: [split][row half][16 classes x 64 rows], K-major (rows contiguous)
-        const uint32_t off = sw128_off(q, r & 63) + (r >> 6) * 2048;
-        *reinterpret_cast<__nv_bfloat16*>(ds + off) = hi;
-        *reinterpret_cast<__nv_bfloat16*>(ds + 4096 + off) = lo;
-      }
-    }
-    fence_async_smem();
-    tc_fence_before();
-    ok = __syncthreads_and(ok);
-    if (!ok) break;
-
-    // ---- backward: D2[slab] += A_slab' d (hi + lo)
-    if (tid == 0) {
-      tc_fence_after();
-      for (int sl = 0; sl < nslab && ok; ++sl) {
-        const int st = static_cast<int>(j_cons % S);
-        if (!mbar_wait_bounded(&full[st], static_cast<uint32_t>((j_cons / S) & 1), wait_limit)) { ok = false; break; }
+      y = valid ? static_cast<int>(b[row0 + r]) : 0;
+    };
+    prefetch(pair);
+    for (int k = 0; k < np && eok; ++k) {
+      int64_t row0;
+      int nrows, shard;
+      pw.at(geo, p_begin + k, row0, nrows, shard);
+      if ((k & 1) == pair) {
+        if (!mbar_wait_or_abort(&d1full[k & 1], static_cast<uint32_t>((k >> 1) & 1), wait_limit, abort_v)) { eok = false; break; }
         tc_fence_after();
-        const uint32_t sa = smem_addr(ring + st * kTcStageBytes);
+        uint32_t v[16], vl[16];
+        tmem_ld16(tmem + lane_base + 32 * (k & 1), v);
+        tmem_ld16(tmem + lane_base + 32 * (k & 1) + 16, vl);
+        const bool valid = r < nrows;
+        float Axb[KC], aa[KC], w[KC], nk[KC];
+        const int yk = y;
 #pragma unroll
-        for (int sp = 0; sp < 2; ++sp)
+        for (int q = 0; q < KC; ++q) {
+          Axb[q] = (__uint_as_float(v[q]) + __uint_as_float(vl[q])) / Mf;
+          nk[q] = nur[q];
+          w[q] = wv[q];
+          aa[q] = Axb[q] + nk[q];
+        }
+        prefetch(k + 2);  // this pair's next panel: loads overlap the prox
+        if (valid) softmax_prox_row<KC>(w, aa, yk, K, Mf, rho_l, newton_iters);
+        unsigned char* dbuf = ds + (k & 1) * 4096;
 #pragma unroll
-          for (int ks = 0; ks < 8; ++ks) {
-            const uint64_t ad = sdesc_sw128(sa + ks * 2048, kTcStageBytes / 2, 1024);
-            const uint64_t bd = sdesc_sw128(smem_addr(ds + sp * 4096 + (ks >> 2) * 2048) + (ks & 3) * 32, 16, 1024);
-            umma_bf16(tmem + 32 + 16 * sl, ad, bd, IDESC_BWD, (first_bwd && sp == 0 && ks == 0) ? 0u : 1u);
+        for (int q = 0; q < 16; ++q) {
+          float dv = 0.f;
+          if (q < KC && q < K && valid) {
+            const float nun = nk[q] + Axb[q] - w[q];
+            omega[(row0 + r) * K + q] = w[q];
+            nu[(row0 + r) * K + q] = nun;
+            dv = w[q] - Axb[q] - nun;
+            const float rr = Axb[q] - w[q];
+            st_res = fmaf(rr, rr, st_res);
+            st_om = fmaf(w[q], w[q], st_om);
+            st_ax = fmaf(Axb[q], Axb[q], st_ax);
           }
-        umma_commit(&empty[st]);
-        ++j_cons;
-        if (j_issue < nload) { ok = issue(j_issue) && ok; ++j_issue; }
+          const __nv_bfloat16 hi = __float2bfloat16_rn(dv);
+          const __nv_bfloat16 lo = __float2bfloat16_rn(dv - __bfloat162float(hi));
+          const uint32_t off = sw128_off(q, r);
+          *reinterpret_cast<__nv_bfloat16*>(dbuf + off) = hi;
+          *reinterpret_cast<__nv_bfloat16*>(dbuf + 2048 + off) = lo;
+        }
+        fence_async_smem();
+        tc_fence_before();
+        mbar_arrive(&dready[k & 1]);
+      }
+      // end of a shard: every epilogue warp copies its 32 columns of each slab of D2
+      if (k + 1 >= np || shard_of(k + 1) != shard) {
+        if (!mbar_wait_or_abort(bwddone, static_cast<uint32_t>(seg & 1), wait_limit, abort_v)) { eok = false; break; }
+        ++seg;
+        tc_fence_after();
+        float* dst = slots + static_cast<int64_t>(c + shard) * ldx;
+        for (int sl = 0; sl < nslab; ++sl) {
+          uint32_t u[16];
+          tmem_ld16(tmem + lane_base + kTcD2Col + 16 * sl, u);
+          const int64_t col = static_cast<int64_t>(sl) * 128 + tid;
+          if (col < lda) {
+#pragma unroll
+            for (int q = 0; q < KC; ++q)
+              if (q < K) dst[col * K + q] = __uint_as_float(u[q]);
+          }
+        }
+        tc_fence_before();
+        if (k + 1 < np) mbar_arrive(flushed);
       }
     }
-    first_bwd = false;
-    ok = __syncthreads_and(ok);
+    if (!eok) *abort_v = 1;
+    st_res = warp_sum(st_res);
+    st_om = warp_sum(st_om);
+    st_ax = warp_sum(st_ax);
+    if (lane == 0) {
+      red[warp * 3 + 0] = st_res;
+      red[warp * 3 + 1] = st_om;
+      red[warp * 3 + 2] = st_ax;
+    }
   }
-  if (ok && cur >= 0) ok = flush(cur) && ok;
-  ok = __syncthreads_and(ok);
+  __syncthreads();
 
-  if (!ok) {
-    // Report, then let this CTA's copies and MMAs in flight finish before freeing TMEM.
+  if (*abort_v) {
+    // Report, then let the copies and MMAs this CTA issued finish before freeing TMEM.
     if (tid == 0) {
       set_err(err, DEV_TIMEOUT_PASS);
-      for (int64_t q = j_cons; q < j_issue; ++q)
+      for (long long q = counts[1]; q < counts[0]; ++q)
         mbar_wait_bounded(&full[q % S], static_cast<uint32_t>((q / S) & 1), wait_limit);
-      umma_commit(bwdbar);
-      mbar_wait_bounded(bwdbar, bwd_phase, wait_limit);
+    }
+    if (warp == 5) {
+      umma_commit_warp(drainbar);  // arrives once every MMA this warp issued has completed
+      mbar_wait_bounded(drainbar, 0, wait_limit);
     }
     __syncthreads();
   }
-
-  st_res = warp_sum(st_res);
-  st_om = warp_sum(st_om);
-  st_ax = warp_sum(st_ax);
-  if (lane == 0) {
-    red[warp * 3 + 0] = st_res;
-    red[warp * 3 + 1] = st_om;
-    red[warp * 3 + 2] = st_ax;
-  }
-  tc_fence_before();
-  __syncthreads();
   if (tid == 0) {
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int w = 0; w < kTcThreads / 32; ++w) {
+    for (int w = 0; w < 4; ++w) {
       s0 += static_cast<double>(red[w * 3 + 0]);
       s1 += static_cast<double>(red[w * 3 + 1]);
       s2 += static_cast<double>(red[w * 3 + 2]);

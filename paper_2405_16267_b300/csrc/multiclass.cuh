@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(XT)
 k_xupd_k(const TP* __restrict__ P, const int64_t* __restrict__ P_off,
          const int* __restrict__ blk_col0, const int* __restrict__ blk_ldp,
          const double* __restrict__ r, double* __restrict__ x, TP* __restrict__ xlo, int M,
-         int64_t ldx, int K) {
+         int64_t ldx, int K, unsigned char* __restrict__ wpk, int nslab) {
   constexpr int C = ClassPad<KC>::C;
   extern __shared__ __align__(16) unsigned char rs_raw[];
   TP* rs = reinterpret_cast<TP*>(rs_raw);  // [ldp][KC]
@@ -74,6 +74,18 @@ k_xupd_k(const TP* __restrict__ P, const int64_t* __restrict__ P_off,
       const double xn = x[o] + static_cast<double>(sum);
       x[o] = xn;
       xlo[o] = static_cast<TP>(xn);
+      if (wpk) {
+        // the same entry as BF16 hi/lo in the tensor-core pass's W tiles: per shard, per
+        // 64-column box a 32 x 64 tile (rows 0-15 hi of the classes, 16-31 lo), 128-byte
+        // swizzle; boxes in column order (two per 128-column slab)
+        const int col = col0 + row;
+        const float v = static_cast<float>(xn);
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+        unsigned char* t = wpk + (static_cast<int64_t>(i) * nslab * 2 + (col >> 6)) * 4096;
+        *reinterpret_cast<__nv_bfloat16*>(t + sw128_off(q, col & 63)) = hi;
+        *reinterpret_cast<__nv_bfloat16*>(t + sw128_off(q + 16, col & 63)) = lo;
+      }
     }
   }
 }

@@ -54,7 +54,7 @@ def test_softmax_fp32_vs_oracle_on_rounded_A():
 
 @pytest.mark.parametrize("pass_rows", [8, 0])
 def test_softmax_bf16_vs_oracle_on_rounded_A(pass_rows):
-    """pass_rows 8: CUDA-core pass; 0: the tensor-core pass (128-row panels)."""
+    """pass_rows 8: CUDA-core pass; 0: the tensor-core pass (64-row panels)."""
     P = synth.sparse_softmax(m=6000, n=200, K=10, nnz=40, N=4, M=4, kappa=40, seed=6)
     Ab = synth.round_to_bf16(P.A)
     st, _ = run_gpu(P, 25, precision=bc.PREC_BF16, A=P.A, pass_rows=pass_rows)
@@ -72,7 +72,7 @@ def test_softmax_bf16_tensor_core_pass(case):
     m, n, K, N, M, kappa, iters = case
     P = synth.sparse_softmax(m=m, n=n, K=K, nnz=kappa, N=N, M=M, kappa=kappa, seed=13)
     Ab = synth.round_to_bf16(P.A)
-    st, _ = run_gpu(P, iters, precision=bc.PREC_BF16, A=P.A, pass_rows=128)
+    st, _ = run_gpu(P, iters, precision=bc.PREC_BF16, A=P.A, pass_rows=64)
     compare_state(st, run_oracle(P, iters, A=Ab), TOL32)
 
 
