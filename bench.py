@@ -51,8 +51,9 @@ def parse():
     ap.add_argument("--pass-stages", type=int, default=0)
     ap.add_argument("--inner", type=int, default=1, help="inner sharing sweeps J per iteration")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance leg")
-    ap.add_argument("--workload", default="logistic", choices=["logistic", "batch", "serve"],
-                    help="batch: 256 uneven instances advanced by batched launches; "
+    ap.add_argument("--workload", default="logistic", choices=["logistic", "softmax", "batch", "serve"],
+                    help="softmax: 500000 x 2000 BF16, 10 classes (tensor-core pass); "
+                         "batch: 256 uneven instances advanced by batched launches; "
                          "serve: a Poisson stream of solves through the serving loop")
     ap.add_argument("--requests", type=int, default=64, help="requests in the serve workload")
     ap.add_argument("--rate", type=float, default=200.0, help="mean arrivals/s (serve)")
@@ -308,6 +309,166 @@ def run_gpu(args, rank, world):
     return result
 
 
+# ----------------------------------------------------------------------------- softmax
+
+SOFTMAX = dict(name="sparse_softmax_500000x2000x10_bf16", m=500000, n=2000, K=10, nnz=500, N=32,
+               M=4, kappa=500, rho=1.0, gamma=10.0, seed=0)
+
+
+def generate_softmax(wl, rows=None):
+    """Seeded FP32 A rows and class labels of the softmax workload (shard by shard)."""
+    m = wl["m"]
+    r0, r1 = (0, m) if rows is None else rows
+    from concurrent.futures import ThreadPoolExecutor
+    pieces = [(max(a, r0), min(b_, r1)) for (a, b_) in synth.split_ranges(m, wl["N"])
+              if max(a, r0) < min(b_, r1)]
+    out_A = np.empty((r1 - r0, wl["n"]), dtype=np.float32)
+    out_b = np.empty(r1 - r0)
+
+    def job(rng):
+        lo, hi = rng
+        P = synth.sparse_softmax(m=m, n=wl["n"], K=wl["K"], nnz=wl["nnz"], N=wl["N"], M=wl["M"],
+                                 kappa=wl["kappa"], seed=wl["seed"], rows=(lo, hi))
+        out_A[lo - r0:hi - r0] = P.A
+        out_b[lo - r0:hi - r0] = P.b
+
+    with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        list(ex.map(job, pieces))
+    return out_A, out_b
+
+
+def run_softmax(args, rank, world):
+    """Sparse softmax regression, 10 classes, A 500000 x 2000 stored in BF16 (FP32 products on
+    the tensor cores), N = 32 shards, M = 4 blocks, entrywise kappa = 500.  A step is one
+    outer iteration (x-update, tensor-core A pass with the softmax prox, consensus, duals)."""
+    import torch
+    from paper_2405_16267_b300 import bicadmm as bc
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = dict(SOFTMAX)
+    if args.m:
+        wl["m"] = args.m
+    t_gen = time.perf_counter()
+    A_np, b_np = generate_softmax(wl)
+    A_pin = torch.from_numpy(A_np).to(torch.bfloat16).pin_memory()  # BF16 host copy
+    b_pin = torch.from_numpy(b_np).pin_memory()
+    del A_np
+    t_gen = time.perf_counter() - t_gen
+    stream = torch.cuda.current_stream(dev)
+    params = dict(loss=bc.LOSS_SOFTMAX, precision=bc.PREC_BF16, N=wl["N"], M=wl["M"], K=wl["K"],
+                  kappa=wl["kappa"], gamma=wl["gamma"], rho_c=wl["rho"], pass_rows=args.pass_rows)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    s = bc.Solver(A_pin, b_pin, stream=stream, **params)
+    s.step(args.warmup, info=False)
+    torch.cuda.synchronize()
+    # live per-kernel times on a few extra steps (events around every launch)
+    bc.set_profiling(s.h, 2)
+    s.step(min(20, args.steps), info=False)
+    kt = bc.get_kernel_times(s.h)
+    clocks = ClockSampler(local)
+    time.sleep(0.15)
+    bc.set_profiling(s.h, 1)
+    info0 = s.step(0)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(args.steps, info=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    pass_ms, pass_launches = bc.get_pass_time(s.h)
+    info1 = s.step(0)
+    launches = info1.kernel_launches - info0.kernel_launches
+    s.close()
+
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        p = bc.default_params(loss=params["loss"], precision=params["precision"], m=wl["m"],
+                              n=wl["n"], K=wl["K"], N_shards=wl["N"], M_blocks=wl["M"],
+                              kappa=wl["kappa"], gamma=wl["gamma"], rho_c=wl["rho"])
+        h = bc.create(p, stream)
+        bc.setup(h, A_pin, b_pin)
+        bc.step(h, args.steps, info=False)
+        x = bc.get_x(h, wl["n"] * wl["K"])
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        bc.destroy(h)
+        barrier()
+        e2e_s = t1 - t0
+        h2d = A_pin.numel() * A_pin.element_size() + b_pin.numel() * b_pin.element_size()
+        e2e = {"value": args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
+               "d2h_bytes_per_step": x.nbytes / args.steps, "seconds": e2e_s,
+               "includes": "create+setup(H2D of BF16 A and b; Gram; Cholesky; inverse)+K iterations+get_x"}
+
+    t_local = ms / 1000.0
+    t_max = reduce_max(t_local, dev) if world > 1 else t_local
+    if e2e and world > 1:
+        e2e["value"] = aggregate_value(world, args.steps, reduce_max(e2e["seconds"], dev))
+    hbm, peak_kind = peaks()
+    m, n, K = wl["m"], wl["n"], wl["K"]
+    # A once in BF16 + labels + omega and nu (K floats each) read and written
+    pass_bytes = m * n * 2 + m * (4 + 16 * K)
+    avg_pass_s = pass_ms / 1000.0 / max(pass_launches, 1)
+    achieved = pass_bytes / avg_pass_s / 1e9
+    cfg = {"workload": wl["name"], "m": m, "n": n, "K": K, "N_shards": wl["N"], "M_blocks": wl["M"],
+           "kappa": wl["kappa"], "rho": wl["rho"], "gamma": wl["gamma"], "loss": "softmax",
+           "A_dtype": "bf16", "inner_iters": 1,
+           "l2": "inputs larger than L2 (A is %.1f GB)" % (m * n * 2 / 1e9), "parallelism": "replicas"}
+    return {
+        "metric": METRIC, "value": aggregate_value(world, args.steps, t_max), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic (seeded; Gaussian A, 500-entry planted W*, Gumbel-argmax labels)",
+        "config": cfg,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "kernel": "k_fused_pass_tc",
+                     "peak_kind": peak_kind + " copy bandwidth",
+                     "algorithmic_bytes_per_launch": pass_bytes, "avg_launch_ms": avg_pass_s * 1e3,
+                     "launches_timed": pass_launches},
+        "live_kernel_ms": {k: (a / b if b else None) for k, (a, b) in kt.items()},
+        "clocks": clk, "gpu_launches": int(launches), "e2e": e2e, "input_generation_s": t_gen,
+    }
+
+
+def run_oracle_softmax(wl, steps, budget_s=30.0):
+    """The FP64 oracle on shard 0 of the softmax workload (BF16-rounded A, as the GPU path
+    sees it); one full iteration extrapolated as N times one shard's iteration."""
+    from oracle import bicadmm_ref as ref
+    r0, r1 = synth.split_ranges(wl["m"], wl["N"])[0]
+    A, b = generate_softmax(wl, rows=(r0, r1))
+    A = synth.round_to_bf16(A)
+    o = ref.BiCADMM(A, b, ref.LOSS_SOFTMAX, 1, wl["M"], wl["kappa"], gamma=wl["gamma"],
+                    rho_c=wl["rho"], K=wl["K"], n_shards_total=wl["N"])
+    o.iterate(1)
+    t0 = time.perf_counter()
+    done = 0
+    while done < steps:
+        o.iterate(1)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = (time.perf_counter() - t0) / done
+    sample = ("shard 0 of %d (%d x %d, K=%d, FP64 on the BF16-rounded A) with M=%d blocks: %d outer "
+              "iterations timed, %.3f s each; full iteration extrapolated as %d x that"
+              % (wl["N"], r1 - r0, wl["n"], wl["K"], wl["M"], done, dt, wl["N"]))
+    return {"value": 1.0 / (wl["N"] * dt), "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+            "sample": sample, "steps_timed": done}
+
+
 # ----------------------------------------------------------------------------- batch
 
 def run_batch(args, rank, world):
@@ -547,6 +708,10 @@ def main():
         res = run_batch(args, rank, world)
     elif args.workload == "serve":
         res = run_serve(args, rank, world)
+    elif args.workload == "softmax":
+        res = run_softmax(args, rank, world)
+        if rank == 0 and not args.no_cpu_baseline and world == 1:
+            res["cpu_baseline"] = run_oracle_softmax(dict(SOFTMAX), steps=10, budget_s=25.0)
     else:
         res = run_gpu(args, rank, world)
         if rank == 0 and not args.no_ttt:

@@ -151,9 +151,12 @@ void free_all(bicadmm_ctx* h) {
 }
 
 // ---------------------------------------------------------------- A-pass dispatch
+// With K > 1 the pass that carries the consensus CTA is preceded by k_consensus_prep (w and
+// the breakpoints given); with K = 1 the consensus CTA forms them itself from x and u.
 ConsensusArgs consensus_args(bicadmm_ctx* h, bool enabled) {
   ConsensusArgs a{};
-  a.x = h->x;
+  a.x = h->K > 1 ? nullptr : h->x;
+  a.prepared = h->K > 1 ? 1 : 0;
   a.u = h->u;
   a.w = h->w;
   a.z = h->z;
@@ -455,9 +458,16 @@ int run_iterations(bicadmm_ctx* h, int n_iters) {
       }
       CK(cudaGetLastError());
       if ((rc = prof_end(h, KIND_XUPD)) != BICADMM_OK) return rc;
-      if ((rc = prof_begin(h, KIND_PASS)) != BICADMM_OK) return rc;
-      // The last sweep's pass also runs the global step in its spare CTA.
+      // The last sweep's pass also runs the global step in its spare CTA; its target w
+      // is formed here by all SMs.
       const bool last = jj == h->p.inner_iters - 1;
+      if (last && h->K > 1) {
+        k_consensus_prep<<<static_cast<unsigned>((n + 255) / 256), 256, 0, h->stream>>>(
+            h->x, h->u, h->s, h->w, h->tau_r, h->c_arr, h->e_arr, N, n, lda);
+        CK(cudaGetLastError());
+        h->launches += 1;
+      }
+      if ((rc = prof_begin(h, KIND_PASS)) != BICADMM_OK) return rc;
       rc = launch_pass_any(h, last);
       if (rc != BICADMM_OK) return rc;
       if ((rc = prof_end(h, KIND_PASS)) != BICADMM_OK) return rc;
@@ -1157,6 +1167,8 @@ int batch_build(bicadmm_batch_ctx* b, int stage_kb, int S) {
     I.dual_part = h->dual_part; I.dual_chunks = h->dual_chunks; I.n = h->p.n; I.gs = h->gs;
     I.trace = h->trace; I.err = h->d_err;
     cons[q] = consensus_args(h, true);
+    cons[q].x = h->x;  // batched consensus CTAs form w and the breakpoints themselves
+    cons[q].prepared = 0;
     for (int i = 0; i < h->N; ++i)
       for (int j = 0; j < h->M; ++j) {
         const int nj = h->blk_col0[j + 1] - h->blk_col0[j];

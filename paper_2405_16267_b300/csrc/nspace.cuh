@@ -236,6 +236,7 @@ struct ConsensusArgs {
   double rho_c, rho_b;
   int* err;
   int enabled;       // used by the fused pass: 1 = its last CTA runs this step
+  int prepared;      // 1: w, tau_r, c_arr, e_arr were formed by k_consensus_prep
 };
 
 template <int GT, int MW>
@@ -246,7 +247,7 @@ __device__ void consensus_block(const ConsensusArgs& a) {
   const double v = a.gs->v, tau_prev = a.gs->tau;
   const double beta = a.N * a.rho_c / a.rho_b;
 
-  for (int64_t r = tid; r < n; r += GT) {
+  for (int64_t r = a.prepared ? n : tid; r < n; r += GT) {
     double wr;
     if (a.x) {
       double acc = 0.0;
@@ -268,15 +269,17 @@ __device__ void consensus_block(const ConsensusArgs& a) {
   // sums of c_r, e_r and the count over the active set {r : tau_r > at}; breakpoints are
   // non-negative, so they compare as their bit patterns.
   auto active_sums = [&](double at, double (&o)[3]) {
-    o[0] = o[1] = o[2] = 0.0;
+    o[0] = o[1] = 0.0;
+    int cnt = 0;
     const long long atb = __double_as_longlong(at);
     for (int64_t r = tid; r < n; r += GT) {
       if (__double_as_longlong(a.tau_r[r]) > atb) {
         o[0] += a.c_arr[r];
         o[1] += a.e_arr[r];
-        o[2] += 1.0;
+        ++cnt;
       }
     }
+    o[2] = static_cast<double>(cnt);
     block_sum<3>(o, red);
   };
 
@@ -383,6 +386,29 @@ __device__ void consensus_block(const ConsensusArgs& a) {
 template <int GT, int MW>
 __global__ void __launch_bounds__(GT, 1) k_global(ConsensusArgs a) {
   consensus_block<GT, MW>(a);
+}
+
+// ------------------------------------------------------------------------------ k_consensus_prep
+// The per-entry part of the (z,t) step, on every SM: w = (1/N) sum_i (x_i + u_i) (shards
+// in index order, deterministic) and, with the current s, the breakpoint tau_r and the
+// coefficients c_r, e_r of h (the same formulas as the consensus block).  Run before the
+// pass that carries the consensus CTA (ConsensusArgs::prepared = 1), which then starts at
+// the root search; on B300 FP64 runs at a small fraction of FP32, so this per-entry work
+// (a division per entry) is what one SM should not do for large n.
+static __global__ void k_consensus_prep(const double* __restrict__ x, const double* __restrict__ u,
+                                        const double* __restrict__ s, double* __restrict__ w,
+                                        double* __restrict__ tau_r, double* __restrict__ c_arr,
+                                        double* __restrict__ e_arr, int N, int64_t n, int64_t lda) {
+  const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  double acc = 0.0;
+  for (int i = 0; i < N; ++i) acc += x[i * lda + r] + u[i * lda + r];
+  const double wr = acc / N;
+  w[r] = wr;
+  const double sr = s[r], sg = dsign(wr);
+  c_arr[r] = sr * wr - fabs(wr);
+  e_arr[r] = (sr - sg) * (sr - sg);
+  tau_r[r] = wr == 0.0 ? 0.0 : (sg * sr < 1.0 ? fabs(wr) / (1.0 - sg * sr) : HUGE_VAL);
 }
 
 // ------------------------------------------------------------------------------ k_dual

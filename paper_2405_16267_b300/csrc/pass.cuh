@@ -19,6 +19,8 @@
 // by the next kernel, so results are deterministic.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "nspace.cuh"
 
@@ -115,11 +117,15 @@ constexpr int kConsMW = 4;
 
 template <typename TA, typename TM, int R, int VPT, int NT>
 __global__ void __launch_bounds__(NT, 1)
-k_fused_pass(const TA* __restrict__ A, int64_t lda, const TM* __restrict__ xlo,
+k_fused_pass(const TA* __restrict__ A, int64_t lda, const TM* __restrict__ xlo_in,
              const TM* __restrict__ b, TM* __restrict__ omega, TM* __restrict__ nu,
              TM* __restrict__ slots, double* __restrict__ cta_stats, PassGeometry geo,
              int S, int loss, TM Mf, TM rho_l, int newton_iters, int* __restrict__ err,
              long long wait_limit, ConsensusArgs cons) {
+  // x_i is held in the storage type when it is the arithmetic type (FP32, FP64) and in the
+  // arithmetic type otherwise (BF16 storage).
+  using XT = typename std::conditional<std::is_same<TA, __nv_bfloat16>::value, TM, TA>::type;
+  const XT* xlo = reinterpret_cast<const XT*>(xlo_in);
   // With cons.enabled the last CTA runs the global (z, t, s, v) step of this outer
   // iteration, which needs only x and u, concurrently with the A stream of the others.
   if (cons.enabled && blockIdx.x == gridDim.x - 1) {
@@ -166,7 +172,7 @@ k_fused_pass(const TA* __restrict__ A, int64_t lda, const TM* __restrict__ xlo,
     for (; n_issued < np && n_issued < S; ++n_issued) issue(n_issued);
   }
 
-  TM xr[VPT][VE];
+  XT xr[VPT][VE];
   TM acc[VPT][VE];
   int cur = -1, shard = 0;
 
@@ -191,14 +197,23 @@ k_fused_pass(const TA* __restrict__ A, int64_t lda, const TM* __restrict__ xlo,
     if (shard != cur) {
       if (cur >= 0) flush(cur);
       cur = shard;
-      const TM* xs = xlo + static_cast<int64_t>(shard) * lda;
 #pragma unroll
       for (int kk = 0; kk < VPT; ++kk) {
         const int64_t v = tid + static_cast<int64_t>(kk) * NT;
+        if constexpr (std::is_same<XT, TA>::value) {  // one 16-byte load per vector
+          const V* xv = reinterpret_cast<const V*>(xlo + static_cast<int64_t>(shard) * lda);
+          V t;
+          if (v < nvec) t = xv[v]; else t = V{};
+          const TA* te = reinterpret_cast<const TA*>(&t);
 #pragma unroll
-        for (int e = 0; e < VE; ++e) {
-          xr[kk][e] = v < nvec ? xs[v * VE + e] : TM(0);
-          acc[kk][e] = TM(0);
+          for (int e = 0; e < VE; ++e) { xr[kk][e] = te[e]; acc[kk][e] = TM(0); }
+        } else {
+          const XT* xs = xlo + static_cast<int64_t>(shard) * lda;
+#pragma unroll
+          for (int e = 0; e < VE; ++e) {
+            xr[kk][e] = v < nvec ? xs[v * VE + e] : XT(0);
+            acc[kk][e] = TM(0);
+          }
         }
       }
     }
@@ -237,7 +252,7 @@ k_fused_pass(const TA* __restrict__ A, int64_t lda, const TM* __restrict__ xlo,
             const V a = sv[r * nvec + v];
             const TA* ae = reinterpret_cast<const TA*>(&a);
 #pragma unroll
-            for (int e = 0; e < VE; ++e) dot[r] = fma(conv<TM>(ae[e]), xr[kk][e], dot[r]);
+            for (int e = 0; e < VE; ++e) dot[r] = fma(conv<TM>(ae[e]), conv<TM>(xr[kk][e]), dot[r]);
           }
         }
       }
