@@ -38,6 +38,26 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// The same with an L2 cache policy (from createpolicy).
+__device__ __forceinline__ void tma_load_2d_hint(void* dst, const CUtensorMap* map, int x, int y,
+                                                 uint64_t* bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(
+          smem_addr(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar)), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst)),
                "r"(ncols)
@@ -348,6 +368,9 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
     if (lane == 0) {
       long long j = 0;
       PanelWalk pw;
+      // forward loads are read again by the backward of the same panel: keep them in L2;
+      // the backward load is their last use
+      const uint64_t keep = l2_policy_evict_last(), drop = l2_policy_evict_first();
       schedule([&](bool fwd, int k) -> bool {
         int64_t row0;
         int nr, sh;
@@ -364,7 +387,8 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
           mbar_arrive_expect_tx(&full[st], kTcStageABytes + (fwd ? 2 * kTcWBytes : 0));
 #pragma unroll
           for (int bx = 0; bx < 4; ++bx)
-            tma_load_2d(dst + bx * kTcBoxBytes, &tmap, sg * kTcStageCols + bx * 64, static_cast<int>(row0), &full[st]);
+            tma_load_2d_hint(dst + bx * kTcBoxBytes, &tmap, sg * kTcStageCols + bx * 64,
+                             static_cast<int>(row0), &full[st], fwd ? keep : drop);
           if (fwd) bulk_copy_g2s(dst + kTcStageABytes, wsrc + 2 * sg * kTcWBytes, 2 * kTcWBytes, &full[st]);
         }
         counts[0] = j;
