@@ -40,6 +40,7 @@ constexpr int kPassThreads = 256;
 constexpr int kDualThreads = 256;
 constexpr int kXupdThreads = 256;
 constexpr int kXupdRows = 32;
+constexpr int kXupdRowsK = 128;  // K > 1: rows of P per CTA (one staging of R_ij per CTA)
 constexpr int kCholThreads = 256;
 constexpr int kTraceCap = kTraceCapacity;
 constexpr int64_t kMaxN = 32768;                 // single-CTA global step limit
@@ -448,12 +449,17 @@ int run_iterations(bicadmm_ctx* h, int n_iters) {
             static_cast<const TM*>(h->Pm), h->d_P_off, h->d_blk_col0, h->d_blk_ldp, h->r, h->x,
             static_cast<TM*>(h->xlo), M, lda);
       } else {
-        const size_t sm = static_cast<size_t>(h->max_ldp) * h->KC * sizeof(TM);
+        const size_t sm = static_cast<size_t>(h->max_ldp + 4) * h->KC * sizeof(TM);
+        const dim3 grid_k(static_cast<unsigned>((h->max_nj + kXupdRowsK - 1) / kXupdRowsK), M, N);
 #define XUPD_K(KCV)                                                                                 \
-  k_xupd_k<TM, KCV, kXupdThreads, kXupdRows><<<xupd_grid, kXupdThreads, sm, h->stream>>>(          \
-      static_cast<const TM*>(h->Pm), h->d_P_off, h->d_blk_col0, h->d_blk_ldp, h->r, h->x,         \
-      static_cast<TM*>(h->xlo), M, lda, h->K, h->wpk, h->nslab)
-        if (h->KC == 4) XUPD_K(4); else if (h->KC == 10) XUPD_K(10); else XUPD_K(16);
+  {                                                                                                 \
+    CK(cudaFuncSetAttribute(k_xupd_k<TM, KCV, kXupdThreads, kXupdRowsK>,                            \
+                            cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));    \
+    k_xupd_k<TM, KCV, kXupdThreads, kXupdRowsK><<<grid_k, kXupdThreads, sm, h->stream>>>(          \
+        static_cast<const TM*>(h->Pm), h->d_P_off, h->d_blk_col0, h->d_blk_ldp, h->r, h->x,       \
+        static_cast<TM*>(h->xlo), M, lda, h->K, h->wpk, h->nslab);                                  \
+  }
+        if (h->KC == 4) XUPD_K(4) else if (h->KC == 10) XUPD_K(10) else XUPD_K(16)
 #undef XUPD_K
       }
       CK(cudaGetLastError());
@@ -569,6 +575,8 @@ int build_geometry(bicadmm_ctx* h) {
     h->max_ldp = std::max(h->max_ldp, h->blk_ldp[j]);
   }
   if (h->max_nj > 8192) return fail(h, BICADMM_ERR_UNSUPPORTED, "feature blocks wider than 8192 columns are not supported; raise M_blocks");
+  if (h->K > 1 && static_cast<size_t>(h->max_ldp + 4) * h->KC * h->esz > 200 * 1024)
+    return fail(h, BICADMM_ERR_UNSUPPORTED, "feature blocks too wide for K classes (x-update tile); raise M_blocks");
   h->G_off.assign(static_cast<size_t>(h->N) * h->M, 0);
   h->P_off.assign(static_cast<size_t>(h->N) * h->M, 0);
   int64_t go = 0, po = 0;

@@ -33,39 +33,54 @@ __global__ void k_check_labels(const TM* __restrict__ b, int64_t m, int K, int* 
 }
 
 // ------------------------------------------------------------------------------ k_xupd_k
-// Grid (row tiles, M, N), XT threads, one warp per row of P_ij.  R_ij (n_j x K) is staged
-// in shared memory as [ldp][KC] (zero padded); the K dot products of a row of P_ij with
-// the columns of R_ij are reduced with one warp reduce-scatter.
+// Grid (row tiles of ROWS, M, N), XT threads, one warp per row of P_ij.  R_ij (n_j x K) is
+// read in its own (column-major-in-K) order and staged transposed in shared memory,
+// [KC][ldp + 4] (zero padded; the 4-element pad spreads the transposing stores over the
+// banks), so a lane reads the K values of its VE consecutive columns as K 16-byte loads;
+// the rows of P_ij are read in 16-byte vectors too.  The K dot products of a row are
+// reduced with one warp reduce-scatter.
 template <typename TP, int KC, int XT, int ROWS>
 __global__ void __launch_bounds__(XT)
 k_xupd_k(const TP* __restrict__ P, const int64_t* __restrict__ P_off,
          const int* __restrict__ blk_col0, const int* __restrict__ blk_ldp,
          const double* __restrict__ r, double* __restrict__ x, TP* __restrict__ xlo, int M,
          int64_t ldx, int K, unsigned char* __restrict__ wpk, int nslab) {
+  using V = typename PVec<TP>::type;
+  constexpr int VE = PVec<TP>::n;
   constexpr int C = ClassPad<KC>::C;
   extern __shared__ __align__(16) unsigned char rs_raw[];
-  TP* rs = reinterpret_cast<TP*>(rs_raw);  // [ldp][KC]
+  TP* rs = reinterpret_cast<TP*>(rs_raw);  // [KC][ldp + 4]
   const int i = blockIdx.z, j = blockIdx.y;
   const int col0 = blk_col0[j], nj = blk_col0[j + 1] - col0, ldp = blk_ldp[j];
+  const int lds = ldp + 4;
   const int row_begin = blockIdx.x * ROWS;
   if (row_begin >= nj) return;
-  for (int e = threadIdx.x; e < ldp * KC; e += XT) {
-    const int bq = e / KC, k = e - bq * KC;
-    rs[e] = (bq < nj && k < K) ? static_cast<TP>(r[i * ldx + static_cast<int64_t>(col0 + bq) * K + k]) : TP(0);
+  for (int e = threadIdx.x; e < lds * KC; e += XT) rs[e] = TP(0);
+  __syncthreads();
+  const double* rsrc = r + i * ldx + static_cast<int64_t>(col0) * K;
+  for (int e = threadIdx.x; e < nj * K; e += XT) {  // contiguous reads
+    const int bq = e / K, k = e - bq * K;
+    rs[k * lds + bq] = static_cast<TP>(rsrc[e]);
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const TP* Pb = P + P_off[i * M + j];
+  const int nv = ldp / VE;
   for (int row = row_begin + warp; row < row_begin + ROWS && row < nj; row += XT / 32) {
-    const TP* pr = Pb + static_cast<int64_t>(row) * ldp;
+    const V* pr = reinterpret_cast<const V*>(Pb + static_cast<int64_t>(row) * ldp);
     TP acc[C];
 #pragma unroll
     for (int k = 0; k < C; ++k) acc[k] = TP(0);
-    for (int bq = lane; bq < nj; bq += 32) {
-      const TP pv = pr[bq];
-      const TP* rb = rs + bq * KC;
+    for (int bv = lane; bv < nv; bv += 32) {
+      const V pv = pr[bv];
+      const TP* pe = reinterpret_cast<const TP*>(&pv);
 #pragma unroll
-      for (int k = 0; k < KC; ++k) acc[k] = fma(pv, rb[k], acc[k]);
+      for (int k = 0; k < KC; ++k) {
+        const V rv = reinterpret_cast<const V*>(rs + k * lds)[bv];
+        const TP* re = reinterpret_cast<const TP*>(&rv);
+#pragma unroll
+        for (int e = 0; e < VE; ++e) acc[k] = fma(pe[e], re[e], acc[k]);
+      }
     }
     const TP sum = warp_reduce_scatter<C>(acc, lane);
     const int q = (lane >> (5 - (C == 4 ? 2 : (C == 8 ? 3 : 4)))) & (C - 1);
