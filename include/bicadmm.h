@@ -152,11 +152,13 @@ int bicadmm_solve(bicadmm_t h, bicadmm_info* info);
 /* Copy the model to host memory x_host[len], len = n K (the flattened n x K W for SOFTMAX).
  * polished = 0: the consensus iterate z.  polished = 1: the solution of the problem
  * restricted to S = the kappa largest |z_r| (ties to the lowest index), solved in FP64 by
- * damped Newton on the device (not part of the paper's algorithm; kappa <= 1024 and K = 1
- * (a softmax model is returned unpolished: ERR_UNSUPPORTED), else
+ * damped Newton on the device (not part of the paper's algorithm; kappa <= 1024, else
  * ERR_UNSUPPORTED; ERR_NUMERIC if the restricted Hessian is not positive definite).
+ * For SOFTMAX the support is the kappa largest entries of the flattened W and the restricted
+ * problem is the cross-entropy over those entries (the rest of W held at zero).
  * support_out (kappa entries, ascending) receives S when non-NULL.  Synchronises the
- * stream; the first polished call allocates the polish buffers (kappa x m doubles). */
+ * stream; the first polished call allocates the polish buffers (kappa x m doubles; twice
+ * that plus 4 m K doubles for SOFTMAX). */
 int bicadmm_get_x(bicadmm_t h, double* x_host, int64_t len, int32_t polished, int64_t* support_out);
 
 /* Copy one state field (BICADMM_FIELD_*) to host memory out_host[len]; len must equal the

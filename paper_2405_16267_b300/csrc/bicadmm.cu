@@ -107,6 +107,12 @@ struct bicadmm_ctx {
          *pHpart = nullptr, *pH = nullptr;
   int* pflag = nullptr;
   bool polish_ready = false;
+  // softmax polish (allocated on first use): support in class order, its classes and class
+  // offsets, A_S and U (kappa x m), per-row q, p, d1, P (m x K)
+  int64_t* ssupp = nullptr;
+  int *scls = nullptr, *skb = nullptr;
+  double *sU = nullptr, *sq = nullptr, *sp = nullptr, *sd1 = nullptr, *sP = nullptr;
+  bool spolish_ready = false;
 
   // profiling: CUDA events around kernel launches on the handle's stream
   int prof = 0;                 // 0 off, 1 the A pass only, 2 every kernel of the iteration
@@ -702,6 +708,8 @@ void handle_bytes(const bicadmm_ctx* h, int64_t* persistent, int64_t* setup_extr
   // polish: supp, A_S, q, d1, d2, p, x_S, step, partials, H
   b += kappa * 8 + kappa * m * 8 + 4 * m * 8 + 2 * kappa * 8 + kPolishRowBlocks * 8 +
        static_cast<int64_t>(kPolishChunks) * kappa * 8 + (kPolishChunks + 1) * kappa * kappa * 8;
+  if (h->K > 1)  // softmax polish: U (kappa x m) and q, p, d1, P (m x K)
+    b += kappa * m * 8 + 4 * m * h->K * 8 + kappa * 12;
   if (persistent) *persistent = b;
   if (setup_extra) *setup_extra = std::min<int64_t>(256ll << 20, m * lda * 8) + h->G_total * 8;
 }
@@ -987,6 +995,139 @@ int run_polish(bicadmm_ctx* h, std::vector<double>& xs_out) {
   CK(cudaStreamSynchronize(h->stream));
   xs_out = xs;
   return BICADMM_OK;
+}
+
+// Softmax polish: the same damped Newton on the kappa support entries of W (polish.cuh,
+// softmax section).  supp_out receives the support in class order (matching xs_out).
+template <typename TA, typename TM, int KC>
+int run_polish_softmax(bicadmm_ctx* h, std::vector<double>& xs_out, std::vector<int64_t>& supp_out) {
+  const int64_t m = h->p.m;
+  const int kappa = static_cast<int>(h->p.kappa), K = h->K;
+  const double gamma = h->p.gamma;
+  const int nblk = static_cast<int>(std::min<int64_t>(kPolishRowBlocks, (m + 255) / 256));
+  const int nch = static_cast<int>(std::min<int64_t>(kPolishChunks, (m + 255) / 256));
+  const int64_t chunk = (m + nch - 1) / nch;
+  int rc;
+  if (!h->polish_ready) {  // shared buffers of the K = 1 polish (sizes in kappa only) + A_S
+#define AL(ptr, bytes) if ((rc = dev_alloc(h, &(ptr), (bytes))) != BICADMM_OK) return rc
+    AL(h->AS, static_cast<size_t>(kappa) * m * sizeof(double));
+    AL(h->pxs, kappa * sizeof(double));
+    AL(h->pstep, kappa * sizeof(double));
+    AL(h->pfpart, nblk * sizeof(double));
+    AL(h->pgpart, static_cast<size_t>(nch) * kappa * sizeof(double));
+    AL(h->pHpart, static_cast<size_t>(nch) * kappa * kappa * sizeof(double));
+    AL(h->pH, static_cast<size_t>(kappa) * kappa * sizeof(double));
+    AL(h->pflag, sizeof(int));
+    AL(h->pq, m * sizeof(double));  // unused by the softmax polish; keeps the K = 1 set complete
+    AL(h->pd1, m * sizeof(double));
+    AL(h->pd2, m * sizeof(double));
+    AL(h->pp, m * sizeof(double));
+    h->polish_ready = true;
+  }
+  if (!h->spolish_ready) {
+    AL(h->ssupp, kappa * sizeof(int64_t));
+    AL(h->scls, kappa * sizeof(int));
+    AL(h->skb, (K + 1) * sizeof(int));
+    AL(h->sU, static_cast<size_t>(kappa) * m * sizeof(double));
+    AL(h->sq, static_cast<size_t>(m) * K * sizeof(double));
+    AL(h->sp, static_cast<size_t>(m) * K * sizeof(double));
+    AL(h->sd1, static_cast<size_t>(m) * K * sizeof(double));
+    AL(h->sP, static_cast<size_t>(m) * K * sizeof(double));
+#undef AL
+    h->spolish_ready = true;
+  }
+  if ((rc = compute_support(h)) != BICADMM_OK) return rc;
+  std::vector<int64_t> sp(kappa);
+  CK(cudaMemcpyAsync(sp.data(), h->supp, kappa * sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  // class order (stable within a class: ascending flat index)
+  std::vector<int64_t> ord;
+  std::vector<int> cls, kb(K + 1, 0);
+  for (int k = 0; k < K; ++k) {
+    kb[k] = static_cast<int>(ord.size());
+    for (int e = 0; e < kappa; ++e)
+      if (sp[e] % K == k) { ord.push_back(sp[e]); cls.push_back(k); }
+  }
+  kb[K] = kappa;
+  CK(cudaMemcpyAsync(h->ssupp, ord.data(), kappa * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->scls, cls.data(), kappa * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->skb, kb.data(), (K + 1) * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  const dim3 ggrid(static_cast<unsigned>(std::min<int64_t>((m + 255) / 256, 1024)), kappa);
+  k_gather_support<TA><<<ggrid, 256, 0, h->stream>>>(static_cast<const TA*>(h->A), h->lda, h->ssupp, m, h->AS, K);
+  CK(cudaGetLastError());
+  h->launches += 1;
+  std::vector<double> xs(kappa, 0.0), step(kappa), fpart(nblk);
+  CK(cudaMemsetAsync(h->pxs, 0, kappa * sizeof(double), h->stream));
+  const int T = (kappa + 31) / 32;
+  const size_t ksm = kappa * sizeof(double);
+  auto objective = [&](double alpha, double* out) -> int {
+    k_polish_rows_sm<TM, KC, 256><<<nblk, 256, ksm, h->stream>>>(
+        h->AS, h->pxs, h->skb, K, m, static_cast<const TM*>(h->b), h->sq, h->sp, h->sd1, h->sP,
+        alpha, h->pfpart, kappa);
+    CK(cudaGetLastError());
+    h->launches += 1;
+    CK(cudaMemcpyAsync(fpart.data(), h->pfpart, nblk * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    double f = 0.0;
+    for (double v : fpart) f += v;
+    *out = f;
+    return BICADMM_OK;
+  };
+  for (int it = 0; it < 100; ++it) {
+    double f0;
+    if ((rc = objective(0.0, &f0)) != BICADMM_OK) return rc;  // also fills q, p, d1
+    double xx = 0.0;
+    for (double v : xs) xx += v * v;
+    f0 += xx / (2.0 * gamma);
+    k_polish_grad_sm<256><<<dim3(nch, kappa), 256, 0, h->stream>>>(h->AS, h->sd1, h->scls, K, kappa, m, chunk, h->pgpart);
+    k_polish_u_sm<<<dim3(static_cast<unsigned>(std::min<int64_t>((m + 255) / 256, 256)), kappa), 256, 0, h->stream>>>(
+        h->AS, h->sp, h->scls, K, kappa, m, h->sU);
+    k_polish_hess_sm<<<dim3(T * (T + 1) / 2, nch), 256, 0, h->stream>>>(h->AS, h->sU, h->scls, kappa, m, chunk, h->pHpart);
+    k_polish_solve<256><<<1, 256, 2 * ksm, h->stream>>>(h->pHpart, h->pgpart, nch, h->pxs, kappa, gamma,
+                                                        h->pH, h->pstep, h->pflag);
+    k_polish_dir_sm<KC, 256><<<nblk, 256, ksm, h->stream>>>(h->AS, h->pstep, h->skb, K, kappa, m, h->sP);
+    CK(cudaGetLastError());
+    h->launches += 5;
+    int flag = 0;
+    CK(cudaMemcpyAsync(step.data(), h->pstep, kappa * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&flag, h->pflag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (flag) return fail(h, BICADMM_ERR_NUMERIC, "polish: restricted Hessian is not positive definite");
+    double alpha = 1.0;
+    for (;;) {
+      double ft;
+      if ((rc = objective(alpha, &ft)) != BICADMM_OK) return rc;
+      double x2 = 0.0;
+      for (int k = 0; k < kappa; ++k) {
+        const double v = xs[k] - alpha * step[k];
+        x2 += v * v;
+      }
+      ft += x2 / (2.0 * gamma);
+      if (!(ft > f0 + 1e-16 * std::fabs(f0)) || !(alpha > 1e-12)) break;
+      alpha *= 0.5;
+    }
+    double sn = 0.0, xn = 0.0;
+    for (int k = 0; k < kappa; ++k) {
+      xs[k] -= alpha * step[k];
+      sn += (alpha * step[k]) * (alpha * step[k]);
+      xn += xs[k] * xs[k];
+    }
+    CK(cudaMemcpyAsync(h->pxs, xs.data(), kappa * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (std::sqrt(sn) <= 1e-13 * std::max(1.0, std::sqrt(xn))) break;
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  xs_out = xs;
+  supp_out = ord;
+  return BICADMM_OK;
+}
+
+template <typename TA, typename TM>
+int run_polish_softmax_k(bicadmm_ctx* h, std::vector<double>& xs, std::vector<int64_t>& sp) {
+  switch (h->KC) {
+    case 4: return run_polish_softmax<TA, TM, 4>(h, xs, sp);
+    case 10: return run_polish_softmax<TA, TM, 10>(h, xs, sp);
+    default: return run_polish_softmax<TA, TM, 16>(h, xs, sp);
+  }
 }
 
 }  // namespace
@@ -1422,14 +1563,21 @@ int bicadmm_get_x(bicadmm_t h, double* x_host, int64_t len, int32_t polished, in
   if (!x_host || len != nK) return fail(h, BICADMM_ERR_ARG, "x_host must hold n K doubles");
   if (polished && h->p.kappa > kMaxPolishKappa)
     return fail(h, BICADMM_ERR_UNSUPPORTED, "polish supports kappa <= 1024");
-  if (polished && h->K > 1)
-    return fail(h, BICADMM_ERR_UNSUPPORTED, "polish is not implemented for the softmax loss");
   if (!polished) {
     CK(cudaMemcpyAsync(x_host, h->z, nK * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     if (support_out) {
       int rc = compute_support(h);
       if (rc != BICADMM_OK) return rc;
     }
+  } else if (h->K > 1) {
+    std::vector<double> xs;
+    std::vector<int64_t> sp;
+    int rc = h->p.precision == BICADMM_PREC_FP64 ? run_polish_softmax_k<double, double>(h, xs, sp)
+             : h->p.precision == BICADMM_PREC_FP32 ? run_polish_softmax_k<float, float>(h, xs, sp)
+                                                   : run_polish_softmax_k<__nv_bfloat16, float>(h, xs, sp);
+    if (rc != BICADMM_OK) return rc;
+    std::fill(x_host, x_host + nK, 0.0);
+    for (int64_t k = 0; k < h->p.kappa; ++k) x_host[sp[k]] = xs[k];
   } else {
     std::vector<double> xs;
     int rc = h->p.precision == BICADMM_PREC_FP64 ? run_polish<double, double>(h, xs)

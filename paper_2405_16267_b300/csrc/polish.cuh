@@ -72,12 +72,13 @@ k_support(const double* __restrict__ z, uint64_t* __restrict__ key, int64_t n, i
     if (sel[q >> 5] >> (q & 31) & 1u) supp[pos++] = cb + q;
 }
 
-// AS[k*m + r] = A[r, supp[k]] in FP64.  Grid (row chunks, kappa).
+// AS[k*m + r] = A[r, supp[k] / K] in FP64 (K = 1: the support's columns; softmax: the
+// feature of each support entry (c, class) = c K + class).  Grid (row chunks, kappa).
 template <typename TA>
 __global__ void k_gather_support(const TA* __restrict__ A, int64_t lda, const int64_t* __restrict__ supp,
-                                 int64_t m, double* __restrict__ AS) {
+                                 int64_t m, double* __restrict__ AS, int K = 1) {
   const int k = blockIdx.y;
-  const int64_t col = supp[k];
+  const int64_t col = supp[k] / K;
   for (int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < m;
        r += static_cast<int64_t>(gridDim.x) * blockDim.x)
     AS[k * m + r] = conv<double>(A[r * lda + col]);
@@ -259,6 +260,174 @@ k_polish_solve(const double* __restrict__ Hpart, const double* __restrict__ gpar
       double sacc = y[a];
       for (int bq = a + 1; bq < kappa; ++bq) sacc -= H[static_cast<int64_t>(bq) * kappa + a] * step[bq];
       step[a] = sacc / H[static_cast<int64_t>(a) * kappa + a];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- softmax polish
+// Restricted softmax problem on the support entries e = (c_e, k_e) of W (flattened c K + k),
+// with the entries ordered by class (class k owns entries kb[k] .. kb[k+1]-1) and x_e their
+// values:  minimise sum_r CE(q_r; y_r) + ||x||^2 / (2 gamma),  q_rk = sum_{e in k} a_{r c_e} x_e.
+// Gradient g_e = sum_r a_{r c_e} (p_{r k_e} - [y_r = k_e]) + x_e / gamma; Hessian
+// H_ee' = sum_r a_{r c_e} a_{r c_e'} p_{r k_e} ([k_e = k_e'] - p_{r k_e'}) + [e = e'] / gamma
+//       = [k_e = k_e'] (U' A_S)_ee' - (U' U)_ee',   U_e = a_{c_e} * p_{k_e} (row-wise).
+
+// Per row: q (K scores) from A_S and x (or q - alpha P for a trial point), softmax p, the
+// loss; stores q, p and d1 = p - onehot(y) when alpha = 0; per-CTA partial objective.
+template <typename TM, int KC, int T>
+__global__ void __launch_bounds__(T)
+k_polish_rows_sm(const double* __restrict__ AS, const double* __restrict__ x,
+                 const int* __restrict__ kb, int K, int64_t m, const TM* __restrict__ b,
+                 double* __restrict__ q, double* __restrict__ pr, double* __restrict__ d1,
+                 const double* __restrict__ P, double alpha, double* __restrict__ fpart, int kappa) {
+  __shared__ double red[32];
+  extern __shared__ double xs[];
+  for (int k = threadIdx.x; k < kappa; k += T) xs[k] = x[k];
+  __shared__ int kbs[KC + 1];
+  for (int k = threadIdx.x; k <= K; k += T) kbs[k] = kb[k];
+  __syncthreads();
+  double facc = 0.0;
+  for (int64_t r = static_cast<int64_t>(blockIdx.x) * T + threadIdx.x; r < m;
+       r += static_cast<int64_t>(gridDim.x) * T) {
+    double qr[KC];
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+      double acc = 0.0;
+      if (k < K) {
+        if (alpha != 0.0) {
+          acc = q[r * K + k] - alpha * P[r * K + k];
+        } else {
+          for (int e = kbs[k]; e < kbs[k + 1]; ++e) acc = fma(AS[e * m + r], xs[e], acc);
+          q[r * K + k] = acc;
+        }
+      }
+      qr[k] = acc;
+    }
+    double mx = -HUGE_VAL;
+#pragma unroll
+    for (int k = 0; k < KC; ++k) if (k < K) mx = fmax(mx, qr[k]);
+    double ssum = 0.0, ex[KC];
+#pragma unroll
+    for (int k = 0; k < KC; ++k) { ex[k] = k < K ? exp(qr[k] - mx) : 0.0; ssum += ex[k]; }
+    const int y = static_cast<int>(b[r]);
+    double qy = 0.0;
+#pragma unroll
+    for (int k = 0; k < KC; ++k) if (k == y) qy = qr[k];
+    facc += mx + log(ssum) - qy;
+    if (alpha == 0.0) {
+#pragma unroll
+      for (int k = 0; k < KC; ++k) {
+        if (k < K) {
+          const double pk = ex[k] / ssum;
+          pr[r * K + k] = pk;
+          d1[r * K + k] = pk - (k == y ? 1.0 : 0.0);
+        }
+      }
+    }
+  }
+  double v[1] = {facc};
+  block_sum<1>(v, red);
+  if (threadIdx.x == 0) fpart[blockIdx.x] = v[0];
+}
+
+// Partial gradient of the softmax polish: gpart[c*kappa + e] = sum over rows of chunk c of
+// AS[e, r] d1[r, k_e].  Grid (chunks, kappa).
+template <int T>
+__global__ void k_polish_grad_sm(const double* __restrict__ AS, const double* __restrict__ d1,
+                                 const int* __restrict__ cls, int K, int kappa, int64_t m,
+                                 int64_t chunk, double* __restrict__ gpart) {
+  __shared__ double red[32];
+  const int e = blockIdx.y, c = blockIdx.x, ke = cls[e];
+  const int64_t r0 = c * chunk, r1 = r0 + chunk < m ? r0 + chunk : m;
+  double acc = 0.0;
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += T) acc = fma(AS[e * m + r], d1[r * K + ke], acc);
+  double v[1] = {acc};
+  block_sum<1>(v, red);
+  if (threadIdx.x == 0) gpart[static_cast<int64_t>(c) * kappa + e] = v[0];
+}
+
+// U[e, r] = AS[e, r] p[r, k_e].
+__global__ void k_polish_u_sm(const double* __restrict__ AS, const double* __restrict__ pr,
+                              const int* __restrict__ cls, int K, int kappa, int64_t m,
+                              double* __restrict__ U) {
+  const int e = blockIdx.y, ke = cls[e];
+  for (int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < m;
+       r += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    U[e * m + r] = AS[e * m + r] * pr[r * K + ke];
+}
+
+// Partial Hessian of the softmax polish, Hpart[c] = [k_e = k_e'] (U' A_S) - U' U over the rows
+// of chunk c (upper tiles, mirrored).  Grid (tile pairs, chunks), 256 threads, 32 x 32 tiles.
+__global__ void __launch_bounds__(256)
+k_polish_hess_sm(const double* __restrict__ AS, const double* __restrict__ U,
+                 const int* __restrict__ cls, int kappa, int64_t m, int64_t chunk,
+                 double* __restrict__ Hpart) {
+  constexpr int TL = 32, KC = 16;
+  __shared__ double Us[KC][TL + 1];
+  __shared__ double As_[KC][TL + 1];
+  __shared__ double Uq[KC][TL + 1];
+  const int T = (kappa + TL - 1) / TL;
+  int qq = blockIdx.x, ti = 0;
+  while (qq >= T - ti) { qq -= T - ti; ++ti; if (ti >= T) return; }
+  const int tj = ti + qq;
+  const int c = blockIdx.y;
+  const int64_t r0 = c * chunk, r1 = r0 + chunk < m ? r0 + chunk : m;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double aA[2][2] = {{0.0, 0.0}, {0.0, 0.0}}, aU[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int64_t rb = r0; rb < r1; rb += KC) {
+    for (int e = threadIdx.x; e < KC * TL; e += 256) {
+      const int cc = e / KC, rr = e - cc * KC;
+      const int64_t r = rb + rr;
+      const int pi = ti * TL + cc, qi = tj * TL + cc;
+      const bool okr = r < r1;
+      Us[rr][cc] = (okr && pi < kappa) ? U[pi * m + r] : 0.0;
+      As_[rr][cc] = (okr && qi < kappa) ? AS[qi * m + r] : 0.0;
+      Uq[rr][cc] = (okr && qi < kappa) ? U[qi * m + r] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < KC; ++rr) {
+      const double u0 = Us[rr][ty * 2], u1 = Us[rr][ty * 2 + 1];
+      const double a0 = As_[rr][tx * 2], a1 = As_[rr][tx * 2 + 1];
+      const double v0 = Uq[rr][tx * 2], v1 = Uq[rr][tx * 2 + 1];
+      aA[0][0] = fma(u0, a0, aA[0][0]); aA[0][1] = fma(u0, a1, aA[0][1]);
+      aA[1][0] = fma(u1, a0, aA[1][0]); aA[1][1] = fma(u1, a1, aA[1][1]);
+      aU[0][0] = fma(u0, v0, aU[0][0]); aU[0][1] = fma(u0, v1, aU[0][1]);
+      aU[1][0] = fma(u1, v0, aU[1][0]); aU[1][1] = fma(u1, v1, aU[1][1]);
+    }
+    __syncthreads();
+  }
+  double* H = Hpart + static_cast<int64_t>(c) * kappa * kappa;
+  for (int a = 0; a < 2; ++a)
+    for (int bq = 0; bq < 2; ++bq) {
+      const int pi = ti * TL + ty * 2 + a, qi = tj * TL + tx * 2 + bq;
+      if (pi < kappa && qi < kappa) {
+        const double v = (cls[pi] == cls[qi] ? aA[a][bq] : 0.0) - aU[a][bq];
+        H[static_cast<int64_t>(pi) * kappa + qi] = v;
+        H[static_cast<int64_t>(qi) * kappa + pi] = v;
+      }
+    }
+}
+
+// P[r, k] = sum_{e in class k} AS[e, r] step[e].
+template <int KC, int T>
+__global__ void k_polish_dir_sm(const double* __restrict__ AS, const double* __restrict__ step,
+                                const int* __restrict__ kb, int K, int kappa, int64_t m,
+                                double* __restrict__ P) {
+  extern __shared__ double ss[];
+  __shared__ int kbs[KC + 1];
+  for (int k = threadIdx.x; k < kappa; k += T) ss[k] = step[k];
+  for (int k = threadIdx.x; k <= K; k += T) kbs[k] = kb[k];
+  __syncthreads();
+  for (int64_t r = static_cast<int64_t>(blockIdx.x) * T + threadIdx.x; r < m;
+       r += static_cast<int64_t>(gridDim.x) * T) {
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+      if (k < K) {
+        double acc = 0.0;
+        for (int e = kbs[k]; e < kbs[k + 1]; ++e) acc = fma(AS[e * m + r], ss[e], acc);
+        P[r * K + k] = acc;
+      }
     }
   }
 }

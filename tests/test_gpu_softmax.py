@@ -122,3 +122,22 @@ def test_softmax_rejects_bad_labels_and_params():
         bc.Solver(P.A, bad, loss=P.loss, N=2, M=2, kappa=4, K=3, stream=torch.cuda.current_stream())
     with pytest.raises(bc.BicadmmError):  # K = 1 with softmax
         bc.Solver(P.A, P.b, loss=P.loss, N=2, M=2, kappa=4, K=1, stream=torch.cuda.current_stream())
+
+
+@pytest.mark.parametrize("precision", [bc.PREC_FP64, bc.PREC_BF16])
+def test_softmax_polish_vs_oracle(precision):
+    """FP64 polish on the entrywise support: the restricted softmax problem solved by damped
+    Newton on the device equals the oracle's polish on the same support (and the same data:
+    the BF16-rounded A for BF16 storage)."""
+    import torch
+    P = synth.sparse_softmax(m=3000, n=40, K=4, nnz=8, N=3, M=2, kappa=8, seed=17, dtype=np.float64,
+                             scale=1.5)
+    A_used = P.A if precision == bc.PREC_FP64 else synth.round_to_bf16(P.A)
+    A_in = P.A if precision == bc.PREC_FP64 else P.A.astype(np.float32)
+    with bc.Solver(A_in, P.b, loss=P.loss, N=P.N, M=P.M, kappa=P.kappa, gamma=P.gamma, rho_c=P.rho,
+                   K=P.K, precision=precision, stream=torch.cuda.current_stream()) as s:
+        s.step(60)
+        x, sup = bc.get_x(s.h, P.n * P.K, polished=True, with_support=True, kappa=P.kappa)
+    want = ref.polish(A_used, P.b, ref.LOSS_SOFTMAX, P.gamma, np.array(sup), K=P.K)
+    assert np.count_nonzero(x) <= P.kappa
+    np.testing.assert_allclose(x, want, rtol=0, atol=1e-9 * np.abs(want).max())
