@@ -163,19 +163,27 @@ PASS_SOURCES = ["paper_2405_16267_b300/csrc/pass.cuh", "paper_2405_16267_b300/cs
                 "paper_2405_16267_b300/csrc/common.cuh"]
 
 
-def pass_sources_sha256():
+# The same for the tensor-core softmax pass (60000-row capture scaled to 500000 rows).
+TC_TRAFFIC = {"sources_sha256": "a7c5f89a467ff17533ec8392090bc51eba31cb3639c4c9806d66c5eda11a5fe6", "bytes_per_launch": 2.437e9,
+              "capture": "profiles/k_fused_pass_tc_sparse_softmax_500000x2000x10_bf16.md"}
+TC_SOURCES = ["paper_2405_16267_b300/csrc/mc_tc.cuh", "paper_2405_16267_b300/csrc/nspace.cuh",
+              "paper_2405_16267_b300/csrc/common.cuh", "paper_2405_16267_b300/csrc/pass.cuh"]
+
+
+def pass_sources_sha256(sources=None):
     import hashlib
     h = hashlib.sha256()
-    for rel in PASS_SOURCES:
+    for rel in (PASS_SOURCES if sources is None else sources):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
 
 
-def pass_traffic():
+def pass_traffic(guard=None, sources=None):
+    guard = PASS_TRAFFIC if guard is None else guard
     try:
-        if pass_sources_sha256() == PASS_TRAFFIC["sources_sha256"]:
-            return PASS_TRAFFIC["bytes_per_launch"]
+        if pass_sources_sha256(sources) == guard["sources_sha256"]:
+            return guard["bytes_per_launch"]
     except OSError:
         pass
     return None
@@ -437,7 +445,9 @@ def run_softmax(args, rank, world):
         "data": "synthetic (seeded; Gaussian A, 500-entry planted W*, Gumbel-argmax labels)",
         "config": cfg,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "kernel": "k_fused_pass_tc",
+                     "frac": achieved / hbm,
+                     "traffic": pass_traffic(TC_TRAFFIC, TC_SOURCES) if wl["m"] == SOFTMAX["m"] else None,
+                     "kernel": "k_fused_pass_tc",
                      "peak_kind": peak_kind + " copy bandwidth",
                      "algorithmic_bytes_per_launch": pass_bytes, "avg_launch_ms": avg_pass_s * 1e3,
                      "launches_timed": pass_launches},
