@@ -215,11 +215,9 @@ __device__ __forceinline__ void softmax_prox_row(float (&w)[KC], const float (&a
 // Warp roles (256 threads): warps 0-3 own the 128 TMEM lanes (epilogue and slot flush),
 // warp 4 lane 0 issues the loads, warp 5 lane 0 issues tcgen05.mma, warps 6-7 idle.
 //
-// Panels are 64 rows.  The forward MMA has M = 128: for even panels its descriptor starts
-// at the box, so the panel rows land in TMEM lanes 0-63 (epilogue warps 0-1); for odd
-// panels it starts 8 KB (64 rows) earlier, so they land in lanes 64-127 (warps 2-3).  The
-// other 64 M-rows read neighbouring shared memory and give lanes that are never read.
-// The two warp pairs run the prox of alternate panels concurrently.
+// Panels are 64 rows.  The forward MMA has M = 64; its accumulator puts row r in TMEM lane
+// 32 (r / 16) + r % 16 (measured), so each of the four epilogue warps owns 16 panel rows
+// (lanes 0-15 of its sub-partition) and all four run the per-row prox of every panel.
 //
 // W_i is read from global memory in its MMA layout (per 64-column box a 32 x 64 BF16 tile:
 // rows 0-15 the hi parts of the 16 classes, rows 16-31 the lo parts; written by
@@ -246,8 +244,8 @@ constexpr int kTcTmemCols = 512;                   // D1 x2 at 0 / 32, D2 slab s
 constexpr int kTcD2Col = 64;
 
 inline size_t fused_pass_tc_smem() {
-  // alignment, a 64-row lead-in read by odd panels of stage 0, ring, d tiles, barriers
-  return 1024 + kTcBoxBytes + static_cast<size_t>(kTcStages) * kTcStageBytes + kTcDBytes + 256;
+  // alignment, ring, d tiles, barriers
+  return 1024 + static_cast<size_t>(kTcStages) * kTcStageBytes + kTcDBytes + 256;
 }
 
 // Bounded wait that also gives up once another role has raised *abort.
@@ -274,12 +272,12 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
     return;
   }
   constexpr int S = kTcStages;
-  constexpr uint32_t IDESC_FWD = idesc_bf16(128, 32, false, false);
+  constexpr uint32_t IDESC_FWD = idesc_bf16(64, 32, false, false);
   constexpr uint32_t IDESC_BWD = idesc_bf16(128, 16, true, false);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  unsigned char* ring = base + kTcBoxBytes;
+  unsigned char* ring = base;
   unsigned char* ds = ring + S * kTcStageBytes;
   uint64_t* full = reinterpret_cast<uint64_t*>(ds + kTcDBytes);
   uint64_t* empty = full + S;
@@ -309,8 +307,8 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
     }
     mbar_init(&d1full[0], 1);
     mbar_init(&d1full[1], 1);
-    mbar_init(&dready[0], 64);
-    mbar_init(&dready[1], 64);
+    mbar_init(&dready[0], 128);
+    mbar_init(&dready[1], 128);
     mbar_init(bwddone, 1);
     mbar_init(flushed, 128);
     mbar_init(drainbar, 1);
@@ -418,8 +416,6 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
           bwd_shard = sh;
         }
         tc_fence_after();
-        // odd panels: M-rows 64..127 are the panel rows (TMEM lanes 64..127)
-        const uint32_t lead = (k & 1) ? kTcBoxBytes : 0u;
         for (int sg = 0; sg < nstage; ++sg, ++j) {
           const int st = static_cast<int>(j % S);
           // TMA completion on the stage barrier makes the data visible to the MMAs (both
@@ -432,7 +428,7 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
             for (int bx = 0; bx < 4; ++bx)
 #pragma unroll
               for (int ks = 0; ks < 4; ++ks)
-                umma_bf16_warp(d1, dsc(tk, sa + bx * kTcBoxBytes - lead + ks * 32),
+                umma_bf16_warp(d1, dsc(tk, sa + bx * kTcBoxBytes + ks * 32),
                                dsc(tk, sa + kTcStageABytes + bx * 4096 + ks * 32), IDESC_FWD,
                                (sg | bx | ks) != 0 ? 1u : 0u);
           } else {
@@ -471,12 +467,12 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
   } else if (warp < 4) {
     // ---------------------------------------------------------------- epilogue warps
     const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
-    const int pair = warp >> 1;  // panels of this parity
-    const int r = tid & 63;      // panel row of this thread
+    const bool has_row = lane < 16;        // M = 64 accumulator: lanes 0-15 of each warp
+    const int r = warp * 16 + (lane & 15);  // panel row of this thread
     int seg = 0;
     bool eok = true;
     PanelWalk pw;
-    // prefetched row data of this pair's next panel
+    // prefetched row data of the next panel
     float nur[KC], wv[KC];
     int y = 0;
     auto prefetch = [&](int k) {
@@ -486,7 +482,7 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
         PanelWalk t;
         t.at(geo, p_begin + k, row0, nrows, sh);
       }
-      const bool valid = k < np && r < nrows;
+      const bool valid = has_row && k < np && r < nrows;
 #pragma unroll
       for (int q = 0; q < KC; ++q) {
         nur[q] = (valid && q < K) ? nu[(row0 + r) * K + q] : 0.f;
@@ -494,18 +490,18 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
       }
       y = valid ? static_cast<int>(b[row0 + r]) : 0;
     };
-    prefetch(pair);
+    prefetch(0);
     for (int k = 0; k < np && eok; ++k) {
       int64_t row0;
       int nrows, shard;
       pw.at(geo, p_begin + k, row0, nrows, shard);
-      if ((k & 1) == pair) {
+      {
         if (!mbar_wait_or_abort(&d1full[k & 1], static_cast<uint32_t>((k >> 1) & 1), wait_limit, abort_v)) { eok = false; break; }
         tc_fence_after();
         uint32_t v[16], vl[16];
         tmem_ld16(tmem + lane_base + 32 * (k & 1), v);
         tmem_ld16(tmem + lane_base + 32 * (k & 1) + 16, vl);
-        const bool valid = r < nrows;
+        const bool valid = has_row && r < nrows;
         float Axb[KC], aa[KC], w[KC], nk[KC];
         const int yk = y;
 #pragma unroll
@@ -515,7 +511,7 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
           w[q] = wv[q];
           aa[q] = Axb[q] + nk[q];
         }
-        prefetch(k + 2);  // this pair's next panel: loads overlap the prox
+        prefetch(k + 1);  // the next panel's rows: the loads overlap the prox
         if (valid) softmax_prox_row<KC>(w, aa, yk, K, Mf, rho_l, newton_iters);
         unsigned char* dbuf = ds + (k & 1) * 4096;
 #pragma unroll
@@ -533,9 +529,11 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
           }
           const __nv_bfloat16 hi = __float2bfloat16_rn(dv);
           const __nv_bfloat16 lo = __float2bfloat16_rn(dv - __bfloat162float(hi));
-          const uint32_t off = sw128_off(q, r);
-          *reinterpret_cast<__nv_bfloat16*>(dbuf + off) = hi;
-          *reinterpret_cast<__nv_bfloat16*>(dbuf + 2048 + off) = lo;
+          if (has_row) {
+            const uint32_t off = sw128_off(q, r);
+            *reinterpret_cast<__nv_bfloat16*>(dbuf + off) = hi;
+            *reinterpret_cast<__nv_bfloat16*>(dbuf + 2048 + off) = lo;
+          }
         }
         fence_async_smem();
         tc_fence_before();
