@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=200.0, help="mean arrivals/s (serve)")
     ap.add_argument("--serve-iters", type=int, default=100, help="iteration cap per request")
     ap.add_argument("--batch", type=int, default=256, help="instances in the batch workload")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
+                    help="storage precision of A in the batch and serve workloads")
     return ap.parse_args()
 
 
@@ -494,6 +496,8 @@ def run_batch(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     specs = synth.batch_instance_specs(count=args.batch)
+    prec = bc.PREC_BF16 if args.precision == "bf16" else bc.PREC_FP32
+    a_es = 2 if args.precision == "bf16" else 4
     stream = torch.cuda.Stream()
     solvers, a_bytes, rows = [], 0, 0
     t0 = time.perf_counter()
@@ -501,9 +505,9 @@ def run_batch(args, rank, world):
         for P in ex.map(synth.batch_instance, specs):
             with torch.cuda.stream(stream):
                 solvers.append(bc.Solver(P.A, P.b, loss=P.loss, N=P.N, M=P.M, kappa=P.kappa,
-                                         gamma=P.gamma, rho_c=P.rho, precision=bc.PREC_FP32,
+                                         gamma=P.gamma, rho_c=P.rho, precision=prec,
                                          stream=stream))
-            a_bytes += P.m * P.n * 4 + 16 * P.m
+            a_bytes += P.m * P.n * a_es + 16 * P.m
             rows += P.m
     setup_s = time.perf_counter() - t0
     b = bc.batch_create(solvers, stream=stream, flags=bc.BATCH_GRAPH | bc.BATCH_AUTOTUNE)
@@ -544,9 +548,9 @@ def run_batch(args, rank, world):
         "value": aggregate_value(world, args.steps, ms / 1000.0), "unit": "batch iters/s",
         "instance_iters_per_s": args.batch * args.steps / (ms / 1000.0),
         "n_gpus": world, "steps": args.steps, "warmup": warm, "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (seeded)",
-        "config": {"workload": "batch%d_uneven_linear_sqhinge_fp32" % args.batch,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if args.precision == "bf16" else "f32", "data": "synthetic (seeded)",
+        "config": {"workload": "batch%d_uneven_linear_sqhinge_%s" % (args.batch, args.precision),
                    "instances": args.batch, "rows_total": rows, "A_bytes": a_bytes,
                    "graph": True, "autotuned_tiling": {"stage_kb": tiling[0], "stages": tiling[1]},
                    "l2": "inputs larger than L2 (%.1f GB)" % (a_bytes / 1e9)},
@@ -576,13 +580,14 @@ def run_serve(args, rank, world):
     data = [synth.device_request(sp) for sp in specs]
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
-    a_bytes = sum(sp["m"] * sp["n"] * 4 for sp in specs)
+    prec = bc.PREC_BF16 if args.precision == "bf16" else bc.PREC_FP32
+    a_bytes = sum(sp["m"] * sp["n"] * (2 if args.precision == "bf16" else 4) for sp in specs)
     clocks = ClockSampler(local)
     with bc.Server(hbm_budget_bytes=150 << 30, max_active=64, iters_per_round=10,
-                   precision=bc.PREC_FP32, use_graph=True, polish=True) as srv:
+                   precision=prec, use_graph=True, polish=True) as srv:
         t0 = srv.clock() + 0.05
         ids = [srv.submit(A, b, arrival=t0 + sp["arrival"], loss=sp["loss"],
-                          precision=bc.PREC_FP32, N_shards=sp["N"], M_blocks=sp["M"],
+                          precision=prec, N_shards=sp["N"], M_blocks=sp["M"],
                           kappa=sp["kappa"], gamma=10.0, rho_c=1.0, max_iters=args.serve_iters,
                           tol_rel=1e-6)
                for sp, (A, b) in zip(specs, data)]
@@ -597,9 +602,10 @@ def run_serve(args, rank, world):
     return {
         "metric": "solves/s (serving, continuous batching)", "value": len(ok) / span,
         "unit": "solves/s", "n_gpus": world, "steps": len(res), "warmup": 0,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if args.precision == "bf16" else "f32",
         "data": "synthetic (seeded, drawn on the device)",
-        "config": {"workload": "serve_poisson%d_mixed_fp32" % int(args.rate),
+        "config": {"workload": "serve_poisson%d_mixed_%s" % (int(args.rate), args.precision),
                    "requests": len(res), "arrival_rate_per_s": args.rate,
                    "offered_A_bytes": a_bytes, "hbm_budget_bytes": 150 << 30,
                    "iters_per_request_cap": args.serve_iters, "tol_rel": 1e-6,

@@ -215,7 +215,7 @@ int bicadmm_consensus_step_noalloc(const double* w, double* z, double* s, double
  * persistent A pass over a panel list spanning every instance's shards, consensus step,
  * dual update).  Each instance's iterates are those of bicadmm_step up to rounding (the
  * A'd partial sums are grouped differently).  Requirements: every handle set up, all of
- * one precision (FP64 or FP32) and device, inner_iters = 1, K = 1.  The batch references the handles (it does
+ * one precision and device, inner_iters = 1, K = 1.  The batch references the handles (it does
  * not own them); destroy the batch before any of its handles.  Handles may still be stepped
  * alone between batch steps.
  * flags: BICADMM_BATCH_GRAPH captures one iteration into a CUDA graph and replays it (needs

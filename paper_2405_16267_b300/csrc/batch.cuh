@@ -11,6 +11,8 @@
 // so the dual kernel sums the right slots.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "nspace.cuh"
 #include "pass.cuh"
@@ -126,7 +128,9 @@ k_fused_pass_batch(const BatchInst* __restrict__ inst, const BatchSeg* __restric
     for (; n_issued < np && n_issued < S; ++n_issued) issue(n_issued);
   }
 
-  TA xr[VPT][VE];
+  // x_i in the storage type when it is the arithmetic type, else (BF16) in the arithmetic type
+  using XT = typename std::conditional<std::is_same<TA, __nv_bfloat16>::value, TM, TA>::type;
+  XT xr[VPT][VE];
   TM acc[VPT][VE];
   int cur_seg = -1, cur_inst = -1, sidx = seg0;
   int64_t nvec = 0, lda = 0;
@@ -181,16 +185,23 @@ k_fused_pass_batch(const BatchInst* __restrict__ inst, const BatchSeg* __restric
         cur_inst = ni;
       }
       cur_seg = sidx;
-      const V* xv = reinterpret_cast<const V*>(static_cast<const TA*>(inst[ni].xlo) +
-                                               static_cast<int64_t>(seg[sidx].shard) * lda);
+      const XT* xsrc = static_cast<const XT*>(inst[ni].xlo) + static_cast<int64_t>(seg[sidx].shard) * lda;
 #pragma unroll
       for (int kk = 0; kk < VPT; ++kk) {
         const int64_t v = tid + static_cast<int64_t>(kk) * NT;
-        V t;
-        if (v < nvec) t = xv[v]; else t = V{};
-        const TA* te = reinterpret_cast<const TA*>(&t);
+        if constexpr (std::is_same<XT, TA>::value) {  // one 16-byte load per vector
+          V t;
+          if (v < nvec) t = reinterpret_cast<const V*>(xsrc)[v]; else t = V{};
+          const TA* te = reinterpret_cast<const TA*>(&t);
 #pragma unroll
-        for (int e = 0; e < VE; ++e) { xr[kk][e] = te[e]; acc[kk][e] = TM(0); }
+          for (int e = 0; e < VE; ++e) { xr[kk][e] = te[e]; acc[kk][e] = TM(0); }
+        } else {
+#pragma unroll
+          for (int e = 0; e < VE; ++e) {
+            xr[kk][e] = v < nvec ? xsrc[v * VE + e] : XT(0);
+            acc[kk][e] = TM(0);
+          }
+        }
       }
     }
     const BatchInst& I = inst[cur_inst];
@@ -226,7 +237,7 @@ k_fused_pass_batch(const BatchInst* __restrict__ inst, const BatchSeg* __restric
             const V a = sv[r * nvec + v];
             const TA* ae = reinterpret_cast<const TA*>(&a);
 #pragma unroll
-            for (int e = 0; e < VE; ++e) dot[r] = fma(TM(ae[e]), TM(xr[kk][e]), dot[r]);
+            for (int e = 0; e < VE; ++e) dot[r] = fma(conv<TM>(ae[e]), conv<TM>(xr[kk][e]), dot[r]);
           }
         }
       }
@@ -280,7 +291,7 @@ k_fused_pass_batch(const BatchInst* __restrict__ inst, const BatchSeg* __restric
             const V a = sv[r * nvec + v];
             const TA* ae = reinterpret_cast<const TA*>(&a);
 #pragma unroll
-            for (int e = 0; e < VE; ++e) acc[kk][e] = fma(dr[r], TM(ae[e]), acc[kk][e]);
+            for (int e = 0; e < VE; ++e) acc[kk][e] = fma(dr[r], conv<TM>(ae[e]), acc[kk][e]);
           }
         }
       }

@@ -1137,7 +1137,9 @@ int run_polish_softmax_k(bicadmm_ctx* h, std::vector<double>& xs, std::vector<in
 struct bicadmm_batch_ctx {
   std::vector<bicadmm_t> hs;
   cudaStream_t stream = nullptr;
-  int esz = 8;
+  int esz = 8;   // bytes of the arithmetic type (m-space, slots)
+  int asz = 8;   // bytes of the stored A element
+  int prec = 0;  // BICADMM_PREC_* of every handle
   int R = 0, S = 0, VPT = 0, G = 0, nseg = 0, n_xitems = 0, n_ditems = 0, max_ldp = 0;
   int stage_kb = 0;
   int64_t P = 0;
@@ -1222,6 +1224,14 @@ int batch_pass_dispatch(bicadmm_batch_ctx* b, int op, int* blocks) {
   return bfail(b, BICADMM_ERR_UNSUPPORTED, "no batched A-pass variant for this tiling");
 }
 
+int batch_pass_any(bicadmm_batch_ctx* b, int op, int* blocks) {
+  switch (b->prec) {
+    case BICADMM_PREC_FP64: return batch_pass_dispatch<double, double>(b, op, blocks);
+    case BICADMM_PREC_FP32: return batch_pass_dispatch<float, float>(b, op, blocks);
+    default: return batch_pass_dispatch<__nv_bfloat16, float>(b, op, blocks);
+  }
+}
+
 constexpr int kBatchMaxRows = 8;  // rows per panel at most (the batched kernel's R)
 
 // Build the panel partition and every table for a tiling: stages of `stage_kb` KB, S of
@@ -1242,11 +1252,11 @@ int batch_build(bicadmm_batch_ctx* b, int stage_kb, int S) {
   b->S = S;
   b->max_ldp = max_ldp;
   b->stage_bytes = static_cast<size_t>(stage_kb) * 1024;
-  if (b->stage_bytes < static_cast<size_t>(max_lda) * b->esz)
+  if (b->stage_bytes < static_cast<size_t>(max_lda) * b->asz)
     return bfail(b, BICADMM_ERR_UNSUPPORTED, "stage smaller than the widest row");
   b->smem = S * b->stage_bytes + S * sizeof(uint64_t) +
             static_cast<size_t>(R) * (kPassThreads / 32 + 1) * b->esz + 16;
-  b->VPT = pick_vpt(max_lda / (b->esz == 8 ? 2 : 4));
+  b->VPT = pick_vpt(max_lda / (16 / b->asz));
   if (b->VPT < 0) return bfail(b, BICADMM_ERR_UNSUPPORTED, "instance rows too wide for the batched pass");
   // segments
   std::vector<BatchSeg> seg;
@@ -1254,7 +1264,7 @@ int batch_build(bicadmm_batch_ctx* b, int stage_kb, int S) {
   for (int q = 0; q < B; ++q) {
     bicadmm_t h = b->hs[q];
     const int rpp = static_cast<int>(std::min<int64_t>(
-        R, static_cast<int64_t>(b->stage_bytes / (static_cast<size_t>(h->lda) * b->esz))));
+        R, static_cast<int64_t>(b->stage_bytes / (static_cast<size_t>(h->lda) * b->asz))));
     for (int i = 0; i < h->N; ++i) {
       const int64_t rows = h->shard_row0[i + 1] - h->shard_row0[i];
       seg.push_back(BatchSeg{q, i, P, h->shard_row0[i], rows, rpp, 0});
@@ -1264,8 +1274,7 @@ int batch_build(bicadmm_batch_ctx* b, int stage_kb, int S) {
   b->P = P;
   b->nseg = static_cast<int>(seg.size());
   int occ = 0;
-  int rc = b->esz == 8 ? batch_pass_dispatch<double, double>(b, 1, &occ)
-                       : batch_pass_dispatch<float, float>(b, 1, &occ);
+  int rc = batch_pass_any(b, 1, &occ);
   if (rc != BICADMM_OK) return rc;
   if (occ < 1) return bfail(b, BICADMM_ERR_UNSUPPORTED, "batched A-pass cannot be resident");
   b->G = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(occ) * b->hs[0]->num_sms, P));
@@ -1371,8 +1380,7 @@ int batch_iteration(bicadmm_batch_ctx* b) {
   BCK(cudaGetLastError());
   if ((rc = bprof(b, 1, true)) != BICADMM_OK) return rc;
   if ((rc = bprof(b, 0, false)) != BICADMM_OK) return rc;
-  rc = b->esz == 8 ? batch_pass_dispatch<double, double>(b, 0, nullptr)
-                   : batch_pass_dispatch<float, float>(b, 0, nullptr);
+  rc = batch_pass_any(b, 0, nullptr);
   if (rc != BICADMM_OK) return rc;
   if ((rc = bprof(b, 0, true)) != BICADMM_OK) return rc;
   if ((rc = bprof(b, 3, false)) != BICADMM_OK) return rc;
@@ -1720,8 +1728,8 @@ int bicadmm_batch_create(bicadmm_t* handles, int32_t count, void* stream, int32_
   for (int q = 0; q < count; ++q) {
     bicadmm_t h = handles[q];
     if (!h || !h->ready) { g_create_error = "every handle must be set up"; return BICADMM_ERR_STATE; }
-    if (h->esz != handles[0]->esz || h->device != handles[0]->device) { g_create_error = "handles must share precision and device"; return BICADMM_ERR_ARG; }
-    if (h->K != 1 || h->p.precision == BICADMM_PREC_BF16) { g_create_error = "batches take FP64 or FP32 handles with K = 1"; return BICADMM_ERR_UNSUPPORTED; }
+    if (h->p.precision != handles[0]->p.precision || h->device != handles[0]->device) { g_create_error = "handles must share precision and device"; return BICADMM_ERR_ARG; }
+    if (h->K != 1) { g_create_error = "batches take handles with K = 1"; return BICADMM_ERR_UNSUPPORTED; }
     if (h->p.inner_iters != 1) { g_create_error = "batched handles must use inner_iters = 1"; return BICADMM_ERR_UNSUPPORTED; }
     for (int q2 = 0; q2 < q; ++q2)
       if (handles[q2] == h) { g_create_error = "a handle appears twice"; return BICADMM_ERR_ARG; }
@@ -1730,13 +1738,15 @@ int bicadmm_batch_create(bicadmm_t* handles, int32_t count, void* stream, int32_
   b->hs.assign(handles, handles + count);
   b->stream = static_cast<cudaStream_t>(stream);
   b->esz = static_cast<int>(handles[0]->esz);
+  b->asz = static_cast<int>(handles[0]->asz);
+  b->prec = handles[0]->p.precision;
   b->use_graph = (flags & BICADMM_BATCH_GRAPH) != 0;
   b->profile = (flags & BICADMM_BATCH_PROFILE) != 0;
   if (b->use_graph && b->profile) { g_create_error = "profiling needs eager launches (no graph)"; delete b; return BICADMM_ERR_ARG; }
   if (b->use_graph && !stream) { g_create_error = "graph capture needs a non-default stream"; delete b; return BICADMM_ERR_ARG; }
   int64_t max_lda = 0;
   for (bicadmm_t h : b->hs) max_lda = std::max(max_lda, h->lda);
-  const size_t row_bytes = static_cast<size_t>(max_lda) * b->esz;
+  const size_t row_bytes = static_cast<size_t>(max_lda) * b->asz;
   // tilings (stage KB, S stages) that hold the widest row and fit the shared memory
   for (int kb : {16, 24, 32, 40, 48, 64})
     for (int S : {2, 3, 4}) {
@@ -2037,7 +2047,7 @@ int bicadmm_server_submit(bicadmm_server_t s, const bicadmm_params* p, const voi
   if (!p || !A || !b || !id_out) return sfail(s, BICADMM_ERR_ARG, "p, A, b and id_out are required");
   if (p->precision != s->sp.precision) return sfail(s, BICADMM_ERR_ARG, "request precision differs from the server's");
   if (p->inner_iters != 1) return sfail(s, BICADMM_ERR_UNSUPPORTED, "served requests use inner_iters = 1");
-  if (p->K != 1 || p->precision == BICADMM_PREC_BF16) return sfail(s, BICADMM_ERR_UNSUPPORTED, "served requests are FP64 or FP32 with K = 1");
+  if (p->K != 1) return sfail(s, BICADMM_ERR_UNSUPPORTED, "served requests take K = 1");
   ServerReq r;
   r.p = *p;
   r.A = A;

@@ -31,7 +31,7 @@ def _solvers(probs, precision=bc.PREC_FP64):
     import torch
     out = []
     for P in probs:
-        A = P.A if precision == bc.PREC_FP64 else P.A.astype(np.float32)
+        A = P.A if precision == bc.PREC_FP64 else P.A.astype(np.float32)  # BF16: rounded at setup
         out.append(bc.Solver(A, P.b, loss=P.loss, N=P.N, M=P.M, kappa=P.kappa, gamma=P.gamma,
                              rho_c=P.rho, precision=precision, stream=torch.cuda.current_stream()))
     return out
@@ -109,6 +109,35 @@ def test_batch_fp32_close_to_alone():
     for st, want in zip(states, alone):
         for k in ("z", "x", "omega", "nu"):
             assert rel_err(st[k], want[k]) <= 1e-4, k
+
+
+@pytest.mark.parametrize("flags", [0, 1])
+def test_batch_bf16_close_to_alone_and_oracle(flags):
+    """BF16 storage in a batch: each instance within 1e-4 of itself stepped alone and of the
+    oracle run on its BF16-rounded A."""
+    import torch
+    probs = _instances(seed=5)
+    iters = 15
+    alone = []
+    for s in _solvers(probs, bc.PREC_BF16):
+        s.step(iters)
+        alone.append(s.state())
+        s.close()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sol = _solvers(probs, bc.PREC_BF16)
+        b = bc.batch_create(sol, stream=stream, flags=flags)
+        bc.batch_step(b, iters)
+        stream.synchronize()
+        bc.batch_destroy(b)
+        states = [s.state() for s in sol]
+        for s in sol:
+            s.close()
+    for st, want, P in zip(states, alone, probs):
+        for k in ("z", "x", "omega", "nu"):
+            assert rel_err(st[k], want[k]) <= 1e-4, k
+        b32 = P.b.astype(np.float32).astype(np.float64)
+        compare_state(st, run_oracle(P, iters, A=synth.round_to_bf16(P.A), b=b32), 1e-4)
 
 
 def test_batch_rejects_bad_requests():

@@ -33,7 +33,7 @@ def _alone(P, iters, precision):
         return bc.get_x(s.h, P.n, polished=True, with_support=True, kappa=P.kappa)
 
 
-@pytest.mark.parametrize("precision,tol", [(bc.PREC_FP64, 1e-9), (bc.PREC_FP32, 1e-4)])
+@pytest.mark.parametrize("precision,tol", [(bc.PREC_FP64, 1e-9), (bc.PREC_FP32, 1e-4), (bc.PREC_BF16, 1e-4)])
 def test_results_same_alone_and_in_the_mix(precision, tol):
     reqs = _requests()
     with bc.Server(hbm_budget_bytes=8 << 30, max_active=16, iters_per_round=7,
