@@ -185,17 +185,23 @@ k_fused_pass_batch(const BatchInst* __restrict__ inst, const BatchSeg* __restric
         cur_inst = ni;
       }
       cur_seg = sidx;
-      const XT* xsrc = static_cast<const XT*>(inst[ni].xlo) + static_cast<int64_t>(seg[sidx].shard) * lda;
+      if constexpr (std::is_same<XT, TA>::value) {  // one 16-byte load per vector
+        const V* xv = reinterpret_cast<const V*>(static_cast<const TA*>(inst[ni].xlo) +
+                                                 static_cast<int64_t>(seg[sidx].shard) * lda);
 #pragma unroll
-      for (int kk = 0; kk < VPT; ++kk) {
-        const int64_t v = tid + static_cast<int64_t>(kk) * NT;
-        if constexpr (std::is_same<XT, TA>::value) {  // one 16-byte load per vector
+        for (int kk = 0; kk < VPT; ++kk) {
+          const int64_t v = tid + static_cast<int64_t>(kk) * NT;
           V t;
-          if (v < nvec) t = reinterpret_cast<const V*>(xsrc)[v]; else t = V{};
+          if (v < nvec) t = xv[v]; else t = V{};
           const TA* te = reinterpret_cast<const TA*>(&t);
 #pragma unroll
           for (int e = 0; e < VE; ++e) { xr[kk][e] = te[e]; acc[kk][e] = TM(0); }
-        } else {
+        }
+      } else {
+        const XT* xsrc = static_cast<const XT*>(inst[ni].xlo) + static_cast<int64_t>(seg[sidx].shard) * lda;
+#pragma unroll
+        for (int kk = 0; kk < VPT; ++kk) {
+          const int64_t v = tid + static_cast<int64_t>(kk) * NT;
 #pragma unroll
           for (int e = 0; e < VE; ++e) {
             xr[kk][e] = v < nvec ? xsrc[v * VE + e] : XT(0);
@@ -311,8 +317,9 @@ struct XItem {
   int inst, shard, block, row_begin;
 };
 
+// FP32: at most 32 registers, so that a full SM's worth of warps keeps P loads in flight.
 template <typename TP, int XT, int ROWS>
-__global__ void __launch_bounds__(XT)
+__global__ void __launch_bounds__(XT, sizeof(TP) == 4 ? 2048 / XT : 1)
 k_xupd_batch(const BatchInst* __restrict__ inst, const XItem* __restrict__ items) {
   using V = typename PVec<TP>::type;
   constexpr int VE = PVec<TP>::n;
@@ -330,7 +337,7 @@ k_xupd_batch(const BatchInst* __restrict__ inst, const XItem* __restrict__ items
   const TP* Pb = static_cast<const TP*>(I.P) + I.P_off[i * I.M_blocks + j];
   const V* rv = reinterpret_cast<const V*>(rs);
   const int nv = ldp / VE;
-  constexpr int U = 8;
+  constexpr int U = 4;  // 16-byte loads in flight per lane (64 warps per SM)
   for (int row = it.row_begin + warp; row < it.row_begin + ROWS && row < nj; row += XT / 32) {
     const V* pr = reinterpret_cast<const V*>(Pb + static_cast<int64_t>(row) * ldp);
     TP acc = TP(0);

@@ -56,8 +56,9 @@ template <typename TP> struct PVec;
 template <> struct PVec<float> { using type = float4; static constexpr int n = 4; };
 template <> struct PVec<double> { using type = double2; static constexpr int n = 2; };
 
+// FP32: at most 32 registers, so that a full SM's worth of warps keeps P loads in flight.
 template <typename TP, typename TX, int XT, int ROWS>
-__global__ void __launch_bounds__(XT)
+__global__ void __launch_bounds__(XT, sizeof(TP) == 4 ? 2048 / XT : 1)
 k_xupd(const TP* __restrict__ P, const int64_t* __restrict__ P_off,
        const int* __restrict__ blk_col0, const int* __restrict__ blk_ldp,
        const double* __restrict__ r, double* __restrict__ x, TX* __restrict__ xlo, int M,
