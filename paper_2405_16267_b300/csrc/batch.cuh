@@ -9,6 +9,12 @@
 // (cta - first CTA of the instance) + shard, and, crossing an instance boundary, flushes the
 // inner-residual sums.  The instance's slot ranges for this partition are kept by the batch
 // so the dual kernel sums the right slots.
+//
+// Narrow instances (a row of at most NT/2 16-byte vectors) go through a second pass kernel
+// over their own panel list, which splits the CTA into RP row groups of L = NT/RP threads:
+// each group takes every RP-th row of the panel, so a panel holds up to R * RP rows and
+// every thread has work; the groups' A'd partial sums are added in shared memory when the
+// segment is flushed.
 #pragma once
 
 #include <type_traits>
@@ -33,6 +39,7 @@ struct BatchInst {
   int c_lo;          // first panel CTA of the batch partition touching this instance
   int G_inst;        // panel CTAs touching it
   int loss, newton_iters;
+  int lsh;           // log2 of the threads per row group (log2 NT for wide instances)
   double M, rho_l;
   // x-update and dual
   const void* P;
@@ -299,6 +306,266 @@ k_fused_pass_batch(const BatchInst* __restrict__ inst, const BatchSeg* __restric
 #pragma unroll
             for (int e = 0; e < VE; ++e) acc[kk][e] = fma(dr[r], conv<TM>(ae[e]), acc[kk][e]);
           }
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && n_issued < np) {
+      issue(n_issued);
+      ++n_issued;
+    }
+  }
+  if (cur_seg >= 0) flush_acc(cur_seg);
+  if (cur_inst >= 0) flush_stats(cur_inst);
+}
+
+// The pass over narrow instances (rows of at most NT/2 vectors): row groups of L = 2^lsh
+// threads (8 <= L <= NT/2), one vector per thread, RP = NT/L rows in flight per step.
+template <typename TA, typename TM, int R, int NT>
+__global__ void __launch_bounds__(NT, 2)
+k_fused_pass_batch_narrow(const BatchInst* __restrict__ inst, const BatchSeg* __restrict__ seg, int nseg,
+                   int64_t P, int S, size_t stage_bytes, long long wait_limit) {
+  using V = typename Vec16<TA>::type;
+  constexpr int VE = Vec16<TA>::n;
+  constexpr int NW = NT / 32;
+  constexpr int kMaxRows = R * 32;  // rows per panel at most (row groups of >= 8 threads)
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c = blockIdx.x, G = gridDim.x;
+  const int64_t p_begin = static_cast<int64_t>(c) * P / G;
+  const int64_t p_end = static_cast<int64_t>(c + 1) * P / G;
+  const int64_t np = p_end - p_begin;
+
+  // layout: S stages of stage_bytes | S mbarriers | red[kMaxRows] | d[kMaxRows] |
+  //         racc[NT * VE] | stat[3 * NW]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + S * stage_bytes);
+  TM* red = reinterpret_cast<TM*>(bars + S);
+  TM* d_s = red + kMaxRows;
+  TM* racc = d_s + kMaxRows;
+  TM* stat = racc + NT * VE;
+
+  if (tid == 0) {
+    for (int st = 0; st < S; ++st) mbar_init(&bars[st], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+
+  auto locate = [&](int64_t p, int& s, int64_t& row0, int& nrows) {
+    while (s + 1 < nseg && seg[s + 1].first_panel <= p) ++s;
+    const BatchSeg& g = seg[s];
+    row0 = g.row0 + (p - g.first_panel) * g.rpp;
+    const int64_t rem = g.row0 + g.rows - row0;
+    nrows = rem < g.rpp ? static_cast<int>(rem) : g.rpp;
+  };
+
+  // segment holding this CTA's first panel (binary search; later lookups walk forward)
+  int seg0 = 0;
+  {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (seg[mid].first_panel <= p_begin) lo = mid; else hi = mid - 1;
+    }
+    seg0 = lo;
+  }
+
+  int64_t n_issued = 0;
+  int issue_seg = seg0;
+  auto issue = [&](int64_t k) {
+    int64_t row0;
+    int nrows;
+    locate(p_begin + k, issue_seg, row0, nrows);
+    const BatchInst& I = inst[seg[issue_seg].inst];
+    const int st = static_cast<int>(k % S);
+    const uint32_t bytes = static_cast<uint32_t>(nrows * I.lda * sizeof(TA));
+    mbar_arrive_expect_tx(&bars[st], bytes);
+    bulk_copy_g2s(smem_raw + st * stage_bytes, static_cast<const TA*>(I.A) + row0 * I.lda, bytes,
+                  &bars[st]);
+  };
+  if (tid == 0) {
+    for (; n_issued < np && n_issued < S; ++n_issued) issue(n_issued);
+  }
+
+  // x_i in the storage type when it is the arithmetic type, else (BF16) in the arithmetic type
+  using XT = typename std::conditional<std::is_same<TA, __nv_bfloat16>::value, TM, TA>::type;
+  XT xr[VE];
+  TM acc[VE];
+  int cur_seg = -1, cur_inst = -1, sidx = seg0;
+  int64_t nvec = 0, lda = 0;
+  int loss = 0, newton_iters = 0;
+  // row groups of the current instance: L threads each, RP of them, wpg warps per group
+  int L = NT / 2, RP = 2, wpg = 1, vl = 0, rp = 0;
+  TM Mf = TM(1), rho_l = TM(1);
+  TM st_res = TM(0), st_om = TM(0), st_ax = TM(0);
+
+  auto flush_acc = [&](int s) {
+    const BatchSeg& g = seg[s];
+    const BatchInst& I = inst[g.inst];
+    TM* dst = static_cast<TM*>(I.slots) + static_cast<int64_t>(c - I.c_lo + g.shard) * I.lda;
+    // add the RP groups' partial sums
+#pragma unroll
+    for (int e = 0; e < VE; ++e) racc[tid * VE + e] = acc[e];
+    __syncthreads();
+    const int span = L * VE;
+    for (int idx = tid; idx < nvec * VE; idx += NT) {
+      TM sum = TM(0);
+      for (int q = 0; q < RP; ++q) sum += racc[q * span + idx];
+      dst[idx] = sum;
+    }
+    __syncthreads();
+  };
+  auto flush_stats = [&](int ii) {
+    const TM a0 = warp_sum(st_res), a1 = warp_sum(st_om), a2 = warp_sum(st_ax);
+    if (lane == 0) {
+      stat[warp * 3 + 0] = a0;
+      stat[warp * 3 + 1] = a1;
+      stat[warp * 3 + 2] = a2;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      TM s0 = TM(0), s1 = TM(0), s2 = TM(0);
+      for (int w = 0; w < NW; ++w) {
+        s0 += stat[w * 3 + 0];
+        s1 += stat[w * 3 + 1];
+        s2 += stat[w * 3 + 2];
+      }
+      const BatchInst& I = inst[ii];
+      double* cs = I.cta_stats + (c - I.c_lo) * 4;
+      cs[0] = static_cast<double>(s0);
+      cs[1] = static_cast<double>(s1);
+      cs[2] = static_cast<double>(s2);
+      cs[3] = 0.0;
+    }
+    __syncthreads();
+    st_res = st_om = st_ax = TM(0);
+  };
+
+  for (int64_t k = 0; k < np; ++k) {
+    int64_t row0;
+    int nrows;
+    locate(p_begin + k, sidx, row0, nrows);
+    if (sidx != cur_seg) {
+      if (cur_seg >= 0) flush_acc(cur_seg);
+      const int ni = seg[sidx].inst;
+      if (ni != cur_inst) {
+        if (cur_inst >= 0) flush_stats(cur_inst);
+        const BatchInst& I = inst[ni];
+        lda = I.lda;
+        nvec = lda / VE;
+        loss = I.loss;
+        newton_iters = I.newton_iters;
+        Mf = static_cast<TM>(I.M);
+        rho_l = static_cast<TM>(I.rho_l);
+        L = 1 << I.lsh;
+        RP = NT >> I.lsh;
+        wpg = L >= 32 ? L >> 5 : 1;
+        vl = tid & (L - 1);
+        rp = tid >> I.lsh;
+        cur_inst = ni;
+      }
+      cur_seg = sidx;
+      if constexpr (std::is_same<XT, TA>::value) {  // one 16-byte load per vector
+        const V* xv = reinterpret_cast<const V*>(static_cast<const TA*>(inst[ni].xlo) +
+                                                 static_cast<int64_t>(seg[sidx].shard) * lda);
+        V t;
+        if (vl < nvec) t = xv[vl]; else t = V{};
+        const TA* te = reinterpret_cast<const TA*>(&t);
+#pragma unroll
+        for (int e = 0; e < VE; ++e) { xr[e] = te[e]; acc[e] = TM(0); }
+      } else {
+        const XT* xsrc = static_cast<const XT*>(inst[ni].xlo) + static_cast<int64_t>(seg[sidx].shard) * lda;
+#pragma unroll
+        for (int e = 0; e < VE; ++e) {
+          xr[e] = vl < nvec ? xsrc[vl * VE + e] : XT(0);
+          acc[e] = TM(0);
+        }
+      }
+    }
+    const BatchInst& I = inst[cur_inst];
+    // row `tid` of the panel: its label and duals, fetched before the wait
+    TM b_r = TM(0), nu_r = TM(0), om_r = TM(0);
+    if (tid < nrows) {
+      b_r = static_cast<const TM*>(I.b)[row0 + tid];
+      nu_r = static_cast<const TM*>(I.nu)[row0 + tid];
+      om_r = static_cast<const TM*>(I.omega)[row0 + tid];
+    }
+    const int st = static_cast<int>(k % S);
+    const uint32_t parity = static_cast<uint32_t>((k / S) & 1);
+    const bool ok = mbar_wait_bounded(&bars[st], parity, wait_limit);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        set_err(I.err, DEV_TIMEOUT_PASS);
+        for (int64_t q = k; q < n_issued; ++q)
+          mbar_wait_bounded(&bars[q % S], static_cast<uint32_t>((q / S) & 1), wait_limit);
+      }
+      return;
+    }
+    const V* sv = reinterpret_cast<const V*>(smem_raw + st * stage_bytes);
+
+    // forward: group rp takes rows rp, rp + RP, ...; thread vl of the group its vectors
+    TM dot[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) dot[r] = TM(0);
+    if (vl < nvec) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int row = r * RP + rp;
+        if (row < nrows) {
+          const V a = sv[row * nvec + vl];
+          const TA* ae = reinterpret_cast<const TA*>(&a);
+#pragma unroll
+          for (int e = 0; e < VE; ++e) dot[r] = fma(conv<TM>(ae[e]), conv<TM>(xr[e]), dot[r]);
+        }
+      }
+    }
+    // sum over the group's lanes within each warp, then one partial per (row, warp of group)
+    const int gl = L < 32 ? L : 32;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      for (int off = gl >> 1; off > 0; off >>= 1) dot[r] += __shfl_xor_sync(0xffffffffu, dot[r], off);
+    }
+    if ((vl & 31) == 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int row = r * RP + rp;
+        if (row < nrows) red[row * wpg + (vl >> 5)] = dot[r];
+      }
+    }
+    __syncthreads();
+
+    // prox epilogue: thread t owns row t of the panel (nrows <= NT)
+    if (tid < nrows) {
+      TM tot = TM(0);
+      for (int w = 0; w < wpg; ++w) tot += red[tid * wpg + w];
+      const TM Axb = tot / Mf;
+      const TM om = omega_prox<TM>(loss, Axb + nu_r, b_r, Mf, rho_l, newton_iters, om_r);
+      const TM nun = nu_r + Axb - om;
+      static_cast<TM*>(I.omega)[row0 + tid] = om;
+      static_cast<TM*>(I.nu)[row0 + tid] = nun;
+      d_s[tid] = om - Axb - nun;
+      const TM rr = Axb - om;
+      st_res = fma(rr, rr, st_res);
+      st_om = fma(om, om, st_om);
+      st_ax = fma(Axb, Axb, st_ax);
+    }
+    __syncthreads();
+
+    TM dr[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int row = r * RP + rp;
+      dr[r] = row < nrows ? d_s[row] : TM(0);
+    }
+    if (vl < nvec) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int row = r * RP + rp;
+        if (row < nrows) {
+          const V a = sv[row * nvec + vl];
+          const TA* ae = reinterpret_cast<const TA*>(&a);
+#pragma unroll
+          for (int e = 0; e < VE; ++e) acc[e] = fma(dr[r], conv<TM>(ae[e]), acc[e]);
         }
       }
     }

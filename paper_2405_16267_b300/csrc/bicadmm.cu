@@ -1144,6 +1144,13 @@ struct bicadmm_batch_ctx {
   int stage_kb = 0;
   int64_t P = 0;
   size_t stage_bytes = 0, smem = 0;
+  std::vector<int> lsh;            // per instance: log2 of the pass's threads per row group
+  // the narrow-instance pass: its own panel list, grid and shared memory
+  BatchSeg* d_seg_n = nullptr;
+  int nseg_n = 0, G_n = 0;
+  int64_t P_n = 0;
+  size_t smem_n = 0;
+  int launches_per_iter = 4;
   std::vector<void*> allocs;       // batch-owned device memory (tables, slots, stats)
   std::vector<void*> table_allocs; // tables rebuilt on retiling
   BatchInst* d_inst = nullptr;
@@ -1194,6 +1201,7 @@ int bdev_alloc(bicadmm_batch_ctx* b, T** ptr, size_t bytes, bool table) {
 
 template <typename TA, typename TM, int R, int VPT>
 int launch_pass_batch_rv(bicadmm_batch_ctx* b) {
+  if (b->P == 0) return BICADMM_OK;
   auto kern = k_fused_pass_batch<TA, TM, R, VPT, kPassThreads>;
   BCK(allow_max_dynamic_smem(kern));
   kern<<<b->G, kPassThreads, b->smem, b->stream>>>(b->d_inst, b->d_seg, b->nseg, b->P, b->S,
@@ -1232,6 +1240,30 @@ int batch_pass_any(bicadmm_batch_ctx* b, int op, int* blocks) {
   }
 }
 
+// The narrow-instance pass; op 0 = launch (nothing when the list is empty), 1 = occupancy.
+template <typename TA, typename TM>
+int batch_pass_narrow(bicadmm_batch_ctx* b, int op, int* blocks) {
+  auto kern = k_fused_pass_batch_narrow<TA, TM, 8, kPassThreads>;
+  BCK(allow_max_dynamic_smem(kern));
+  if (op == 1) {
+    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, kPassThreads, b->smem_n));
+    return BICADMM_OK;
+  }
+  if (b->P_n == 0) return BICADMM_OK;
+  kern<<<b->G_n, kPassThreads, b->smem_n, b->stream>>>(b->d_inst, b->d_seg_n, b->nseg_n, b->P_n, b->S,
+                                                       b->stage_bytes, kWaitLimitCycles);
+  BCK(cudaGetLastError());
+  return BICADMM_OK;
+}
+
+int batch_pass_narrow_any(bicadmm_batch_ctx* b, int op, int* blocks) {
+  switch (b->prec) {
+    case BICADMM_PREC_FP64: return batch_pass_narrow<double, double>(b, op, blocks);
+    case BICADMM_PREC_FP32: return batch_pass_narrow<float, float>(b, op, blocks);
+    default: return batch_pass_narrow<__nv_bfloat16, float>(b, op, blocks);
+  }
+}
+
 constexpr int kBatchMaxRows = 8;  // rows per panel at most (the batched kernel's R)
 
 // Build the panel partition and every table for a tiling: stages of `stage_kb` KB, S of
@@ -1254,34 +1286,72 @@ int batch_build(bicadmm_batch_ctx* b, int stage_kb, int S) {
   b->stage_bytes = static_cast<size_t>(stage_kb) * 1024;
   if (b->stage_bytes < static_cast<size_t>(max_lda) * b->asz)
     return bfail(b, BICADMM_ERR_UNSUPPORTED, "stage smaller than the widest row");
-  b->smem = S * b->stage_bytes + S * sizeof(uint64_t) +
-            static_cast<size_t>(R) * (kPassThreads / 32 + 1) * b->esz + 16;
-  b->VPT = pick_vpt(max_lda / (16 / b->asz));
+  const int ve = static_cast<int>(16 / b->asz);
+  constexpr int NW = kPassThreads / 32;
+  // wide pass: stages | mbarriers | red[R][NW] | d[R]
+  b->smem = S * b->stage_bytes + S * sizeof(uint64_t) + static_cast<size_t>(R) * (NW + 1) * b->esz + 16;
+  // narrow pass: stages | mbarriers | red and d (R * 32 rows each) | the row groups' A'd
+  // partial sums (one vector per thread) | per-warp statistics
+  b->smem_n = S * b->stage_bytes + S * sizeof(uint64_t) +
+              (2 * static_cast<size_t>(R) * 32 + static_cast<size_t>(kPassThreads) * ve + 3 * NW) * b->esz + 16;
+  // Row groups: an instance whose rows hold at most kPassThreads / 2 vectors runs in the
+  // narrow pass with groups of L = max(R, next power of two >= its vectors) threads.
+  int lg_nt = 0;
+  while ((1 << lg_nt) < kPassThreads) ++lg_nt;
+  b->lsh.assign(B, lg_nt);
+  int64_t max_lda_w = 0;
+  for (int q = 0; q < B; ++q) {
+    const int64_t nv = b->hs[q]->lda / ve;
+    if (2 * nv <= kPassThreads) {
+      int l = 0;
+      while ((int64_t{1} << l) < std::max<int64_t>(nv, R)) ++l;
+      b->lsh[q] = l;
+    } else {
+      max_lda_w = std::max(max_lda_w, b->hs[q]->lda);
+    }
+  }
+  b->VPT = max_lda_w > 0 ? pick_vpt(max_lda_w / ve) : 1;
   if (b->VPT < 0) return bfail(b, BICADMM_ERR_UNSUPPORTED, "instance rows too wide for the batched pass");
-  // segments
-  std::vector<BatchSeg> seg;
-  int64_t P = 0;
+  // segments, one list per pass
+  std::vector<BatchSeg> seg, seg_n;
+  int64_t P = 0, P_n = 0;
   for (int q = 0; q < B; ++q) {
     bicadmm_t h = b->hs[q];
+    const bool nar = b->lsh[q] < lg_nt;
+    const int64_t rows_max = nar ? static_cast<int64_t>(R) * (kPassThreads >> b->lsh[q]) : R;
     const int rpp = static_cast<int>(std::min<int64_t>(
-        R, static_cast<int64_t>(b->stage_bytes / (static_cast<size_t>(h->lda) * b->asz))));
+        rows_max, static_cast<int64_t>(b->stage_bytes / (static_cast<size_t>(h->lda) * b->asz))));
     for (int i = 0; i < h->N; ++i) {
       const int64_t rows = h->shard_row0[i + 1] - h->shard_row0[i];
-      seg.push_back(BatchSeg{q, i, P, h->shard_row0[i], rows, rpp, 0});
-      P += (rows + rpp - 1) / rpp;
+      int64_t& PP = nar ? P_n : P;
+      (nar ? seg_n : seg).push_back(BatchSeg{q, i, PP, h->shard_row0[i], rows, rpp, 0});
+      PP += (rows + rpp - 1) / rpp;
     }
   }
   b->P = P;
   b->nseg = static_cast<int>(seg.size());
-  int occ = 0;
-  int rc = batch_pass_any(b, 1, &occ);
-  if (rc != BICADMM_OK) return rc;
-  if (occ < 1) return bfail(b, BICADMM_ERR_UNSUPPORTED, "batched A-pass cannot be resident");
-  b->G = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(occ) * b->hs[0]->num_sms, P));
-  auto owner = [&](int64_t panel) {
-    int64_t c = panel * b->G / P;
-    while (c > 0 && c * P / b->G > panel) --c;
-    while ((c + 1) * P / b->G <= panel) ++c;
+  b->P_n = P_n;
+  b->nseg_n = static_cast<int>(seg_n.size());
+  b->G = b->G_n = 0;
+  int rc = BICADMM_OK;
+  if (P > 0) {
+    int occ = 0;
+    if ((rc = batch_pass_any(b, 1, &occ)) != BICADMM_OK) return rc;
+    if (occ < 1) return bfail(b, BICADMM_ERR_UNSUPPORTED, "batched A-pass cannot be resident");
+    b->G = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(occ) * b->hs[0]->num_sms, P));
+  }
+  if (P_n > 0) {
+    int occ = 0;
+    if ((rc = batch_pass_narrow_any(b, 1, &occ)) != BICADMM_OK) return rc;
+    if (occ < 1) return bfail(b, BICADMM_ERR_UNSUPPORTED, "batched narrow A-pass cannot be resident");
+    b->G_n = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(occ) * b->hs[0]->num_sms, P_n));
+  }
+  b->launches_per_iter = 3 + (P > 0) + (P_n > 0);
+  // CTA of a pass that owns a panel of its list
+  auto owner = [](int64_t panel, int64_t PP, int GG) {
+    int64_t c = panel * GG / PP;
+    while (c > 0 && c * PP / GG > panel) --c;
+    while ((c + 1) * PP / GG <= panel) ++c;
     return static_cast<int>(c);
   };
   // per-instance tables
@@ -1289,18 +1359,23 @@ int batch_build(bicadmm_batch_ctx* b, int stage_kb, int S) {
   std::vector<ConsensusArgs> cons(B);
   std::vector<XItem> xitems;
   std::vector<DItem> ditems;
-  size_t si = 0;
+  size_t si_w = 0, si_n = 0;
   for (int q = 0; q < B; ++q) {
     bicadmm_t h = b->hs[q];
-    const BatchSeg& s0 = seg[si];
-    const BatchSeg& s1 = seg[si + h->N - 1];
-    const int c_lo = owner(s0.first_panel);
-    const int c_hi = owner(s1.first_panel + (s1.rows + s1.rpp - 1) / s1.rpp - 1);
+    const bool nar = b->lsh[q] < lg_nt;
+    const std::vector<BatchSeg>& list = nar ? seg_n : seg;
+    size_t& si = nar ? si_n : si_w;
+    const int64_t PP = nar ? P_n : P;
+    const int GG = nar ? b->G_n : b->G;
+    const BatchSeg& s0 = list[si];
+    const BatchSeg& s1 = list[si + h->N - 1];
+    const int c_lo = owner(s0.first_panel, PP, GG);
+    const int c_hi = owner(s1.first_panel + (s1.rows + s1.rpp - 1) / s1.rpp - 1, PP, GG);
     std::vector<int> lo(h->N), hi(h->N);
     for (int i = 0; i < h->N; ++i) {
-      const BatchSeg& g = seg[si + i];
-      lo[i] = owner(g.first_panel) - c_lo + i;
-      hi[i] = owner(g.first_panel + (g.rows + g.rpp - 1) / g.rpp - 1) - c_lo + i;
+      const BatchSeg& g = list[si + i];
+      lo[i] = owner(g.first_panel, PP, GG) - c_lo + i;
+      hi[i] = owner(g.first_panel + (g.rows + g.rpp - 1) / g.rpp - 1, PP, GG) - c_lo + i;
     }
     si += h->N;
     const int G_inst = c_hi - c_lo + 1;
@@ -1319,6 +1394,7 @@ int batch_build(bicadmm_batch_ctx* b, int stage_kb, int S) {
     I.A = h->A; I.lda = h->lda; I.xlo = h->xlo; I.b = h->b; I.omega = h->omega; I.nu = h->nu;
     I.slots = slots; I.cta_stats = stats; I.c_lo = c_lo; I.G_inst = G_inst;
     I.loss = h->p.loss; I.newton_iters = h->p.newton_iters; I.M = h->M; I.rho_l = h->p.rho_l;
+    I.lsh = b->lsh[q];
     I.P = h->Pm; I.P_off = h->d_P_off; I.blk_col0 = h->d_blk_col0; I.blk_ldp = h->d_blk_ldp;
     I.M_blocks = h->M; I.N = h->N; I.x = h->x; I.u = h->u; I.r = h->r; I.z = h->z;
     I.rho_c = h->p.rho_c; I.c0 = h->c0; I.slot_lo = d_lo; I.slot_hi = d_hi;
@@ -1338,12 +1414,16 @@ int batch_build(bicadmm_batch_ctx* b, int stage_kb, int S) {
   b->n_xitems = static_cast<int>(xitems.size());
   b->n_ditems = static_cast<int>(ditems.size());
   if ((rc = bdev_alloc(b, &b->d_inst, B * sizeof(BatchInst), true)) != BICADMM_OK) return rc;
-  if ((rc = bdev_alloc(b, &b->d_seg, seg.size() * sizeof(BatchSeg), true)) != BICADMM_OK) return rc;
+  if (!seg.empty() && (rc = bdev_alloc(b, &b->d_seg, seg.size() * sizeof(BatchSeg), true)) != BICADMM_OK) return rc;
+  if (!seg_n.empty() && (rc = bdev_alloc(b, &b->d_seg_n, seg_n.size() * sizeof(BatchSeg), true)) != BICADMM_OK) return rc;
   if ((rc = bdev_alloc(b, &b->d_xitems, xitems.size() * sizeof(XItem), true)) != BICADMM_OK) return rc;
   if ((rc = bdev_alloc(b, &b->d_ditems, ditems.size() * sizeof(DItem), true)) != BICADMM_OK) return rc;
   if ((rc = bdev_alloc(b, &b->d_cons, B * sizeof(ConsensusArgs), true)) != BICADMM_OK) return rc;
   BCK(cudaMemcpyAsync(b->d_inst, inst.data(), B * sizeof(BatchInst), cudaMemcpyHostToDevice, b->stream));
-  BCK(cudaMemcpyAsync(b->d_seg, seg.data(), seg.size() * sizeof(BatchSeg), cudaMemcpyHostToDevice, b->stream));
+  if (!seg.empty())
+    BCK(cudaMemcpyAsync(b->d_seg, seg.data(), seg.size() * sizeof(BatchSeg), cudaMemcpyHostToDevice, b->stream));
+  if (!seg_n.empty())
+    BCK(cudaMemcpyAsync(b->d_seg_n, seg_n.data(), seg_n.size() * sizeof(BatchSeg), cudaMemcpyHostToDevice, b->stream));
   BCK(cudaMemcpyAsync(b->d_xitems, xitems.data(), xitems.size() * sizeof(XItem), cudaMemcpyHostToDevice, b->stream));
   BCK(cudaMemcpyAsync(b->d_ditems, ditems.data(), ditems.size() * sizeof(DItem), cudaMemcpyHostToDevice, b->stream));
   BCK(cudaMemcpyAsync(b->d_cons, cons.data(), B * sizeof(ConsensusArgs), cudaMemcpyHostToDevice, b->stream));
@@ -1367,8 +1447,8 @@ int bprof(bicadmm_batch_ctx* b, int kind, bool end) {
   return BICADMM_OK;
 }
 
-// One outer iteration of every instance: 4 launches (kinds: 1 x-update, 0 pass,
-// 3 consensus, 2 dual).
+// One outer iteration of every instance: 4 or 5 launches (kinds: 1 x-update, 0 pass over
+// the wide and over the narrow instances, 3 consensus, 2 dual).
 template <typename TM>
 int batch_iteration(bicadmm_batch_ctx* b) {
   int rc;
@@ -1380,8 +1460,8 @@ int batch_iteration(bicadmm_batch_ctx* b) {
   BCK(cudaGetLastError());
   if ((rc = bprof(b, 1, true)) != BICADMM_OK) return rc;
   if ((rc = bprof(b, 0, false)) != BICADMM_OK) return rc;
-  rc = batch_pass_any(b, 0, nullptr);
-  if (rc != BICADMM_OK) return rc;
+  if ((rc = batch_pass_any(b, 0, nullptr)) != BICADMM_OK) return rc;
+  if ((rc = batch_pass_narrow_any(b, 0, nullptr)) != BICADMM_OK) return rc;
   if ((rc = bprof(b, 0, true)) != BICADMM_OK) return rc;
   if ((rc = bprof(b, 3, false)) != BICADMM_OK) return rc;
   k_global_batch<512, 2><<<static_cast<unsigned>(b->hs.size()), 512, 0, b->stream>>>(b->d_cons);
@@ -1390,7 +1470,7 @@ int batch_iteration(bicadmm_batch_ctx* b) {
   k_dual_batch<TM, kDualThreads><<<b->n_ditems, kDualThreads, 0, b->stream>>>(b->d_inst, b->d_ditems);
   BCK(cudaGetLastError());
   if ((rc = bprof(b, 2, true)) != BICADMM_OK) return rc;
-  b->launches += 4;
+  b->launches += b->launches_per_iter;
   return BICADMM_OK;
 }
 
@@ -1817,7 +1897,7 @@ int bicadmm_batch_step(bicadmm_batch_t b, int32_t n_iters, int64_t* launches_out
   for (; done < n_iters; ++done) {
     if (b->graph) {
       BCK(cudaGraphLaunch(b->graph, b->stream));
-      b->launches += 4;
+      b->launches += b->launches_per_iter;
     } else if ((rc = batch_run(b, 1)) != BICADMM_OK) {
       return rc;
     }
@@ -2097,7 +2177,7 @@ int bicadmm_server_run(bicadmm_server_t s, double until, int64_t* completed_out)
     k = std::max(k, 1);
     int64_t launches = 0;
     if ((rc = bicadmm_batch_step(s->batch, k, &launches)) != BICADMM_OK) return sfail(s, rc, s->batch->err);
-    s->launches += 4 * k;
+    s->launches += static_cast<int64_t>(s->batch->launches_per_iter) * k;
     for (int64_t id : s->active) s->reqs[id].iters += k;
     ++s->rounds;
     // new arrivals are set up (setup stream) while the round runs on the device

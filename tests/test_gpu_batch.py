@@ -62,7 +62,9 @@ def test_batch_equals_alone(flags):
         for s in sol:
             s.close()
     assert 16 <= rows <= 64 and stages >= 2  # stage KB, stage count
-    assert launches == 4 * iters or (flags & 1)  # graph replays count one iteration's 4
+    # graph replays count one iteration's launches; eager: 4 or 5 per iteration (one pass
+    # launch for the wide and one for the narrow instances)
+    assert launches in (4 * iters, 5 * iters) or (flags & 1)
     for st, want, P in zip(states, alone, probs):
         for k in ("z", "x", "u", "s", "omega", "nu"):
             assert rel_err(st[k], want[k]) <= TOL64, (P.name, k)
@@ -138,6 +140,56 @@ def test_batch_bf16_close_to_alone_and_oracle(flags):
             assert rel_err(st[k], want[k]) <= 1e-4, k
         b32 = P.b.astype(np.float32).astype(np.float64)
         compare_state(st, run_oracle(P, iters, A=synth.round_to_bf16(P.A), b=b32), 1e-4)
+
+
+def _mixed_instances(seed=0):
+    """Row widths across both batched pass kernels: row groups of 8, 16, 32 and 128 threads
+    (narrow pass) and one or more vectors per thread (wide pass); shards shorter than a
+    panel."""
+    specs = [(bc.LOSS_SQUARED, 900, 20, 3, 1, 3), (bc.LOSS_LOGISTIC, 70, 30, 3, 1, 2),
+             (bc.LOSS_SQHINGE, 1200, 100, 2, 1, 5), (bc.LOSS_SQUARED, 1500, 240, 4, 2, 8),
+             (bc.LOSS_LOGISTIC, 1100, 300, 3, 2, 6), (bc.LOSS_SQUARED, 1300, 520, 2, 2, 9),
+             (bc.LOSS_SQHINGE, 2000, 1100, 4, 3, 11)]
+    return [synth.small_problem(loss, m=m, n=n, nnz=kappa, N=N, M=M, kappa=kappa,
+                                seed=300 + k + seed)
+            for k, (loss, m, n, N, M, kappa) in enumerate(specs)]
+
+
+@pytest.mark.parametrize("precision", [bc.PREC_FP64, bc.PREC_FP32, bc.PREC_BF16])
+def test_batch_mixed_widths(precision):
+    """Instances of every row-group size and of the wide pass in one batch: each within the
+    precision's tolerance of itself stepped alone and of the oracle (on the rounded A)."""
+    import torch
+    probs = _mixed_instances()
+    iters = 12
+    tol = TOL64 if precision == bc.PREC_FP64 else 1e-4
+    alone = []
+    for s in _solvers(probs, precision):
+        s.step(iters)
+        alone.append(s.state())
+        s.close()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sol = _solvers(probs, precision)
+        b = bc.batch_create(sol, stream=stream, flags=bc.BATCH_AUTOTUNE)
+        launches = bc.batch_step(b, iters)
+        stream.synchronize()
+        bc.batch_destroy(b)
+        states = [s.state() for s in sol]
+        for s in sol:
+            s.close()
+    assert launches == 5 * iters
+    for st, want, P in zip(states, alone, probs):
+        for k in ("z", "x", "omega", "nu"):
+            assert rel_err(st[k], want[k]) <= tol, (P.name, k)
+        if precision == bc.PREC_FP64:
+            o = run_oracle(P, iters)
+        else:
+            A = P.A.astype(np.float32).astype(np.float64)
+            if precision == bc.PREC_BF16:
+                A = synth.round_to_bf16(P.A)
+            o = run_oracle(P, iters, A=A, b=P.b.astype(np.float32).astype(np.float64))
+        compare_state(st, o, tol, support_exact=precision == bc.PREC_FP64)
 
 
 def test_batch_rejects_bad_requests():
