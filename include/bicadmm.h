@@ -149,6 +149,15 @@ int bicadmm_step(bicadmm_t h, int32_t n_iters, bicadmm_info* info);
  * iterations have run in this call.  Not converging is not an error: info->converged = 0. */
 int bicadmm_solve(bicadmm_t h, bicadmm_info* info);
 
+/* Replay outer iterations from a CUDA graph: with iters_per_graph > 0, bicadmm_step (and so
+ * bicadmm_solve) runs its first iteration eagerly, captures iters_per_graph iterations of
+ * this handle into a graph once (recorded, not run), then runs the requested iterations as
+ * whole replays plus an eager remainder.  The iterates are those of eager stepping; only
+ * the host launch cost changes (it dominates small problems).  0 switches replay off and
+ * frees the graph.  Needs a non-default stream (ERR_ARG otherwise); ignored while
+ * profiling is on. */
+int bicadmm_set_graph(bicadmm_t h, int32_t iters_per_graph);
+
 /* Copy the model to host memory x_host[len], len = n K (the flattened n x K W for SOFTMAX).
  * polished = 0: the consensus iterate z.  polished = 1: the solution of the problem
  * restricted to S = the kappa largest |z_r| (ties to the lowest index), solved in FP64 by

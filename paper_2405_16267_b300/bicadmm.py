@@ -77,6 +77,7 @@ SIGNATURES = [
     ("bicadmm_get_state", ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                          ctypes.c_int64]),
     ("bicadmm_set_profiling", ctypes.c_int, [_VP, ctypes.c_int32]),
+    ("bicadmm_set_graph", ctypes.c_int, [_VP, ctypes.c_int32]),
     ("bicadmm_get_pass_time", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(ctypes.c_int64)]),
     ("bicadmm_get_kernel_times", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
@@ -239,6 +240,11 @@ KERNEL_KINDS = ("pass", "xupd", "dual", "rhs")
 def set_profiling(h, on=True):
     """on: False/0 off, True/1 the A pass only, 2 every kernel of the iteration."""
     _check(lib().bicadmm_set_profiling(h, int(on)), h)
+
+
+def set_graph(h, iters_per_graph):
+    """Replay iters_per_graph outer iterations per CUDA graph launch (0 = eager launches)."""
+    _check(lib().bicadmm_set_graph(h, int(iters_per_graph)), h)
 
 
 def get_kernel_times(h, reset=True):
@@ -420,6 +426,9 @@ class Solver:
 
     def step(self, n_iters, info=True):
         return step(self.h, n_iters, info)
+
+    def set_graph(self, iters_per_graph):
+        set_graph(self.h, iters_per_graph)
 
     def solve(self):
         return solve(self.h)

@@ -65,6 +65,10 @@ struct bicadmm_ctx {
   int64_t launches = 0;
   int64_t iters_done = 0;
   bool converged = false;
+  // CUDA graph of graph_iters outer iterations, replayed by bicadmm_step (0 = eager)
+  int graph_iters = 0;
+  cudaGraphExec_t graph = nullptr;
+  int64_t graph_launches = 0;  // kernels in one replay
 
   // geometry
   int N = 0, M = 0;
@@ -151,6 +155,8 @@ int dev_alloc(bicadmm_ctx* h, T** ptr, size_t bytes) {
 }
 
 void free_all(bicadmm_ctx* h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->graph = nullptr;
   for (void* p : h->allocs) cudaFree(p);
   h->allocs.clear();
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
@@ -1612,13 +1618,71 @@ int bicadmm_setup(bicadmm_t h, const void* A, int32_t A_dtype, int64_t lda, int3
   return BICADMM_OK;
 }
 
+// Capture graph_iters outer iterations of the handle into a CUDA graph (the launches are
+// recorded, not run; the counters are restored).
+int capture_graph(bicadmm_ctx* h) {
+  const int64_t l0 = h->launches, i0 = h->iters_done;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = h->esz == 8 ? run_iterations<double>(h, h->graph_iters) : run_iterations<float>(h, h->graph_iters);
+  const cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
+  h->graph_launches = h->launches - l0;
+  h->launches = l0;
+  h->iters_done = i0;
+  if (rc != BICADMM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (ce != cudaSuccess) return fail(h, BICADMM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+  const cudaError_t ie = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    h->graph = nullptr;
+    return fail(h, BICADMM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+  }
+  return BICADMM_OK;
+}
+
 int bicadmm_step(bicadmm_t h, int32_t n_iters, bicadmm_info* info) {
   if (!h) return BICADMM_ERR_ARG;
   if (!h->ready) return fail(h, BICADMM_ERR_STATE, "bicadmm_step before a successful bicadmm_setup");
   if (n_iters < 0) return fail(h, BICADMM_ERR_ARG, "n_iters must be >= 0");
-  int rc = h->esz == 8 ? run_iterations<double>(h, n_iters) : run_iterations<float>(h, n_iters);
+  int rc = BICADMM_OK;
+  int done = 0;
+  if (h->graph_iters > 0 && h->prof == 0) {
+    // the first iteration runs eagerly (kernel attributes are set outside any capture)
+    if (!h->graph && n_iters >= 1) {
+      rc = h->esz == 8 ? run_iterations<double>(h, 1) : run_iterations<float>(h, 1);
+      if (rc != BICADMM_OK) return rc;
+      ++done;
+      if ((rc = capture_graph(h)) != BICADMM_OK) return rc;
+    }
+    if (h->graph) {
+      for (; done + h->graph_iters <= n_iters; done += h->graph_iters) {
+        CK(cudaGraphLaunch(h->graph, h->stream));
+        h->launches += h->graph_launches;
+        h->iters_done += h->graph_iters;
+      }
+    }
+  }
+  if (done < n_iters)
+    rc = h->esz == 8 ? run_iterations<double>(h, n_iters - done) : run_iterations<float>(h, n_iters - done);
   if (rc != BICADMM_OK) return rc;
   if (info) return fill_info(h, info);
+  return BICADMM_OK;
+}
+
+int bicadmm_set_graph(bicadmm_t h, int32_t iters_per_graph) {
+  if (!h) return BICADMM_ERR_ARG;
+  if (iters_per_graph < 0) return fail(h, BICADMM_ERR_ARG, "iters_per_graph must be >= 0");
+  if (iters_per_graph > 0 && h->stream == nullptr)
+    return fail(h, BICADMM_ERR_ARG, "graph replay needs a non-default stream");
+  if (h->graph) {
+    CK(cudaStreamSynchronize(h->stream));
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  h->graph_iters = iters_per_graph;
   return BICADMM_OK;
 }
 
