@@ -79,7 +79,10 @@ enum {
   BICADMM_FIELD_S = 3,      /* nK: bi-linear variable s in S^kappa                    */
   BICADMM_FIELD_OMEGA = 4,  /* m x K: omega-bar of eq. (p:GPU;omega), shard-major rows */
   BICADMM_FIELD_NU = 5,     /* m x K: sharing duals nu of eq. (p:GPU;nu)              */
-  BICADMM_FIELD_SCALARS = 6 /* 3: t, v (scaled bi-linear dual, eq. v-update), tau    */
+  BICADMM_FIELD_SCALARS = 6, /* 3: t, v (scaled bi-linear dual, eq. v-update), tau   */
+  BICADMM_FIELD_P = 7        /* sum over (i, j) of n_j^2: the block inverses
+                                (rho_l A_ij'A_ij + c0 I)^-1 of the x_ij solve, shard-major
+                                then block, each n_j x n_j row-major (setup's output)   */
 };
 
 typedef struct {

@@ -17,7 +17,7 @@ from .build_lib import LIB
 LOSS_SQUARED, LOSS_LOGISTIC, LOSS_SOFTMAX, LOSS_SQHINGE = 0, 1, 2, 3
 PREC_FP64, PREC_FP32, PREC_BF16 = 0, 1, 2
 DTYPE_F64, DTYPE_F32, DTYPE_BF16 = 0, 1, 2
-FIELD_X, FIELD_U, FIELD_Z, FIELD_S, FIELD_OMEGA, FIELD_NU, FIELD_SCALARS = range(7)
+FIELD_X, FIELD_U, FIELD_Z, FIELD_S, FIELD_OMEGA, FIELD_NU, FIELD_SCALARS, FIELD_P = range(8)
 
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_STATE",
           -5: "ERR_NUMERIC", -6: "ERR_TIMEOUT", -7: "ERR_UNSUPPORTED"}
@@ -450,6 +450,20 @@ class Solver:
                     u=get_state(self.h, FIELD_U, N * n).reshape(N, n),
                     z=get_state(self.h, FIELD_Z, n), s=get_state(self.h, FIELD_S, n),
                     omega=om, nu=nu, t=sc[0], v=sc[1], tau=sc[2])
+
+    def block_inverses(self, blocks):
+        """The setup's (rho_l A_ij'A_ij + c0 I)^-1 as a list (shards) of lists (blocks) of
+        n_j x n_j arrays; `blocks` = the column ranges [(c0, c1), ...] of the M blocks."""
+        sizes = [c1 - c0 for c0, c1 in blocks]
+        flat = get_state(self.h, FIELD_P, self.N * sum(nj * nj for nj in sizes))
+        out, o = [], 0
+        for _ in range(self.N):
+            row = []
+            for nj in sizes:
+                row.append(flat[o:o + nj * nj].reshape(nj, nj))
+                o += nj * nj
+            out.append(row)
+        return out
 
     def close(self):
         if self.h:

@@ -28,6 +28,7 @@
 #include "batch.cuh"
 #include "multiclass.cuh"
 #include "mc_tc.cuh"
+#include "gram_tc.cuh"
 #include "pass.cuh"
 #include "polish.cuh"
 #include "setup.cuh"
@@ -858,12 +859,36 @@ int build_factors(bicadmm_ctx* h) {
   if (e != cudaSuccess) { cudaGetLastError(); return fail(h, BICADMM_ERR_OOM, "Gram buffer allocation failed"); }
 
   int rc = BICADMM_OK;
-  const int T = (h->max_nj + 63) / 64;
-  const dim3 ggrid(T * (T + 1) / 2, h->M, h->N);
-  k_gram<TA, TM><<<ggrid, 256, 0, h->stream>>>(static_cast<const TA*>(h->A), h->lda, h->d_shard_row0,
-                                               h->d_blk_col0, G, h->d_G_off, h->M);
+  GramItem* d_items = nullptr;
+  if constexpr (std::is_same<TA, __nv_bfloat16>::value) {
+    // tensor cores: (shard, block, 128-column strip, 256-column chunk) items over each
+    // block's 64-aligned column window, chunk/strip pairs that touch the upper triangle
+    std::vector<GramItem> items;
+    for (int i = 0; i < h->N; ++i)
+      for (int j = 0; j < h->M; ++j) {
+        const int c0 = h->blk_col0[j], c1 = h->blk_col0[j + 1];
+        const int w = ((c1 + 63) & ~63) - (c0 & ~63);
+        for (int a = 0; a < (w + 127) / 128; ++a)
+          for (int bq = 0; bq < (w + 255) / 256; ++bq)
+            if (256 * bq + 256 > 128 * a) items.push_back(GramItem{i, j, a, bq});
+      }
+    e = cudaMalloc(&d_items, items.size() * sizeof(GramItem));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(GramItem), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = allow_max_dynamic_smem(k_gram_tc);
+    if (e == cudaSuccess) {
+      k_gram_tc<<<static_cast<unsigned>(items.size()), kGramThreads, gram_tc_smem(), h->stream>>>(
+          h->tmap, d_items, h->d_shard_row0, h->d_blk_col0, G, h->d_G_off, h->M, h->d_err, kWaitLimitCycles);
+      e = cudaGetLastError();
+    }
+  } else {
+    const int T = (h->max_nj + 63) / 64;
+    const dim3 ggrid(T * (T + 1) / 2, h->M, h->N);
+    k_gram<TA, TM><<<ggrid, 256, 0, h->stream>>>(static_cast<const TA*>(h->A), h->lda, h->d_shard_row0,
+                                                 h->d_blk_col0, G, h->d_G_off, h->M);
+    e = cudaGetLastError();
+  }
   h->launches += 1;
-  e = cudaGetLastError();
   if (e == cudaSuccess) {
     auto kc = k_chol<kCholThreads>;
     const size_t sm = static_cast<size_t>(h->max_nj) * sizeof(double);
@@ -893,6 +918,7 @@ int build_factors(bicadmm_ctx* h) {
   cudaError_t e2 = cudaStreamSynchronize(h->stream);
   if (rc == BICADMM_OK && e2 != cudaSuccess) rc = fail(h, BICADMM_ERR_CUDA, std::string("factor sync: ") + cudaGetErrorString(e2));
   cudaFree(G);
+  if (d_items) cudaFree(d_items);
   if (rc != BICADMM_OK) return rc;
   return check_device_error(h);
 }
@@ -1574,7 +1600,8 @@ int bicadmm_create(const bicadmm_params* params, void* stream, bicadmm_t* out) {
   }
   rc = build_geometry(h);
   if (rc == BICADMM_OK) rc = allocate(h);
-  if (rc == BICADMM_OK && h->use_tc) rc = make_tmap(h);
+  // BF16 storage: the 2D tensor map of A serves the tensor-core Gram (and the softmax pass)
+  if (rc == BICADMM_OK && (h->use_tc || h->p.precision == BICADMM_PREC_BF16)) rc = make_tmap(h);
   if (rc == BICADMM_OK) rc = reset_state(h);
   if (rc != BICADMM_OK) {
     g_create_error = h->err;
@@ -1791,6 +1818,30 @@ int bicadmm_get_state(bicadmm_t h, int32_t field, double* out_host, int64_t len)
       out_host[1] = g.v;
       out_host[2] = g.tau;
       break;
+    }
+    case BICADMM_FIELD_P: {
+      int64_t total = 0;
+      for (int j = 0; j < h->M; ++j) {
+        const int64_t nj = h->blk_col0[j + 1] - h->blk_col0[j];
+        total += N * nj * nj;
+      }
+      if (!need(total)) return fail(h, BICADMM_ERR_ARG, "length must be the sum of n_j^2 over shards and blocks");
+      std::vector<unsigned char> tmp(static_cast<size_t>(h->P_total) * h->esz);
+      CK(cudaMemcpyAsync(tmp.data(), h->Pm, tmp.size(), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      int64_t o = 0;
+      for (int i = 0; i < N; ++i)
+        for (int j = 0; j < h->M; ++j) {
+          const int nj = h->blk_col0[j + 1] - h->blk_col0[j], ldp = h->blk_ldp[j];
+          const int64_t base = h->P_off[static_cast<size_t>(i) * h->M + j];
+          for (int a = 0; a < nj; ++a)
+            for (int c = 0; c < nj; ++c) {
+              const int64_t q = base + static_cast<int64_t>(a) * ldp + c;
+              out_host[o++] = h->esz == 8 ? reinterpret_cast<const double*>(tmp.data())[q]
+                                          : static_cast<double>(reinterpret_cast<const float*>(tmp.data())[q]);
+            }
+        }
+      return BICADMM_OK;
     }
     default:
       return fail(h, BICADMM_ERR_ARG, "unknown field");

@@ -1,0 +1,53 @@
+"""The setup's block inverses (rho_l A_ij'A_ij + c0 I)^-1 of the x_ij solve (eq. p:GPU;x)
+against the oracle's factorisation of the same matrices, in every storage precision: FP64
+and FP32 Gram matrices on the CUDA cores, BF16 on the tensor cores (column windows that
+start off the 64-column grid, blocks wider than one 256-column chunk, shards whose length
+is not a multiple of the 64-row stage, a shard shorter than one stage)."""
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import bicadmm_ref as ref
+from paper_2405_16267_b300 import bicadmm as bc
+from paper_2405_16267_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+CASES = [  # (m, n, N, M, K)
+    (3001, 517, 3, 4, 1),     # blocks of 130/129 columns starting off the 64-grid
+    (2100, 700, 2, 2, 1),     # 350-column blocks: several strips and chunks
+    (1000, 90, 5, 1, 1),      # 200-row shards (3 stages + a 8-row tail)
+    (220, 64, 4, 1, 1),       # 55-row shards: one partial stage
+    (1500, 150, 3, 2, 3),     # softmax, three classes (same block matrices)
+]
+# relative error per unit condition number of the block matrix: FP64 arithmetic; FP32
+# storage of P (and FP32 partial sums of the products: CUDA cores flush to FP64 every 256
+# rows, the tensor cores accumulate a shard in FP32)
+TOL = {bc.PREC_FP64: 1e-13, bc.PREC_FP32: 3e-6, bc.PREC_BF16: 3e-6}
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("precision", [bc.PREC_FP64, bc.PREC_FP32, bc.PREC_BF16])
+def test_block_inverses_match_oracle(case, precision):
+    m, n, N, M, K = case
+    if K == 1:
+        P = synth.small_problem(ref.LOSS_SQUARED, m=m, n=n, nnz=3, N=N, M=M, kappa=3, seed=m + n)
+    else:
+        P = synth.sparse_softmax(m=m, n=n, K=K, nnz=6, N=N, M=M, kappa=6, seed=m + n)
+    A = P.A
+    if precision == bc.PREC_FP32:
+        A = A.astype(np.float32).astype(np.float64)
+    elif precision == bc.PREC_BF16:
+        A = synth.round_to_bf16(P.A)
+    o = ref.BiCADMM(A, P.b, P.loss, P.N, P.M, P.kappa, gamma=P.gamma, rho_c=P.rho, K=K)
+    A_in = P.A if precision == bc.PREC_FP64 else P.A.astype(np.float32)
+    with bc.Solver(A_in, P.b, loss=P.loss, N=P.N, M=P.M, kappa=P.kappa, gamma=P.gamma,
+                   rho_c=P.rho, precision=precision, K=K) as s:
+        got = s.block_inverses(o.blocks)
+    for i in range(N):
+        for j in range(M):
+            nj = o.blocks[j][1] - o.blocks[j][0]
+            want = scipy.linalg.cho_solve(o.factors[i][j], np.eye(nj))
+            kappa = np.linalg.cond(want)
+            err = np.max(np.abs(got[i][j] - want)) / np.max(np.abs(want))
+            assert err <= TOL[precision] * max(kappa, 10.0), (i, j, err, kappa)
