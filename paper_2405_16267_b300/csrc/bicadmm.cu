@@ -718,7 +718,8 @@ void handle_bytes(const bicadmm_ctx* h, int64_t* persistent, int64_t* setup_extr
   if (h->K > 1)  // softmax polish: U (kappa x m) and q, p, d1, P (m x K)
     b += kappa * m * 8 + 4 * m * h->K * 8 + kappa * 12;
   if (persistent) *persistent = b;
-  if (setup_extra) *setup_extra = std::min<int64_t>(256ll << 20, m * lda * 8) + h->G_total * 8;
+  // staging of the input, the Gram matrices and the transposed factor inverse Y' = L^-T
+  if (setup_extra) *setup_extra = std::min<int64_t>(256ll << 20, m * lda * 8) + 2 * h->G_total * 8;
 }
 
 int allocate(bicadmm_ctx* h) {
@@ -889,35 +890,83 @@ int build_factors(bicadmm_ctx* h) {
     e = cudaGetLastError();
   }
   h->launches += 1;
-  if (e == cudaSuccess) {
-    auto kc = k_chol<kCholThreads>;
-    const size_t sm = static_cast<size_t>(h->max_nj) * sizeof(double);
-    if (sm > 48 * 1024) e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
-    if (e == cudaSuccess) {
-      kc<<<h->N * h->M, kCholThreads, sm, h->stream>>>(G, h->d_G_off, h->d_blk_col0, h->M,
-                                                    h->p.rho_l, h->c0, h->d_err);
-      h->launches += 1;
-      e = cudaGetLastError();
-    }
+  // Blocked factorisation when an NB-column panel of the widest block fits in shared memory:
+  // Cholesky, Y = L^-1 by columns, P = Y'Y by tiles (n^3/2 FMAs per block); otherwise the
+  // column-by-column kernels (Cholesky, then both triangular solves per column of P).
+  int nb_panel = 0;
+  for (int cand : {32, 16, 8})
+    if (static_cast<size_t>(cand) * (h->max_nj + 1) * sizeof(double) <= (200u << 10)) { nb_panel = cand; break; }
+  double* YT = nullptr;
+  if (e == cudaSuccess && nb_panel > 0) {
+    e = cudaMalloc(&YT, std::max<int64_t>(h->G_total, 1) * sizeof(double));
+    if (e != cudaSuccess) { cudaGetLastError(); YT = nullptr; nb_panel = 0; e = cudaSuccess; }
   }
-  if (e == cudaSuccess) {
-    // one warp per column; as many warps as fit 200 KB of column vectors (at most 8)
-    const int warps = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(8, (200 << 10) / (8 * h->max_nj))));
-    const size_t sm = static_cast<size_t>(warps) * h->max_nj * sizeof(double);
-    auto ki = k_inv_cols<TM>;
-    if (sm > 48 * 1024) e = cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
+  if (e == cudaSuccess && nb_panel > 0) {
+    const size_t sm = static_cast<size_t>(nb_panel) * (h->max_nj + 1) * sizeof(double);
+#define CHOL_BLK(NBV)                                                                               \
+  {                                                                                                 \
+    auto kc = k_chol_blk<kCholThreads, NBV>;                                                        \
+    e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)); \
+    if (e == cudaSuccess) {                                                                         \
+      kc<<<h->N * h->M, kCholThreads, sm, h->stream>>>(G, h->d_G_off, h->d_blk_col0, h->M,          \
+                                                    h->p.rho_l, h->c0, h->d_err);                   \
+      e = cudaGetLastError();                                                                       \
+    }                                                                                               \
+  }
+    if (nb_panel == 32) CHOL_BLK(32) else if (nb_panel == 16) CHOL_BLK(16) else CHOL_BLK(8)
+#undef CHOL_BLK
+    h->launches += 1;
     if (e == cudaSuccess) {
-      const dim3 grid(h->N * h->M, (h->max_nj + warps - 1) / warps);
-      ki<<<grid, 32 * warps, sm, h->stream>>>(G, h->d_G_off, h->d_blk_col0, h->d_blk_ldp, h->M,
-                                              static_cast<TM*>(h->Pm), h->d_P_off);
+      const int warps = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(8, (200 << 10) / (8 * h->max_nj))));
+      const size_t smy = static_cast<size_t>(warps) * h->max_nj * sizeof(double);
+      if (smy > 48 * 1024) e = cudaFuncSetAttribute(k_inv_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smy));
+      if (e == cudaSuccess) {
+        const dim3 grid(h->N * h->M, (h->max_nj + warps - 1) / warps);
+        k_inv_fwd<<<grid, 32 * warps, smy, h->stream>>>(G, h->d_G_off, h->d_blk_col0, h->M, YT);
+        e = cudaGetLastError();
+      }
       h->launches += 1;
+    }
+    if (e == cudaSuccess) {
+      const int T = (h->max_nj + 63) / 64;
+      const dim3 grid(T * (T + 1) / 2, h->M, h->N);
+      k_yty<TM><<<grid, 256, 0, h->stream>>>(YT, h->d_G_off, h->d_blk_col0, h->d_blk_ldp, h->M,
+                                             static_cast<TM*>(h->Pm), h->d_P_off);
       e = cudaGetLastError();
+      h->launches += 1;
+    }
+  } else {
+    if (e == cudaSuccess) {
+      auto kc = k_chol<kCholThreads>;
+      const size_t sm = static_cast<size_t>(h->max_nj) * sizeof(double);
+      if (sm > 48 * 1024) e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
+      if (e == cudaSuccess) {
+        kc<<<h->N * h->M, kCholThreads, sm, h->stream>>>(G, h->d_G_off, h->d_blk_col0, h->M,
+                                                      h->p.rho_l, h->c0, h->d_err);
+        h->launches += 1;
+        e = cudaGetLastError();
+      }
+    }
+    if (e == cudaSuccess) {
+      // one warp per column; as many warps as fit 200 KB of column vectors (at most 8)
+      const int warps = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(8, (200 << 10) / (8 * h->max_nj))));
+      const size_t sm = static_cast<size_t>(warps) * h->max_nj * sizeof(double);
+      auto ki = k_inv_cols<TM>;
+      if (sm > 48 * 1024) e = cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
+      if (e == cudaSuccess) {
+        const dim3 grid(h->N * h->M, (h->max_nj + warps - 1) / warps);
+        ki<<<grid, 32 * warps, sm, h->stream>>>(G, h->d_G_off, h->d_blk_col0, h->d_blk_ldp, h->M,
+                                                static_cast<TM*>(h->Pm), h->d_P_off);
+        h->launches += 1;
+        e = cudaGetLastError();
+      }
     }
   }
   if (e != cudaSuccess) rc = fail(h, BICADMM_ERR_CUDA, std::string("factor kernels: ") + cudaGetErrorString(e));
   cudaError_t e2 = cudaStreamSynchronize(h->stream);
   if (rc == BICADMM_OK && e2 != cudaSuccess) rc = fail(h, BICADMM_ERR_CUDA, std::string("factor sync: ") + cudaGetErrorString(e2));
   cudaFree(G);
+  if (YT) cudaFree(YT);
   if (d_items) cudaFree(d_items);
   if (rc != BICADMM_OK) return rc;
   return check_device_error(h);

@@ -134,6 +134,199 @@ k_chol(double* __restrict__ G, const int64_t* __restrict__ G_off, const int* __r
   }
 }
 
+// One CTA per block (i, j): K = rho_l G + c0 I, then the Cholesky factor K = L L' in place
+// in the lower triangle, right-looking with NB-column panels: the panel (rows kb.., columns
+// kb..kb+NB) is held column-major in shared memory; one warp factors its diagonal block,
+// every thread solves some of the rows below against it, and the trailing lower triangle
+// is updated in 64 x 64 tiles (4 x 4 per thread, rows ty + 16 a, columns tx + 16 b) from
+// the panel.  The entries above the diagonal are left as they were.
+template <int CT, int NB>
+__global__ void __launch_bounds__(CT)
+k_chol_blk(double* __restrict__ G, const int64_t* __restrict__ G_off, const int* __restrict__ blk_col0,
+           int M, double rho_l, double c0, int* __restrict__ err) {
+  static_assert(CT == 256 && NB <= 32, "16 x 16 threads; one lane per diagonal-block row");
+  extern __shared__ double panT[];  // [NB][ldpan]
+  const int blk = blockIdx.x, j = blk % M;
+  const int nj = blk_col0[j + 1] - blk_col0[j];
+  const int ldpan = nj + 1;
+  double* K = G + G_off[blk];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, tx = tid & 15, ty = tid >> 4;
+  for (int64_t e = tid; e < static_cast<int64_t>(nj) * nj; e += CT) {
+    const int a = static_cast<int>(e / nj), bq = static_cast<int>(e - static_cast<int64_t>(a) * nj);
+    K[e] = rho_l * K[e] + (a == bq ? c0 : 0.0);
+  }
+  __syncthreads();
+  for (int kb = 0; kb < nj; kb += NB) {
+    const int nb = nj - kb < NB ? nj - kb : NB, nr = nj - kb;
+    for (int e = tid; e < nr * nb; e += CT) {
+      const int r = e / nb, k = e - r * nb;
+      panT[k * ldpan + r] = r >= k ? K[static_cast<int64_t>(kb + r) * nj + kb + k] : 0.0;
+    }
+    __syncthreads();
+    if (warp == 0) {  // diagonal block: lane = row
+      for (int c = 0; c < nb; ++c) {
+        double d = panT[c * ldpan + c];
+        if (lane == 0 && !(d > 0.0)) set_err(err, DEV_NONPOS_PIVOT);
+        d = d > 0.0 ? sqrt(d) : 1.0;
+        __syncwarp();
+        if (lane > c && lane < nb) panT[c * ldpan + lane] /= d;
+        if (lane == c) panT[c * ldpan + c] = d;
+        __syncwarp();
+        if (lane > c && lane < nb) {
+          const double lr = panT[c * ldpan + lane];
+          for (int k = c + 1; k <= lane; ++k) panT[k * ldpan + lane] -= lr * panT[c * ldpan + k];
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // rows below the diagonal block: x L11' = a, i.e. x_k = (a_k - sum_{q<k} x_q L11[k][q]) / L11[k][k]
+    for (int r = nb + tid; r < nr; r += CT) {
+      double x[NB];
+#pragma unroll
+      for (int k = 0; k < NB; ++k) x[k] = k < nb ? panT[k * ldpan + r] : 0.0;
+#pragma unroll
+      for (int k = 0; k < NB; ++k) {
+        if (k < nb) {
+          double sum = x[k];
+#pragma unroll
+          for (int q = 0; q < k; ++q) sum = fma(-x[q], panT[q * ldpan + k], sum);
+          x[k] = sum / panT[k * ldpan + k];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NB; ++k)
+        if (k < nb) panT[k * ldpan + r] = x[k];
+    }
+    __syncthreads();
+    for (int e = tid; e < nr * nb; e += CT) {
+      const int r = e / nb, k = e - r * nb;
+      if (r >= k) K[static_cast<int64_t>(kb + r) * nj + kb + k] = panT[k * ldpan + r];
+    }
+    // trailing lower triangle: K[r][c] -= sum_k L[r][k] L[c][k] for nb <= c <= r < nr
+    const int nt = nr - nb, T = (nt + 63) / 64;
+    for (int tile = 0; tile < T * (T + 1) / 2; ++tile) {
+      int ti = 0, q = tile;
+      while (q > ti) { q -= ti + 1; ++ti; }
+      const int tj = q;  // tj <= ti
+      const int r0 = nb + ti * 64, c0t = nb + tj * 64;
+      double acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int bq = 0; bq < 4; ++bq) acc[a][bq] = 0.0;
+      for (int k = 0; k < nb; ++k) {
+        double av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int r = r0 + ty + 16 * a, c = c0t + tx + 16 * a;
+          av[a] = r < nr ? panT[k * ldpan + r] : 0.0;
+          bv[a] = c < nr ? panT[k * ldpan + c] : 0.0;
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int bq = 0; bq < 4; ++bq) acc[a][bq] = fma(av[a], bv[bq], acc[a][bq]);
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int bq = 0; bq < 4; ++bq) {
+          const int r = r0 + ty + 16 * a, c = c0t + tx + 16 * bq;
+          if (r < nr && c <= r) K[static_cast<int64_t>(kb + r) * nj + kb + c] -= acc[a][bq];
+        }
+    }
+    __syncthreads();
+  }
+}
+
+// Y = L^-1 column by column (one warp per column c: forward substitution L y = e_c, y in
+// shared memory), stored transposed: YT row c = column c of Y (zero before c).
+__global__ void k_inv_fwd(const double* __restrict__ G, const int64_t* __restrict__ G_off,
+                          const int* __restrict__ blk_col0, int M, double* __restrict__ YT) {
+  extern __shared__ double ycol[];  // [warps][nj]
+  const int blk = blockIdx.x, j = blk % M;
+  const int nj = blk_col0[j + 1] - blk_col0[j];
+  const int nw = blockDim.x >> 5, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.y * nw + warp;
+  if (c >= nj) return;
+  const double* K = G + G_off[blk];
+  double* y = ycol + static_cast<int64_t>(warp) * nj;
+  for (int a = c; a < nj; ++a) {
+    const double* La = K + static_cast<int64_t>(a) * nj;
+    double part = 0.0;
+    for (int bq = c + lane; bq < a; bq += 32) part = fma(La[bq], y[bq], part);
+    part = warp_sum(part);
+    if (lane == 0) y[a] = ((a == c ? 1.0 : 0.0) - part) / La[a];
+    __syncwarp();
+  }
+  double* Yr = YT + G_off[blk] + static_cast<int64_t>(c) * nj;
+  for (int a = lane; a < nj; a += 32) Yr[a] = a < c ? 0.0 : y[a];
+}
+
+// P_ij = K^-1 = L^-T L^-1 = Y' Y: P[a][b] = sum_{k >= max(a, b)} YT[a][k] YT[b][k], FP64
+// sums, written in TP with row stride ldp (both triangles; the tile pair (0, 0) also zeroes
+// the padding columns).  Grid (upper-triangle 64 x 64 tile pairs, M, N), 4 x 4 per thread.
+template <typename TP>
+__global__ void __launch_bounds__(256)
+k_yty(const double* __restrict__ YT, const int64_t* __restrict__ G_off, const int* __restrict__ blk_col0,
+      const int* __restrict__ blk_ldp, int M, TP* __restrict__ P, const int64_t* __restrict__ P_off) {
+  constexpr int TILE = 64, KC = 32;
+  __shared__ double As[KC][TILE + 1];
+  __shared__ double Bs[KC][TILE + 1];
+  const int i = blockIdx.z, j = blockIdx.y, blk = i * M + j;
+  const int nj = blk_col0[j + 1] - blk_col0[j], ldp = blk_ldp[j];
+  const int T = (nj + TILE - 1) / TILE;
+  int q = blockIdx.x, ti = 0;
+  while (q >= T - ti) { q -= T - ti; ++ti; if (ti >= T) return; }
+  const int tj = ti + q;  // ti <= tj
+  const double* Y = YT + G_off[blk];
+  TP* Pb = P + P_off[blk];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  if (blockIdx.x == 0 && ldp > nj) {
+    for (int64_t e = threadIdx.x; e < static_cast<int64_t>(nj) * (ldp - nj); e += 256) {
+      const int a = static_cast<int>(e / (ldp - nj)), cc = nj + static_cast<int>(e - static_cast<int64_t>(a) * (ldp - nj));
+      Pb[static_cast<int64_t>(a) * ldp + cc] = TP(0);
+    }
+  }
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int bq = 0; bq < 4; ++bq) acc[a][bq] = 0.0;
+  // YT[a][k] = 0 for k < a, so the sum starts at the column tile's first index
+  for (int k0 = tj * TILE; k0 < nj; k0 += KC) {
+    for (int e = threadIdx.x; e < KC * TILE; e += 256) {
+      const int r = e / KC, k = e - r * KC;
+      const int ra = ti * TILE + r, rb = tj * TILE + r, kk = k0 + k;
+      As[k][r] = (ra < nj && kk < nj) ? Y[static_cast<int64_t>(ra) * nj + kk] : 0.0;
+      Bs[k][r] = (rb < nj && kk < nj) ? Y[static_cast<int64_t>(rb) * nj + kk] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < KC; ++k) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) { av[a] = As[k][ty + 16 * a]; bv[a] = Bs[k][tx + 16 * a]; }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int bq = 0; bq < 4; ++bq) acc[a][bq] = fma(av[a], bv[bq], acc[a][bq]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int bq = 0; bq < 4; ++bq) {
+      const int ra = ti * TILE + ty + 16 * a, cb = tj * TILE + tx + 16 * bq;
+      if (ra < nj && cb < nj) {
+        Pb[static_cast<int64_t>(ra) * ldp + cb] = static_cast<TP>(acc[a][bq]);
+        Pb[static_cast<int64_t>(cb) * ldp + ra] = static_cast<TP>(acc[a][bq]);
+      }
+    }
+}
+
 // Columns of K^-1 = L^-T L^-1: grid (blocks, column groups), one warp per column c:
 // forward L y = e_c then back L' p = y, the column held in shared memory; P is written in
 // TP with row stride ldp (P is symmetric, so column c is written as row c, its padding
