@@ -656,6 +656,49 @@ def run_time_to_tol(stream, tol=1e-6):
                      "support_recovered": set(supp.tolist()) == truth,
                      "rel_err_polished_vs_planted": float(np.linalg.norm(x - P.x_star) / np.linalg.norm(P.x_star))}
     out["solve_speedup_fp32_vs_fp64"] = out["fp64"]["solve_s"] / out["fp32"]["solve_s"]
+    # The served form: the same problem through the serving loop (continuous batching) in
+    # FP32 and BF16 storage, alone and in a mix with three other Table-1 instances arriving
+    # together; time = result ready minus arrival (setup, rounds with tolerance checks and the
+    # polish included), against the plain FP64 path's setup + solve + polish.
+    x64 = None
+    with bc.Solver(A64, b64, loss=P.loss, N=P.N, M=P.M, kappa=P.kappa, gamma=P.gamma, rho_c=P.rho,
+                   precision=bc.PREC_FP64, tol_rel=tol, check_every=5, max_iters=5000, stream=stream) as s:
+        s.solve()
+        x64 = bc.get_x(s.h, P.n, polished=True)
+    fp64_total = out["fp64"]["setup_s"] + out["fp64"]["solve_s"] + out["fp64"]["polish_s"]
+    others = [synth.table1_sls(**dict(TABLE1, seed=TABLE1["seed"] + q)) for q in (1, 2, 3)]
+    A_others = [torch.from_numpy(Q.A).float().cuda() for Q in others]
+    b_others = [torch.from_numpy(Q.b).cuda() for Q in others]
+    for name, prec in (("served_fp32", bc.PREC_FP32), ("served_bf16", bc.PREC_BF16)):
+        entry = {}
+        for mix in (False, True):
+            with bc.Server(hbm_budget_bytes=40 << 30, max_active=8, iters_per_round=10,
+                           precision=prec, polish=True) as srv:
+                common = dict(gamma=P.gamma, rho_c=P.rho, tol_rel=tol, check_every=5, max_iters=5000,
+                              precision=prec)
+                torch.cuda.synchronize()
+                t0 = srv.clock()
+                rid = srv.submit(A32, b64, arrival=t0, loss=P.loss, N_shards=P.N, M_blocks=P.M,
+                                 kappa=P.kappa, **common)
+                mates = []
+                if mix:
+                    for Q, Aq, bq in zip(others, A_others, b_others):
+                        mates.append(srv.submit(Aq, bq, arrival=t0, loss=Q.loss, N_shards=Q.N,
+                                                M_blocks=Q.M, kappa=Q.kappa, **common))
+                srv.run()
+                r = srv.result(rid)
+                rm = [srv.result(q) for q in mates]
+            x = r["x"]
+            e = {"time_s": r["done"] - r["arrival"], "iters": int(r["info"].iters),
+                 "converged": bool(r["info"].converged),
+                 "support_recovered": set(r["support"].tolist()) == truth,
+                 "rel_diff_vs_fp64_polished": float(np.linalg.norm(x - x64) / np.linalg.norm(x64))}
+            if mix:
+                e["all_four_done_s"] = max([r["done"]] + [q["done"] for q in rm]) - r["arrival"]
+                e["all_converged"] = bool(r["info"].converged) and all(bool(q["info"].converged) for q in rm)
+            entry["in_mix_of_4" if mix else "alone"] = e
+        entry["speedup_vs_fp64_alone"] = fp64_total / entry["alone"]["time_s"]
+        out[name] = entry
     out["paper_table1_s"] = {"value": TABLE1_PAPER_S, "hardware": "RTX 4070 + i7-13700, PyTorch 2.3",
                              "note": "context only: other machine, tolerance unstated"}
     return out
