@@ -115,8 +115,18 @@ __device__ __forceinline__ void locate_panel(const PassGeometry& g, int64_t p, i
 // Consensus-step mask words for NT threads: n <= 32 * kConsMW * NT.
 constexpr int kConsMW = 4;
 
+// FP32 storage with few vectors per thread: the forward keeps the thread's vectors of the
+// panel in registers for the backward, so the stage is released (and the panel S ahead is
+// loaded into it) right after the forward, while the row epilogue and the backward run.
+// Taken when x, the A'd sums and the held vectors fit the 128 registers of two CTAs per SM
+// (estimate: 4-byte words of x and A'd, 4 per held vector, 40 for the rest).
+template <typename TA, int R, int VPT>
+__host__ __device__ constexpr bool pass_holds_panel() {
+  return sizeof(TA) == 4 && 2 * VPT * 4 + 4 * R * VPT + 40 <= 128;
+}
+
 template <typename TA, typename TM, int R, int VPT, int NT>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT, pass_holds_panel<TA, R, VPT>() ? 2 : 1)
 k_fused_pass(const TA* __restrict__ A, int64_t lda, const TM* __restrict__ xlo_in,
              const TM* __restrict__ b, TM* __restrict__ omega, TM* __restrict__ nu,
              TM* __restrict__ slots, double* __restrict__ cta_stats, PassGeometry geo,
@@ -239,6 +249,8 @@ k_fused_pass(const TA* __restrict__ A, int64_t lda, const TM* __restrict__ xlo_i
     const V* sv = reinterpret_cast<const V*>(stages + st * stage_elems);
 
     // Forward: partial dots of the panel rows with x_i.
+    constexpr bool kHoldA = pass_holds_panel<TA, R, VPT>();
+    V areg[kHoldA ? VPT : 1][kHoldA ? R : 1];
     TM dot[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) dot[r] = TM(0);
@@ -250,6 +262,7 @@ k_fused_pass(const TA* __restrict__ A, int64_t lda, const TM* __restrict__ xlo_i
         for (int r = 0; r < R; ++r) {
           if (r < nrows) {
             const V a = sv[r * nvec + v];
+            if constexpr (kHoldA) areg[kk][r] = a;
             const TA* ae = reinterpret_cast<const TA*>(&a);
 #pragma unroll
             for (int e = 0; e < VE; ++e) dot[r] = fma(conv<TM>(ae[e]), conv<TM>(xr[kk][e]), dot[r]);
@@ -264,6 +277,12 @@ k_fused_pass(const TA* __restrict__ A, int64_t lda, const TM* __restrict__ xlo_i
       for (int r = 0; r < R; ++r) red[r * NW + warp] = dot[r];
     }
     __syncthreads();
+    if constexpr (kHoldA) {  // every thread holds its part of the panel: reload the stage
+      if (tid == 0 && n_issued < np) {
+        issue(n_issued);
+        ++n_issued;
+      }
+    }
 
     // Row epilogue: mean block product, omega prox, nu update, target shift d.
     if (warp == 0) {
@@ -306,7 +325,8 @@ k_fused_pass(const TA* __restrict__ A, int64_t lda, const TM* __restrict__ xlo_i
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           if (r < nrows) {
-            const V a = sv[r * nvec + v];
+            V a;
+            if constexpr (kHoldA) a = areg[kk][r]; else a = sv[r * nvec + v];
             const TA* ae = reinterpret_cast<const TA*>(&a);
 #pragma unroll
             for (int e = 0; e < VE; ++e) acc[kk][e] = fma(dr[r], conv<TM>(ae[e]), acc[kk][e]);
@@ -314,10 +334,12 @@ k_fused_pass(const TA* __restrict__ A, int64_t lda, const TM* __restrict__ xlo_i
         }
       }
     }
-    __syncthreads();  // every thread is done with this stage
-    if (tid == 0 && n_issued < np) {
-      issue(n_issued);
-      ++n_issued;
+    if constexpr (!kHoldA) {
+      __syncthreads();  // every thread is done with this stage
+      if (tid == 0 && n_issued < np) {
+        issue(n_issued);
+        ++n_issued;
+      }
     }
   }
   if (cur >= 0) flush(cur);
