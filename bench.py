@@ -159,7 +159,7 @@ class ClockSampler:
 # DRAM traffic of one pass launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of a 20000-row launch of the same kernel, scaled by rows to the
 # 200000-row launch.  Reported only while the kernel sources are the captured ones.
-PASS_TRAFFIC = {"sources_sha256": "59b547354de62eb983a1ac027087c039c18be2336d0909c22d57a53b3c0e2bd0", "bytes_per_launch": 4.0685e9,
+PASS_TRAFFIC = {"sources_sha256": "e735e11d90201c094bdb5c6e9e8761dc986b6887b9fdf72fd727cf0a00b0e76c", "bytes_per_launch": 4.0698e9,
                 "capture": "profiles/k_fused_pass_sparse_logistic_200000x5000_fp32.md"}
 PASS_SOURCES = ["paper_2405_16267_b300/csrc/pass.cuh", "paper_2405_16267_b300/csrc/nspace.cuh",
                 "paper_2405_16267_b300/csrc/common.cuh"]
