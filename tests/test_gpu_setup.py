@@ -2,7 +2,8 @@
 against the oracle's factorisation of the same matrices, in every storage precision: FP64
 and FP32 Gram matrices on the CUDA cores, BF16 on the tensor cores (column windows that
 start off the 64-column grid, blocks wider than one 256-column chunk, shards whose length
-is not a multiple of the 64-row stage, a shard shorter than one stage)."""
+is not a multiple of the 64-row stage, a shard shorter than one stage), and blocks wide
+enough for the narrower Cholesky panels and for the column-by-column fallback."""
 import numpy as np
 import pytest
 import scipy.linalg
@@ -19,6 +20,9 @@ CASES = [  # (m, n, N, M, K)
     (1000, 90, 5, 1, 1),      # 200-row shards (3 stages + a 8-row tail)
     (220, 64, 4, 1, 1),       # 55-row shards: one partial stage
     (1500, 150, 3, 2, 3),     # softmax, three classes (same block matrices)
+    (2000, 900, 2, 1, 1),     # a 900-column block: 16-column Cholesky panels
+    (3600, 3500, 1, 1, 1),    # a 3500-column block: too wide for a panel in shared memory,
+                              # the column-by-column kernels
 ]
 # relative error per unit condition number of the block matrix: FP64 arithmetic; FP32
 # storage of P (and FP32 partial sums of the products: CUDA cores flush to FP64 every 256
