@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <chrono>
 #include <cmath>
 #include <deque>
@@ -718,8 +719,8 @@ void handle_bytes(const bicadmm_ctx* h, int64_t* persistent, int64_t* setup_extr
   if (h->K > 1)  // softmax polish: U (kappa x m) and q, p, d1, P (m x K)
     b += kappa * m * 8 + 4 * m * h->K * 8 + kappa * 12;
   if (persistent) *persistent = b;
-  // staging of the input, the Gram matrices and the transposed factor inverse Y' = L^-T
-  if (setup_extra) *setup_extra = std::min<int64_t>(256ll << 20, m * lda * 8) + 2 * h->G_total * 8;
+  // two staging slots of the input, the Gram matrices and the factor inverse Y = L^-1
+  if (setup_extra) *setup_extra = 2 * std::min<int64_t>(256ll << 20, m * lda * 8) + 2 * h->G_total * 8;
 }
 
 int allocate(bicadmm_ctx* h) {
@@ -853,8 +854,11 @@ int check_labels(bicadmm_ctx* h) {
   return check_device_error(h);
 }
 
+// load_shard (optional): enqueues the arrival of shard i's rows of A on the handle's stream;
+// the Gram matrices are then formed shard by shard right behind it, so they overlap the
+// transfers of later shards.
 template <typename TA, typename TM>
-int build_factors(bicadmm_ctx* h) {
+int build_factors(bicadmm_ctx* h, const std::function<int(int)>* load_shard = nullptr) {
   double* G = nullptr;
   cudaError_t e = cudaMalloc(&G, std::max<int64_t>(h->G_total, 1) * sizeof(double));
   if (e != cudaSuccess) { cudaGetLastError(); return fail(h, BICADMM_ERR_OOM, "Gram buffer allocation failed"); }
@@ -865,7 +869,9 @@ int build_factors(bicadmm_ctx* h) {
     // tensor cores: (shard, block, 128-column strip, 256-column chunk) items over each
     // block's 64-aligned column window, chunk/strip pairs that touch the upper triangle
     std::vector<GramItem> items;
-    for (int i = 0; i < h->N; ++i)
+    std::vector<size_t> first(h->N + 1, 0);  // items of shard i: [first[i], first[i + 1])
+    for (int i = 0; i < h->N; ++i) {
+      first[i] = items.size();
       for (int j = 0; j < h->M; ++j) {
         const int c0 = h->blk_col0[j], c1 = h->blk_col0[j + 1];
         const int w = ((c1 + 63) & ~63) - (c0 & ~63);
@@ -873,23 +879,41 @@ int build_factors(bicadmm_ctx* h) {
           for (int bq = 0; bq < (w + 255) / 256; ++bq)
             if (256 * bq + 256 > 128 * a) items.push_back(GramItem{i, j, a, bq});
       }
+    }
+    first[h->N] = items.size();
     e = cudaMalloc(&d_items, items.size() * sizeof(GramItem));
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(GramItem), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = allow_max_dynamic_smem(k_gram_tc);
-    if (e == cudaSuccess) {
-      k_gram_tc<<<static_cast<unsigned>(items.size()), kGramThreads, gram_tc_smem(), h->stream>>>(
-          h->tmap, d_items, h->d_shard_row0, h->d_blk_col0, G, h->d_G_off, h->M, h->d_err, kWaitLimitCycles);
-      e = cudaGetLastError();
+    // one launch for all shards, or one per shard after its rows have arrived
+    for (int i = 0; e == cudaSuccess && rc == BICADMM_OK && i < (load_shard ? h->N : 1); ++i) {
+      const size_t i0 = load_shard ? first[i] : 0, i1 = load_shard ? first[i + 1] : items.size();
+      if (load_shard) rc = (*load_shard)(i);
+      if (rc == BICADMM_OK && i1 > i0) {
+        k_gram_tc<<<static_cast<unsigned>(i1 - i0), kGramThreads, gram_tc_smem(), h->stream>>>(
+            h->tmap, d_items + i0, h->d_shard_row0, h->d_blk_col0, G, h->d_G_off, h->M, h->d_err,
+            kWaitLimitCycles);
+        e = cudaGetLastError();
+        h->launches += 1;
+      }
     }
   } else {
     const int T = (h->max_nj + 63) / 64;
-    const dim3 ggrid(T * (T + 1) / 2, h->M, h->N);
-    k_gram<TA, TM><<<ggrid, 256, 0, h->stream>>>(static_cast<const TA*>(h->A), h->lda, h->d_shard_row0,
-                                                 h->d_blk_col0, G, h->d_G_off, h->M);
-    e = cudaGetLastError();
+    for (int i = 0; e == cudaSuccess && rc == BICADMM_OK && i < (load_shard ? h->N : 1); ++i) {
+      if (load_shard && (rc = (*load_shard)(i)) != BICADMM_OK) break;
+      const dim3 ggrid(T * (T + 1) / 2, h->M, load_shard ? 1 : h->N);
+      k_gram<TA, TM><<<ggrid, 256, 0, h->stream>>>(static_cast<const TA*>(h->A), h->lda, h->d_shard_row0,
+                                                   h->d_blk_col0, G, h->d_G_off, h->M, load_shard ? i : 0);
+      e = cudaGetLastError();
+      h->launches += 1;
+    }
   }
-  h->launches += 1;
+  if (rc != BICADMM_OK) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(G);
+    if (d_items) cudaFree(d_items);
+    return rc;
+  }
   // Blocked factorisation when an NB-column panel of the widest block fits in shared memory:
   // Cholesky, Y = L^-1 by columns, P = Y'Y by tiles (n^3/2 FMAs per block); otherwise the
   // column-by-column kernels (Cholesky, then both triangular solves per column of P).
@@ -1588,6 +1612,96 @@ int batch_capture(bicadmm_batch_ctx* b) {
 
 // =============================================================================== C ABI
 
+// Host A: copied in chunks of rows (within one shard, at most 256 MB) on a side stream into
+// two alternating device staging slots; each chunk is converted into the padded device
+// layout on the handle's stream as soon as it lands, and a shard's Gram matrices follow its
+// last chunk there, so that they overlap the copies of later shards.  b first (small).
+template <typename TA, typename TM>
+int setup_host_pipelined(bicadmm_ctx* h, const void* A, int32_t A_dtype, int64_t lda_src,
+                         const void* b, int32_t b_dtype, int32_t b_on_device) {
+  int rc = load_matrix<TM>(h, b, b_dtype, 1, b_on_device, static_cast<TM*>(h->b), h->p.m, 1, 1);
+  if (rc == BICADMM_OK) rc = check_labels<TM>(h);
+  if (rc != BICADMM_OK) return rc;
+  const size_t in_es = A_dtype == BICADMM_DTYPE_F64 ? 8 : (A_dtype == BICADMM_DTYPE_BF16 ? 2 : 4);
+  const int64_t row_in = lda_src * static_cast<int64_t>(in_es);
+  const int64_t cap_rows = std::max<int64_t>(1, (256ll << 20) / std::max<int64_t>(row_in, 1));
+  struct Chunk { int64_t r0, nr; };
+  std::vector<std::vector<Chunk>> chunks(h->N);
+  int64_t max_rows = 1;
+  for (int i = 0; i < h->N; ++i)
+    for (int64_t r = h->shard_row0[i]; r < h->shard_row0[i + 1]; r += cap_rows) {
+      const int64_t nr = std::min(cap_rows, h->shard_row0[i + 1] - r);
+      chunks[i].push_back(Chunk{r, nr});
+      max_rows = std::max(max_rows, nr);
+    }
+  void* stage[2] = {nullptr, nullptr};
+  cudaStream_t cs = nullptr;
+  std::vector<cudaEvent_t> evs;
+  auto new_event = [&](cudaEvent_t* ev) -> cudaError_t {
+    cudaError_t e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) evs.push_back(*ev);
+    return e;
+  };
+  cudaError_t e = cudaMalloc(&stage[0], static_cast<size_t>(max_rows) * row_in);
+  if (e == cudaSuccess) e = cudaMalloc(&stage[1], static_cast<size_t>(max_rows) * row_in);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    for (void* p : stage)
+      if (p) cudaFree(p);
+    return fail(h, BICADMM_ERR_OOM, "staging buffer allocation failed");
+  }
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  // the copies start after earlier work on the handle's stream (which may still read A)
+  cudaEvent_t start_ev = nullptr;
+  if (e == cudaSuccess) e = new_event(&start_ev);
+  if (e == cudaSuccess) e = cudaEventRecord(start_ev, h->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, start_ev, 0);
+  cudaEvent_t converted[2] = {nullptr, nullptr};  // last conversion out of each slot
+  long long q = 0;
+  std::function<int(int)> load_shard = [&](int i) -> int {
+    for (const Chunk& ch : chunks[i]) {
+      const int slot = static_cast<int>(q & 1);
+      cudaEvent_t copied = nullptr;
+      if (e == cudaSuccess && converted[slot]) e = cudaStreamWaitEvent(cs, converted[slot], 0);
+      // the last row may be shorter than lda_src: copy exactly (nr-1)*lda_src + n elements
+      const size_t bytes = (static_cast<size_t>(ch.nr - 1) * lda_src + h->p.n) * in_es;
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(stage[slot], static_cast<const char*>(A) + ch.r0 * row_in, bytes,
+                            cudaMemcpyHostToDevice, cs);
+      if (e == cudaSuccess) e = new_event(&copied);
+      if (e == cudaSuccess) e = cudaEventRecord(copied, cs);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, copied, 0);
+      if (e != cudaSuccess) return fail(h, BICADMM_ERR_CUDA, std::string("H2D copy: ") + cudaGetErrorString(e));
+      const int64_t total = ch.nr * h->lda;
+      const unsigned grid = static_cast<unsigned>(std::min<int64_t>((total + 255) / 256, 65535));
+      TA* dst = static_cast<TA*>(h->A) + ch.r0 * h->lda;
+      if (A_dtype == BICADMM_DTYPE_F64)
+        k_convert_rows<double, TA><<<grid, 256, 0, h->stream>>>(static_cast<const double*>(stage[slot]), lda_src, dst, h->lda, ch.nr, h->p.n);
+      else if (A_dtype == BICADMM_DTYPE_BF16)
+        k_convert_rows<__nv_bfloat16, TA><<<grid, 256, 0, h->stream>>>(static_cast<const __nv_bfloat16*>(stage[slot]), lda_src, dst, h->lda, ch.nr, h->p.n);
+      else
+        k_convert_rows<float, TA><<<grid, 256, 0, h->stream>>>(static_cast<const float*>(stage[slot]), lda_src, dst, h->lda, ch.nr, h->p.n);
+      e = cudaGetLastError();
+      h->launches += 1;
+      if (e == cudaSuccess) e = new_event(&converted[slot]);
+      if (e == cudaSuccess) e = cudaEventRecord(converted[slot], h->stream);
+      if (e != cudaSuccess) return fail(h, BICADMM_ERR_CUDA, std::string("convert: ") + cudaGetErrorString(e));
+      ++q;
+    }
+    return BICADMM_OK;
+  };
+  if (e != cudaSuccess) rc = fail(h, BICADMM_ERR_CUDA, std::string("copy stream: ") + cudaGetErrorString(e));
+  if (rc == BICADMM_OK) rc = build_factors<TA, TM>(h, &load_shard);
+  cudaStreamSynchronize(h->stream);
+  if (cs) {
+    cudaStreamSynchronize(cs);
+    cudaStreamDestroy(cs);
+  }
+  for (cudaEvent_t x : evs) cudaEventDestroy(x);
+  for (void* p : stage) cudaFree(p);
+  return rc;
+}
+
 extern "C" {
 
 int bicadmm_default_params(bicadmm_params* p) {
@@ -1673,7 +1787,13 @@ int bicadmm_setup(bicadmm_t h, const void* A, int32_t A_dtype, int64_t lda, int3
   h->err.clear();
   int rc = reset_state(h);
   if (rc != BICADMM_OK) return rc;
-  if (h->p.precision == BICADMM_PREC_FP64) {
+  if (!A_on_device) {
+    switch (h->p.precision) {
+      case BICADMM_PREC_FP64: rc = setup_host_pipelined<double, double>(h, A, A_dtype, lda, b, b_dtype, b_on_device); break;
+      case BICADMM_PREC_FP32: rc = setup_host_pipelined<float, float>(h, A, A_dtype, lda, b, b_dtype, b_on_device); break;
+      default: rc = setup_host_pipelined<__nv_bfloat16, float>(h, A, A_dtype, lda, b, b_dtype, b_on_device); break;
+    }
+  } else if (h->p.precision == BICADMM_PREC_FP64) {
     rc = load_matrix<double>(h, A, A_dtype, lda, A_on_device, static_cast<double*>(h->A), h->p.m, h->p.n, h->lda);
     if (rc == BICADMM_OK) rc = load_matrix<double>(h, b, b_dtype, 1, b_on_device, static_cast<double*>(h->b), h->p.m, 1, 1);
     if (rc == BICADMM_OK) rc = check_labels<double>(h);

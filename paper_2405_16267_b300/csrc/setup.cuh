@@ -20,18 +20,19 @@ __global__ void k_convert_rows(const TIN* __restrict__ src, int64_t lda_src,
 }
 
 // G_ij = A_ij' A_ij for every shard i and block j, FP64 output (row stride n_j).
-// Grid (upper-triangle tile pairs, M, N); 256 threads compute a 64 x 64 tile, 4 x 4 each.
+// Grid (upper-triangle tile pairs, M, shards from shard0); 256 threads compute a 64 x 64
+// tile, 4 x 4 each.
 // TC is the multiply type; with TC = float the running sums are moved into FP64 every
 // 256 rows to bound the FP32 accumulation error.
 template <typename TA, typename TC>
 __global__ void __launch_bounds__(256)
 k_gram(const TA* __restrict__ A, int64_t lda, const int64_t* __restrict__ shard_row0,
        const int* __restrict__ blk_col0, double* __restrict__ G, const int64_t* __restrict__ G_off,
-       int M) {
+       int M, int shard0) {
   constexpr int TILE = 64, KC = 32;
   __shared__ TC As[KC][TILE + 1];
   __shared__ TC Bs[KC][TILE + 1];
-  const int i = blockIdx.z, j = blockIdx.y;
+  const int i = shard0 + blockIdx.z, j = blockIdx.y;
   const int col0 = blk_col0[j], nj = blk_col0[j + 1] - col0;
   const int T = (nj + TILE - 1) / TILE;
   int q = blockIdx.x, ti = 0;

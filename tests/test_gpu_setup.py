@@ -55,3 +55,30 @@ def test_block_inverses_match_oracle(case, precision):
             kappa = np.linalg.cond(want)
             err = np.max(np.abs(got[i][j] - want)) / np.max(np.abs(want))
             assert err <= TOL[precision] * max(kappa, 10.0), (i, j, err, kappa)
+
+
+@pytest.mark.parametrize("K", [1, 4])
+def test_host_bf16_input_equals_rounded_fp32_input(K):
+    """BF16 storage from a host BF16 matrix (copied shard by shard, the Gram matrices of a
+    shard overlapping the later copies) and from an FP32 matrix rounded at setup: the same
+    block inverses and, after a few iterations, the same state bit for bit."""
+    import torch
+    if K == 1:
+        P = synth.small_problem(ref.LOSS_LOGISTIC, m=2500, n=300, nnz=5, N=5, M=2, kappa=5, seed=9)
+    else:
+        P = synth.sparse_softmax(m=2500, n=200, K=K, nnz=8, N=5, M=2, kappa=8, seed=9)
+    o = ref.BiCADMM(P.A, P.b, P.loss, P.N, P.M, P.kappa, K=K)
+    A32 = torch.from_numpy(P.A.astype(np.float32))
+    states = []
+    for A_in in (A32.to(torch.bfloat16).pin_memory(), A32.numpy()):
+        with bc.Solver(A_in, P.b, loss=P.loss, N=P.N, M=P.M, kappa=P.kappa, gamma=P.gamma,
+                       rho_c=P.rho, precision=bc.PREC_BF16, K=K) as s:
+            inv = s.block_inverses(o.blocks)
+            s.step(6)
+            states.append((inv, s.state()))
+    (inv_a, st_a), (inv_b, st_b) = states
+    for i in range(P.N):
+        for j in range(P.M):
+            assert np.array_equal(inv_a[i][j], inv_b[i][j])
+    for key in ("x", "z", "omega", "nu"):
+        assert np.array_equal(st_a[key], st_b[key]), key
