@@ -67,6 +67,7 @@ def test_softmax_bf16_vs_oracle_on_rounded_A(pass_rows):
     (60000, 300, 10, 16, 2, 40, 8),     # several shards per CTA, ragged panels
     (9000, 2048, 3, 3, 4, 30, 6),       # full 2048-column rows, 4-class tiles
     (5000, 130, 16, 5, 2, 50, 10),      # 16 classes, one partial slab
+    (3000, 200, 10, 40, 2, 20, 6),      # 75-row shards: a full and an 11-row panel each
 ])
 def test_softmax_bf16_tensor_core_pass(case):
     m, n, K, N, M, kappa, iters = case
