@@ -104,6 +104,17 @@ def test_pass_tiling_choices_agree(rows, stages):
     compare_state(st, o, TOL64)
 
 
+@pytest.mark.parametrize("rows,stages", [(8, 1), (4, 1), (2, 1), (0, 0)])
+def test_pass_tiling_choices_fp32(rows, stages):
+    """FP32 storage, one-stage panels (the panel held in registers while its stage reloads)
+    and the automatic choice: the oracle's iterates on the FP32-rounded A."""
+    P = synth.small_problem(ref.LOSS_LOGISTIC, m=3001, n=700, nnz=6, N=3, M=2, kappa=6, seed=8)
+    A32 = P.A.astype(np.float32).astype(np.float64)
+    st, _ = run_gpu(P, 20, precision=bc.PREC_FP32, pass_rows=rows, pass_stages=stages)
+    o = run_oracle(P, 20, A=A32, b=P.b)
+    compare_state(st, o, 1e-4)
+
+
 def test_solve_stops_at_tolerance():
     import torch
     P = synth.sparse_linear(unit_columns=True)
