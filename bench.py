@@ -511,7 +511,7 @@ def run_batch(args, rank, world):
             rows += P.m
     setup_s = time.perf_counter() - t0
     b = bc.batch_create(solvers, stream=stream, flags=bc.BATCH_GRAPH | bc.BATCH_AUTOTUNE)
-    warm = max(args.warmup, 30)  # the autotuner spends the first iterations on candidate tilings
+    warm = max(args.warmup, 80)  # the autotuner spends the first iterations (2 per candidate tiling)
     bc.batch_step(b, warm)
     stream.synchronize()
     tiling = bc.batch_tiling(b)

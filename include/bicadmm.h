@@ -233,11 +233,11 @@ int bicadmm_consensus_step_noalloc(const double* w, double* z, double* s, double
  * flags: BICADMM_BATCH_GRAPH captures one iteration into a CUDA graph and replays it (needs
  * a non-default stream); BICADMM_BATCH_PROFILE times each launch (not with GRAPH);
  * BICADMM_BATCH_AUTOTUNE spends the first iterations timing each
- * tiling that fits — shared-memory stage size (16..64 KB; each instance's panels take as
+ * tiling that fits — shared-memory stage size (16..96 KB; each instance's panels take as
  * many rows as fit in a stage, at most 8, or at most 8 per row group for instances whose
  * rows hold at most 128 16-byte vectors, which run in a second pass launch) and stage
- * count (2..4) — 2 iterations each (ordinary iterations of every instance), and keeps the
- * fastest.  Kind 0 of bicadmm_batch_kernel_times covers both pass launches.
+ * count (1..4; one stage only from 32 KB) — 2 iterations each (ordinary iterations of every
+ * instance), and keeps the fastest.  Kind 0 of bicadmm_batch_kernel_times covers both pass launches.
  * stream: cudaStream_t used for all batch work.
  * bicadmm_batch_step runs n_iters iterations of every instance (does not synchronise) and
  * writes the batch's kernel-launch count so far to *launches_out when non-NULL.

@@ -2119,9 +2119,11 @@ int bicadmm_batch_create(bicadmm_t* handles, int32_t count, void* stream, int32_
   int64_t max_lda = 0;
   for (bicadmm_t h : b->hs) max_lda = std::max(max_lda, h->lda);
   const size_t row_bytes = static_cast<size_t>(max_lda) * b->asz;
-  // tilings (stage KB, S stages) that hold the widest row and fit the shared memory
-  for (int kb : {16, 24, 32, 40, 48, 64})
-    for (int S : {2, 3, 4}) {
+  // tilings (stage KB, S stages) that hold the widest row and fit the shared memory; one
+  // stage of 32 KB or more lets the two CTAs of an SM alternate between loading and computing
+  for (int kb : {16, 24, 32, 40, 48, 64, 96})
+    for (int S : {1, 2, 3, 4}) {
+      if (S == 1 && kb < 32) continue;
       const size_t st = static_cast<size_t>(kb) * 1024;
       if (st >= row_bytes && S * st <= kPassSmemBudget) b->candidates.push_back({kb, S});
     }
