@@ -2128,9 +2128,11 @@ int bicadmm_batch_create(bicadmm_t* handles, int32_t count, void* stream, int32_
       if (st >= row_bytes && S * st <= kPassSmemBudget) b->candidates.push_back({kb, S});
     }
   if (b->candidates.empty()) { g_create_error = "rows too wide for the batched pass"; delete b; return BICADMM_ERR_UNSUPPORTED; }
-  // default: 40 KB stages (or one widest row), two stages: two CTAs per SM
-  const int kb0 = static_cast<int>(std::max<size_t>(40, (row_bytes + 1023) / 1024));
-  const int S0 = 2;
+  // default (the autotuner's choice on a 256-instance mix): one 96 KB stage for 4- and
+  // 8-byte storage, two 48 KB stages for BF16 (or one widest row per stage); two CTAs per SM
+  const bool bf16 = b->asz == 2;
+  const int kb0 = static_cast<int>(std::max<size_t>(bf16 ? 48 : 96, (row_bytes + 1023) / 1024));
+  const int S0 = bf16 && 2 * kb0 <= 200 ? 2 : 1;
   if (!(flags & BICADMM_BATCH_AUTOTUNE)) b->candidates.clear();
   int rc = batch_build(b, kb0, S0);
   if (rc != BICADMM_OK) {
