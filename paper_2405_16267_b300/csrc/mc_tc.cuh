@@ -325,9 +325,21 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
+  // Shard of this CTA's first panel (binary search over the shards' first panels): every
+  // walker starts there, so a lookup walks at most the shards the CTA spans, not all shards
+  // before it (a walk from shard 0 per lookup made the last CTAs a quarter slower).
+  int shard0 = 0;
+  {
+    int lo = 0, hi = geo.N - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (geo.panel_start[mid] <= p_begin) lo = mid; else hi = mid - 1;
+    }
+    shard0 = lo;
+  }
   // Panel k -> (first row, rows, shard) with a forward-moving shard hint.
   struct PanelWalk {
-    int hint = 0;
+    int hint;
     __device__ void at(const PassGeometry& g, int64_t p, int64_t& row0, int& nrows, int& shard) {
       locate_panel<kTcRows>(g, p, hint, row0, nrows);
       shard = hint;
@@ -336,7 +348,7 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
   // shard of panel k (k < np) or -1
   auto shard_of = [&](int k) -> int {
     if (k < 0 || k >= np) return -1;
-    PanelWalk t;
+    PanelWalk t{shard0};
     int64_t r0;
     int nr, sh;
     t.at(geo, p_begin + k, r0, nr, sh);
@@ -344,7 +356,7 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
   };
   // Step order shared by the producer and the MMA issuer: calls fn(is_forward, k).
   auto schedule = [&](auto&& fn) {
-    PanelWalk pw;
+    PanelWalk pw{shard0};
     int prev_shard = -1;
     for (int k = 0; k < np; ++k) {
       int64_t r0;
@@ -365,7 +377,7 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
     // ---------------------------------------------------------------- producer
     if (lane == 0) {
       long long j = 0;
-      PanelWalk pw;
+      PanelWalk pw{shard0};
       // forward loads are read again by the backward of the same panel: keep them in L2;
       // the backward load is their last use
       const uint64_t keep = l2_policy_evict_last(), drop = l2_policy_evict_first();
@@ -471,7 +483,7 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
     const int r = warp * 16 + (lane & 15);  // panel row of this thread
     int seg = 0;
     bool eok = true;
-    PanelWalk pw;
+    PanelWalk pw{shard0};
     // prefetched row data of the next panel
     float nur[KC], wv[KC];
     int y = 0;
@@ -479,7 +491,7 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
       int64_t row0 = 0;
       int nrows = 0, sh;
       if (k < np) {
-        PanelWalk t;
+        PanelWalk t{shard0};
         t.at(geo, p_begin + k, row0, nrows, sh);
       }
       const bool valid = has_row && k < np && r < nrows;
