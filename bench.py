@@ -166,7 +166,7 @@ PASS_SOURCES = ["paper_2405_16267_b300/csrc/pass.cuh", "paper_2405_16267_b300/cs
 
 
 # The same for the tensor-core softmax pass (60000-row capture scaled to 500000 rows).
-TC_TRAFFIC = {"sources_sha256": "edc5336365d359a2a9ce6ee308ab970916af2b9abc5540a1d61d1f2416369d97", "bytes_per_launch": 2.430e9,
+TC_TRAFFIC = {"sources_sha256": "806df15d084d82674dfe15219c94995dd51111825c9c312e1f2a5769e3e9a6af", "bytes_per_launch": 2.468e9,
               "capture": "profiles/k_fused_pass_tc_sparse_softmax_500000x2000x10_bf16.md"}
 TC_SOURCES = ["paper_2405_16267_b300/csrc/mc_tc.cuh", "paper_2405_16267_b300/csrc/nspace.cuh",
               "paper_2405_16267_b300/csrc/common.cuh", "paper_2405_16267_b300/csrc/pass.cuh"]
