@@ -159,10 +159,10 @@ class ClockSampler:
 # DRAM traffic of one pass launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of a 20000-row launch of the same kernel, scaled by rows to the
 # 200000-row launch.  Reported only while the kernel sources are the captured ones.
-PASS_TRAFFIC = {"sources_sha256": "b7c8005d37702fbdd76fee5ef61bbb2c0fecde95a9da3344be79c881206e0d1a", "bytes_per_launch": 4.0721e9,
+PASS_TRAFFIC = {"sources_sha256": "e735e11d90201c094bdb5c6e9e8761dc986b6887b9fdf72fd727cf0a00b0e76c", "bytes_per_launch": 4.0721e9,
                 "capture": "profiles/k_fused_pass_sparse_logistic_200000x5000_fp32.md"}
 PASS_SOURCES = ["paper_2405_16267_b300/csrc/pass.cuh", "paper_2405_16267_b300/csrc/nspace.cuh",
-                "paper_2405_16267_b300/csrc/common.cuh", "paper_2405_16267_b300/csrc/bicadmm.cu"]
+                "paper_2405_16267_b300/csrc/common.cuh"]
 
 
 # The same for the tensor-core softmax pass (60000-row capture scaled to 500000 rows).
