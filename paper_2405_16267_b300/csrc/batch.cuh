@@ -682,30 +682,11 @@ k_dual_batch(const BatchInst* __restrict__ inst, const DItem* __restrict__ items
   __syncthreads();
   if (!last) return;
   __threadfence();
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    double pr = 0.0, nx = 0.0;
-    for (int ii = lane; ii < N; ii += 32) {
-      double s0 = 0.0, s1 = 0.0;
-      for (int cidx = 0; cidx < nch; ++cidx) {
-        s0 += I.dual_part[(static_cast<int64_t>(ii) * nch + cidx) * 2 + 0];
-        s1 += I.dual_part[(static_cast<int64_t>(ii) * nch + cidx) * 2 + 1];
-      }
-      pr += sqrt(s0);
-      nx += sqrt(s1);
-    }
-    pr = warp_sum(pr);
-    nx = warp_sum(nx);
-    double q0 = 0.0, q1 = 0.0, q2 = 0.0;
-    for (int g = lane; g < I.G_inst; g += 32) {
-      q0 += I.cta_stats[g * 4 + 0];
-      q1 += I.cta_stats[g * 4 + 1];
-      q2 += I.cta_stats[g * 4 + 2];
-    }
-    q0 = warp_sum(q0);
-    q1 = warp_sum(q1);
-    q2 = warp_sum(q2);
-    if (lane == 0) {
+  double fs[5];
+  dual_final_sums<DT>(I.dual_part, N, nch, I.cta_stats, I.G_inst, fs);
+  {
+    const double pr = fs[0], nx = fs[1], q0 = fs[2], q1 = fs[3], q2 = fs[4];
+    if (threadIdx.x == 0) {
       GlobalState* gs = I.gs;
       Resid& rec = I.trace[gs->iter % kTraceCapacity];
       rec.p_r = pr;

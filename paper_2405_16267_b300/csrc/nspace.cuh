@@ -419,6 +419,52 @@ static __global__ void k_consensus_prep(const double* __restrict__ x, const doub
 // fixed-order sum of the last pass's slots of shard i.  The last CTA to finish reduces the
 // sums (fixed order) with the pass's inner-residual sums into the residual record and
 // advances the iteration counter.
+// The last CTA's sums in k_dual / k_dual_batch, in a fixed order with the whole CTA: warp w
+// takes shards w, w + NW, ... and its lanes the chunks lane, lane + 32, ... of each (one
+// warp_sum per shard), every thread a strided share of the pass CTAs' statistics; per-warp
+// results are added in warp order by thread 0, which receives pr = sum_i ||x_i - z||,
+// nx = sum_i ||x_i|| and the three inner-residual sums.
+template <int DT>
+__device__ __forceinline__ void dual_final_sums(const double* __restrict__ part, int N, int nch,
+                                                const double* __restrict__ cta_stats, int G,
+                                                double (&out)[5]) {
+  constexpr int NW = DT / 32;
+  __shared__ double fin[NW * 5];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double w[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int ii = warp; ii < N; ii += NW) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int c = lane; c < nch; c += 32) {
+      s0 += part[(static_cast<int64_t>(ii) * nch + c) * 2 + 0];
+      s1 += part[(static_cast<int64_t>(ii) * nch + c) * 2 + 1];
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    w[0] += sqrt(s0);
+    w[1] += sqrt(s1);
+  }
+  double g[3] = {0.0, 0.0, 0.0};
+  for (int q = threadIdx.x; q < G; q += DT) {
+    g[0] += cta_stats[q * 4 + 0];
+    g[1] += cta_stats[q * 4 + 1];
+    g[2] += cta_stats[q * 4 + 2];
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) w[2 + k] = warp_sum(g[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) fin[warp * 5 + k] = w[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 5; ++k) out[k] = 0.0;
+  if (threadIdx.x == 0) {
+    for (int ww = 0; ww < NW; ++ww)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) out[k] += fin[ww * 5 + k];
+  }
+}
+
 template <typename TM, int DT>
 __global__ void __launch_bounds__(DT)
 k_dual(double* __restrict__ u, const double* __restrict__ x, const double* __restrict__ z,
@@ -453,31 +499,11 @@ k_dual(double* __restrict__ u, const double* __restrict__ x, const double* __res
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // Final reduction by one warp in a fixed order: lane l takes shards l, l+32, ...
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    double pr = 0.0, nx = 0.0;
-    for (int ii = lane; ii < N; ii += 32) {
-      double s0 = 0.0, s1 = 0.0;
-      for (int cidx = 0; cidx < nch; ++cidx) {
-        s0 += part[(static_cast<int64_t>(ii) * nch + cidx) * 2 + 0];
-        s1 += part[(static_cast<int64_t>(ii) * nch + cidx) * 2 + 1];
-      }
-      pr += sqrt(s0);
-      nx += sqrt(s1);
-    }
-    pr = warp_sum(pr);
-    nx = warp_sum(nx);
-    double q0 = 0.0, q1 = 0.0, q2 = 0.0;
-    for (int g = lane; g < G; g += 32) {
-      q0 += cta_stats[g * 4 + 0];
-      q1 += cta_stats[g * 4 + 1];
-      q2 += cta_stats[g * 4 + 2];
-    }
-    q0 = warp_sum(q0);
-    q1 = warp_sum(q1);
-    q2 = warp_sum(q2);
-    if (lane == 0) {
+  double fs[5];
+  dual_final_sums<DT>(part, N, nch, cta_stats, G, fs);
+  {
+    const double pr = fs[0], nx = fs[1], q0 = fs[2], q1 = fs[3], q2 = fs[4];
+    if (threadIdx.x == 0) {
       Resid& rec = trace[gs->iter % trace_cap];
       rec.p_r = pr;
       rec.p_rel = pr / fmax(fmax(nx, N * rec.znorm), 1e-30);
