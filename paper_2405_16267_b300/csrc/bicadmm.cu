@@ -689,7 +689,10 @@ int build_geometry(bicadmm_ctx* h) {
   // One resident slot is kept for the consensus CTA that rides on the last pass.
   const int64_t slots_total = static_cast<int64_t>(occ) * h->num_sms - 1;
   if (slots_total < 1) return fail(h, BICADMM_ERR_UNSUPPORTED, "A-pass needs at least two resident CTAs");
-  h->G = static_cast<int>(std::min<int64_t>(slots_total, h->P_panels));
+  // At least 4 panels per CTA: a shard's A'd partial sums are spread over one slot per CTA
+  // that touches it, and every x-update right-hand side sums them (small problems had
+  // ~60 slots per shard with one panel per CTA).
+  h->G = static_cast<int>(std::min<int64_t>(slots_total, std::max<int64_t>(1, (h->P_panels + 3) / 4)));
   // slots: CTA c writes slot (c + shard) for every shard it touches
   h->slot_lo.assign(h->N, 0);
   h->slot_hi.assign(h->N, 0);
