@@ -658,9 +658,10 @@ k_dual_batch(const BatchInst* __restrict__ inst, const DItem* __restrict__ items
   const BatchInst& I = inst[it.inst];
   const int i = it.shard, nch = I.dual_chunks, N = I.N;
   const int64_t lda = I.lda, n = I.n;
-  const int64_t col = static_cast<int64_t>(it.chunk) * DT + threadIdx.x;
   double a[2] = {0.0, 0.0};
-  if (col < lda) {
+  // each item takes the columns chunk * DT + tid + k * nch * DT of its shard
+  for (int64_t col = static_cast<int64_t>(it.chunk) * DT + threadIdx.x; col < lda;
+       col += static_cast<int64_t>(nch) * DT) {
     const int64_t o = i * lda + col;
     const double xv = I.x[o], zv = I.z[col], dv = xv - zv;
     const double un = I.u[o] + dv;
@@ -669,8 +670,8 @@ k_dual_batch(const BatchInst* __restrict__ inst, const DItem* __restrict__ items
     const TM* slots = static_cast<const TM*>(I.slots);
     for (int sl = I.slot_lo[i]; sl <= I.slot_hi[i]; ++sl) q += slots[sl * lda + col];
     I.r[o] = I.rho_l * static_cast<double>(q) + I.rho_c * (zv - un) - I.c0 * xv;
-    a[0] = dv * dv;
-    a[1] = xv * xv;
+    a[0] += dv * dv;
+    a[1] += xv * xv;
   }
   block_sum<2>(a, red);
   if (threadIdx.x == 0) {

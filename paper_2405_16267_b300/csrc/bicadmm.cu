@@ -708,7 +708,9 @@ int build_geometry(bicadmm_ctx* h) {
     h->slot_hi[i] = owner(h->panel_start[i + 1] - 1) + i;
   }
   h->nslots = h->G + h->N;
-  h->dual_chunks = static_cast<int>((h->ldx + kDualThreads - 1) / kDualThreads);
+  // CTAs per shard of k_dual (each loops over its columns): at most 8, so that few CTAs
+  // take part in the last-CTA ticket
+  h->dual_chunks = static_cast<int>(std::min<int64_t>(8, (h->ldx + kDualThreads - 1) / kDualThreads));
   return BICADMM_OK;
 }
 

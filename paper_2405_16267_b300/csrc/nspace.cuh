@@ -475,9 +475,10 @@ k_dual(double* __restrict__ u, const double* __restrict__ x, const double* __res
   __shared__ double red[32 * 2];
   __shared__ bool last;
   const int i = blockIdx.y, nch = gridDim.x;
-  const int64_t col = static_cast<int64_t>(blockIdx.x) * DT + threadIdx.x;
   double a[2] = {0.0, 0.0};
-  if (col < lda) {
+  // each CTA takes the columns blockIdx.x * DT + tid + k * nch * DT of its shard
+  for (int64_t col = static_cast<int64_t>(blockIdx.x) * DT + threadIdx.x; col < lda;
+       col += static_cast<int64_t>(nch) * DT) {
     const int64_t o = i * lda + col;
     const double xv = x[o], zv = z[col], dv = xv - zv;
     const double un = u[o] + dv;
@@ -485,8 +486,8 @@ k_dual(double* __restrict__ u, const double* __restrict__ x, const double* __res
     TM q = TM(0);  // the slots are partial sums in the arithmetic type of the pass
     for (int sl = slot_lo[i]; sl <= slot_hi[i]; ++sl) q += slots[sl * lda + col];
     r[o] = rho_l * static_cast<double>(q) + rho_c * (zv - un) - c0 * xv;
-    a[0] = dv * dv;  // padding columns hold zeros
-    a[1] = xv * xv;
+    a[0] += dv * dv;  // padding columns hold zeros
+    a[1] += xv * xv;
   }
   block_sum<2>(a, red);
   if (threadIdx.x == 0) {
