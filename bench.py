@@ -159,14 +159,14 @@ class ClockSampler:
 # DRAM traffic of one pass launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of a 20000-row launch of the same kernel, scaled by rows to the
 # 200000-row launch.  Reported only while the kernel sources are the captured ones.
-PASS_TRAFFIC = {"sources_sha256": "aad8007361913c251757c7ecfeb3eb7cda33609a171a141d3e341f560da97ce2", "bytes_per_launch": 4.0625e9,
+PASS_TRAFFIC = {"sources_sha256": "ced2df2fe87b27133f65bd54317ccedf76e2cb66c4548e0f13994549b7446295", "bytes_per_launch": 4.0626e9,
                 "capture": "profiles/k_fused_pass_sparse_logistic_200000x5000_fp32.md"}
 PASS_SOURCES = ["paper_2405_16267_b300/csrc/pass.cuh", "paper_2405_16267_b300/csrc/nspace.cuh",
                 "paper_2405_16267_b300/csrc/common.cuh"]
 
 
 # The same for the tensor-core softmax pass (60000-row capture scaled to 500000 rows).
-TC_TRAFFIC = {"sources_sha256": "96ffb0776bbfa32e9055e3b068bbc77086d4ff24e227276f1b5116ac9ac00ec5", "bytes_per_launch": 2.462e9,
+TC_TRAFFIC = {"sources_sha256": "9b0526507586922457d9ddccce1ff8f7a59db02f3453bf448c4e7e49c91bf91f", "bytes_per_launch": 2.4625e9,
               "capture": "profiles/k_fused_pass_tc_sparse_softmax_500000x2000x10_bf16.md"}
 TC_SOURCES = ["paper_2405_16267_b300/csrc/mc_tc.cuh", "paper_2405_16267_b300/csrc/nspace.cuh",
               "paper_2405_16267_b300/csrc/common.cuh", "paper_2405_16267_b300/csrc/pass.cuh"]
