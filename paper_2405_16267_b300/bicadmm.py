@@ -262,12 +262,42 @@ def get_pass_time(h):
     return ms.value, cnt.value
 
 
+def check_noalloc_args(w, z, s, tvt):
+    """Reject, before any launch, tensors the kernels would index out of bounds: every
+    argument a contiguous float64 CUDA tensor on one device, len(z) == len(s) == len(w) = n,
+    len(tvt) >= 4.  Returns n."""
+    import torch
+    names = ("w", "z", "s", "tvt")
+    for name, t in zip(names, (w, z, s, tvt)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError("%s must be a torch tensor" % name)
+        if t.dtype != torch.float64:
+            raise ValueError("%s must be float64, got %s" % (name, t.dtype))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+    n = w.numel()
+    if z.numel() != n or s.numel() != n:
+        raise ValueError("w, z and s must have the same length (%d, %d, %d)"
+                         % (n, z.numel(), s.numel()))
+    if tvt.numel() < 4:
+        raise ValueError("tvt must hold at least 4 doubles")
+    for name, t in zip(names, (w, z, s, tvt)):
+        if not t.is_cuda:
+            raise ValueError("%s must be a CUDA tensor" % name)
+    if len({t.device for t in (w, z, s, tvt)}) != 1:
+        raise ValueError("w, z, s and tvt must be on one device")
+    if w.device.index != torch.cuda.current_device():
+        raise ValueError("the tensors must be on the current CUDA device (the library "
+                         "launches there)")
+    return n
+
+
 def consensus_step_noalloc(w, z, s, tvt, kappa, N_shards, rho_c, rho_b, stream=None):
     """Allocation-free consensus update on caller device tensors (float64, contiguous):
     w, z, s of length n and tvt of length 4 (see include/bicadmm.h)."""
+    n = check_noalloc_args(w, z, s, tvt)
     if stream is not None and hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
-    n = w.numel()
     _check(lib().bicadmm_consensus_step_noalloc(w.data_ptr(), z.data_ptr(), s.data_ptr(),
                                                 tvt.data_ptr(), n, int(kappa), int(N_shards),
                                                 float(rho_c), float(rho_b), _VP(stream or 0)))

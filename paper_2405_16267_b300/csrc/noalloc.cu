@@ -9,7 +9,9 @@
 // file supplies the scratch.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
+#include <mutex>
 
 #include "bicadmm.h"
 #include "common.cuh"
@@ -40,8 +42,26 @@ struct NoAllocScratch {
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
 // Device address of g_noalloc_scratch, looked up once per device (host code cannot use
-// the symbol itself as a device pointer).
-NoAllocScratch* g_scratch_addr[kMaxDevices] = {};
+// the symbol itself as a device pointer).  The first lookup on a device runs under a
+// mutex, so first calls from several host threads are well defined.
+std::atomic<NoAllocScratch*> g_scratch_addr[kMaxDevices] = {};
+std::mutex g_scratch_mutex;
+
+NoAllocScratch* scratch_for_device(int dev) {
+  NoAllocScratch* sc = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (sc) return sc;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  sc = g_scratch_addr[dev].load(std::memory_order_relaxed);
+  if (sc) return sc;
+  void* ptr = nullptr;
+  if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  sc = static_cast<NoAllocScratch*>(ptr);
+  g_scratch_addr[dev].store(sc, std::memory_order_release);
+  return sc;
+}
 
 __global__ void k_noalloc_prologue(NoAllocScratch* sc, const double* tvt) {
   // Clear everything the consensus kernel reads before writing; take v^k from the caller.
@@ -74,15 +94,8 @@ extern "C" int bicadmm_consensus_step_noalloc(const double* w, double* z, double
     cudaGetLastError();
     return BICADMM_ERR_CUDA;
   }
-  if (!g_scratch_addr[dev]) {
-    void* ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
-      cudaGetLastError();
-      return BICADMM_ERR_CUDA;
-    }
-    g_scratch_addr[dev] = static_cast<NoAllocScratch*>(ptr);
-  }
-  NoAllocScratch* sc = g_scratch_addr[dev];
+  NoAllocScratch* sc = scratch_for_device(dev);
+  if (!sc) return BICADMM_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   k_noalloc_prologue<<<1, 1, 0, st>>>(sc, tvt);
   ConsensusArgs a{};

@@ -11,6 +11,13 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA device (B300, sm_103a)")
     config.addinivalue_line("markers", "slow: longer CPU test")
+    # Child processes of tests/test_oracle_mutants.py plant one mistake in the oracle.
+    mutant = os.environ.get("BICADMM_ORACLE_MUTANT")
+    if mutant:
+        sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+        import oracle_mutants
+        from oracle import bicadmm_ref
+        oracle_mutants.apply(bicadmm_ref, mutant)
 
 
 def pytest_collection_modifyitems(config, items):

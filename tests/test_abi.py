@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 from paper_2405_16267_b300 import bicadmm as bc
@@ -82,3 +84,26 @@ def test_null_handle_calls_are_safe(lib):
     assert lib.bicadmm_destroy(None) == 0
     assert lib.bicadmm_step(None, 1, None) == -1
     assert lib.bicadmm_default_params(None) == -1
+
+
+def test_noalloc_binding_rejects_bad_tensors_before_launch():
+    """The allocation-free entry point indexes w, z, s (n doubles) and tvt (4 doubles) on the
+    device; the binding rejects every argument that would make it read or write outside them,
+    on the host, before any launch (CPU tensors here, so no launch is even possible)."""
+    import torch
+    n = 16
+    ok = lambda k=n: torch.zeros(k, dtype=torch.float64)
+    tvt = ok(4)
+    bad_cases = [
+        ("float64", (ok().float(), ok(), ok(), tvt)),
+        ("float64", (ok(), ok(), ok(), tvt.float())),
+        ("contiguous", (ok(2 * n)[::2], ok(), ok(), tvt)),
+        ("same length", (ok(), ok(n - 1), ok(), tvt)),
+        ("same length", (ok(), ok(), ok(n + 1), tvt)),
+        ("at least 4", (ok(), ok(), ok(), ok(3))),
+        ("torch tensor", (np.zeros(n), ok(), ok(), tvt)),
+        ("CUDA tensor", (ok(), ok(), ok(), tvt)),
+    ]
+    for what, args in bad_cases:
+        with pytest.raises(ValueError, match=what):
+            bc.consensus_step_noalloc(*args, kappa=2, N_shards=1, rho_c=1.0, rho_b=0.5)

@@ -36,6 +36,29 @@ def test_zt_step_worked_examples(case):
     assert abs(t - g["expected"]["t"]) < 1e-14
 
 
+# ----------------------------------------------------------------- residuals
+
+@pytest.mark.parametrize("case", range(3))
+def test_residuals_worked_examples(case):
+    """Termination residuals (Sec. 3) and their relative forms on hand-derived states: the
+    oracle's solver object is given the state directly (one row per shard, M = 1)."""
+    g = golden()["residuals"][case]
+    inp = g["inputs"]
+    N = inp["N"]
+    x = np.array(inp["x"], dtype=np.float64)
+    n = x.shape[1]
+    o = ref.BiCADMM(np.eye(N, n) + 1.0, np.zeros(N), ref.LOSS_SQUARED, N, 1, 1,
+                    rho_c=inp["rho_c"])
+    o.x = x
+    o.z = np.array(inp["z"], dtype=np.float64)
+    o.t = inp["t"]
+    o.Axbar = np.array(inp["Axbar"], dtype=np.float64)
+    o.omega = np.array(inp["omega"], dtype=np.float64)
+    r = o.residuals(np.array(inp["z_prev"], dtype=np.float64), inp["g"])
+    for key, want in g["expected"].items():
+        assert abs(r[key] - want) <= 1e-15 * max(1.0, abs(want)), (key, r[key], want)
+
+
 def _zt_objective(z, t, w, s, v, N, rho_c, rho_b):
     return 0.5 * N * rho_c * np.sum((z - w) ** 2) + 0.5 * rho_b * (s @ z - t + v) ** 2
 
