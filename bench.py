@@ -11,8 +11,12 @@ global (z,t,s,v) step, dual update).  `value` is outer iterations per second wit
 resident in HBM; `e2e` is the same metric through the public C ABI from pinned host
 buffers (create + setup + K iterations + get_x, H2D of A and b inside the timed region).
 
---impl reference times the FP64 CPU oracle on a bounded sample (one of the 16 shards)
-and extrapolates to the whole workload.
+The default line also carries `legs.softmax`: the 500000 x 2000 x 10 BF16 softmax workload's
+value, tensor-core pass roofline and end-to-end figure (skip with --no-legs).
+
+--impl reference times the FP64 CPU oracle on a bounded sample (one of the 16 shards): its
+steps are shard iterations (steps x ms_per_step = the time spent) and its value is the
+whole workload's rate extrapolated from them (`extrapolated`, `extrapolation_factor`).
 """
 from __future__ import annotations
 
@@ -51,6 +55,8 @@ def parse():
     ap.add_argument("--pass-stages", type=int, default=0)
     ap.add_argument("--inner", type=int, default=1, help="inner sharing sweeps J per iteration")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance leg")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="default workload only: skip the softmax leg added to its line")
     ap.add_argument("--workload", default="logistic", choices=["logistic", "softmax", "batch", "serve"],
                     help="softmax: 500000 x 2000 BF16, 10 classes (tensor-core pass); "
                          "batch: 256 uneven instances advanced by batched launches; "
@@ -458,6 +464,21 @@ def run_softmax(args, rank, world):
     }
 
 
+def softmax_leg(args):
+    """The softmax workload's figures (tensor-core pass), measured in the default run so they
+    appear beside the headline: its own value, roofline of k_fused_pass_tc and end to end."""
+    import copy
+    a = copy.copy(args)
+    a.steps = min(args.steps, 300)
+    a.warmup = max(args.warmup, 3)
+    a.pass_rows = 0
+    a.inner = 1
+    r = run_softmax(a, 0, 1)
+    keep = ("metric", "value", "unit", "steps", "warmup", "ms_per_step", "dtype", "config",
+            "roofline", "e2e", "gpu_launches", "clocks", "live_kernel_ms")
+    return {k: r[k] for k in keep if k in r}
+
+
 def run_oracle_softmax(wl, steps, budget_s=30.0):
     """The FP64 oracle on shard 0 of the softmax workload (BF16-rounded A, as the GPU path
     sees it); one full iteration extrapolated as N times one shard's iteration."""
@@ -737,18 +758,26 @@ def run_oracle_sample(wl, steps, warmup, budget_s=90.0):
               "timed, %.3f s each; full iteration extrapolated as %d x that"
               % (wl["N"], r1 - r0, wl["n"], wl["M"], done, dt, wl["N"]))
     return {"value": value, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-            "sample": sample, "steps_timed": done}
+            "sample": sample, "steps_timed": done, "seconds_per_sample_step": dt,
+            "seconds_timed": dt * done, "extrapolated": True}
 
 
 def run_reference(args, rank, world):
+    """The oracle arm.  A step here is what was actually timed: one outer iteration of shard
+    0 (1/N of the workload's rows); steps x ms_per_step is the time spent.  `value` is the
+    whole workload's iterations/s, extrapolated as N shard iterations per iteration
+    (`extrapolated`, `extrapolation_factor`)."""
     if rank != 0:
         return None
     wl = dict(WORKLOAD)
     cb = run_oracle_sample(wl, args.steps, args.warmup)
     return {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
             "n_gpus": world, "steps": cb["steps_timed"], "warmup": args.warmup,
-            "ms_per_step": 1000.0 / cb["value"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            "ms_per_step": 1000.0 * cb["seconds_per_sample_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            "step_unit": "one outer iteration of shard 0 of %d (the timed sample)" % wl["N"],
+            "extrapolated": True, "extrapolation_factor": wl["N"],
+            "timed_seconds": cb["seconds_timed"],
             "config": config_dict(wl), "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -780,6 +809,8 @@ def main():
             res["time_to_tol"] = run_time_to_tol(torch.cuda.current_stream())
         if rank == 0 and not args.no_cpu_baseline and world == 1:
             res["cpu_baseline"] = run_oracle_sample(dict(WORKLOAD), steps=8, warmup=1, budget_s=20.0)
+        if world == 1 and not args.no_legs and args.m is None:
+            res["legs"] = {"softmax": softmax_leg(args)}
     if world > 1 and args.impl == "gpu":
         import torch.distributed as dist
         dist.destroy_process_group()

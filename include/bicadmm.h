@@ -115,7 +115,13 @@ typedef struct {
   double i_r;            /* inner sharing residual ||Axbar - omega||                   */
   double p_rel, d_rel, b_rel, i_rel;  /* relative forms used by the stop rule           */
   double t, v, tau;      /* bi-linear scalars and the l1 multiplier / (N rho_c)         */
-  int64_t kernel_launches;  /* kernels this handle has launched since create          */
+  int64_t kernel_launches;  /* iteration kernels this handle has launched since create
+                               (step/solve; the objective's kernels are not counted)   */
+  double objective;      /* F(z) = sum_r l(a_r z; b_r) + ||z||^2 / (2 gamma), problem
+                            (p:SML) of Sec. 2 at the consensus iterate z, with the stored
+                            (rounded) A and every product and sum in FP64.  Computed on the
+                            device when info is returned (three small launches; a row
+                            product runs only over the features where z is nonzero).     */
 } bicadmm_info;
 
 /* Fill *p with defaults: squared loss, FP64, gamma 10, rho_c 1, rho_b = rho_c/2,
@@ -195,6 +201,17 @@ int bicadmm_get_trace(bicadmm_t h, double* out_host, int64_t max_records, int64_
 int bicadmm_set_profiling(bicadmm_t h, int32_t on);
 int bicadmm_get_kernel_times(bicadmm_t h, double* ms_out, int64_t* launches_out, int32_t reset);
 int bicadmm_get_pass_time(bicadmm_t h, double* ms_out, int64_t* launches_out);
+
+/* Fault injection for tests (the paper has no counterpart; no effect unless called).
+ * From the next K = 1 A-pass launch on, the load of panel `panel` (a global panel index,
+ * 0 <= panel < the handle's panel count) is never posted: neither its expected byte count
+ * nor its copy is issued, so the CTA that owns it waits at most wait_limit_cycles (>= 1000
+ * SM cycles) on that stage, records BICADMM_ERR_TIMEOUT, lets the copies it did post land
+ * and exits; no other CTA waits on it and nothing faults.  The handle's iterates are then
+ * invalid: destroy it.  panel < 0 disarms the hook and restores the normal wait limit
+ * (about 2 s).  Errors: ERR_ARG (no such panel, K > 1, limit too small), ERR_STATE with
+ * graph replay on. */
+int bicadmm_inject_pass_stall(bicadmm_t h, int64_t panel, int64_t wait_limit_cycles);
 
 /* Allocation-free consensus update.  The paper has no counterpart: this entry point exists
  * for callers that cannot call cudaMalloc when they call in, such as code running while a

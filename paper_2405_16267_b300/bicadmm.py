@@ -43,7 +43,7 @@ class Info(ctypes.Structure):
                 ("p_rel", ctypes.c_double), ("d_rel", ctypes.c_double),
                 ("b_rel", ctypes.c_double), ("i_rel", ctypes.c_double),
                 ("t", ctypes.c_double), ("v", ctypes.c_double), ("tau", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("objective", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -84,6 +84,7 @@ SIGNATURES = [
                                                 ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
     ("bicadmm_get_trace", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
                                          ctypes.POINTER(ctypes.c_int64)]),
+    ("bicadmm_inject_pass_stall", ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int64]),
     ("bicadmm_consensus_step_noalloc", ctypes.c_int,
      [_VP, _VP, _VP, _VP, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
       ctypes.c_double, _VP]),
@@ -260,6 +261,12 @@ def get_pass_time(h):
     cnt = ctypes.c_int64()
     _check(lib().bicadmm_get_pass_time(h, ctypes.byref(ms), ctypes.byref(cnt)), h)
     return ms.value, cnt.value
+
+
+def inject_pass_stall(h, panel, wait_limit_cycles=2_000_000):
+    """Test hook: the next K = 1 A pass never loads `panel`, so its CTA times out after
+    wait_limit_cycles (see include/bicadmm.h); panel < 0 disarms it."""
+    _check(lib().bicadmm_inject_pass_stall(h, int(panel), int(wait_limit_cycles)), h)
 
 
 def check_noalloc_args(w, z, s, tvt):

@@ -10,6 +10,7 @@ import os
 import shutil
 import subprocess
 import sys
+import time
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
@@ -53,11 +54,15 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
            *sorted(glob.glob(os.path.join(CSRC, "*.cu"))), "-o", LIB + ".tmp"]
     if verbose:
         print(" ".join(cmd), flush=True)
+    started = time.time()
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         sys.stderr.write(res.stdout + res.stderr)
         raise RuntimeError("nvcc failed building libbicadmm.so")
     os.replace(LIB + ".tmp", LIB)
+    # Stamp the library with the time the compiler started, so a source edited while it ran
+    # is seen as newer than the library and triggers the next build.
+    os.utime(LIB, (started, started))
     return LIB
 
 

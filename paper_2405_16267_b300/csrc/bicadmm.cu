@@ -29,6 +29,7 @@
 #include "batch.cuh"
 #include "multiclass.cuh"
 #include "mc_tc.cuh"
+#include "objective.cuh"
 #include "gram_tc.cuh"
 #include "pass.cuh"
 #include "polish.cuh"
@@ -88,6 +89,10 @@ struct bicadmm_ctx {
   int R = 0, S = 0, VPT = 0, G = 0, nslots = 0, max_nj = 0, max_ldp = 0, dual_chunks = 0;
   int64_t P_panels = 0, G_total = 0, P_total = 0;
   size_t pass_smem = 0;
+  // fault injection for tests (bicadmm_inject_pass_stall): the K = 1 pass never posts the
+  // load of stall_panel and waits at most wait_limit cycles on a stage
+  int64_t stall_panel = -1;
+  long long wait_limit = kWaitLimitCycles;
 
   // device buffers
   void *A = nullptr, *b = nullptr, *omega = nullptr, *nu = nullptr, *slots = nullptr,
@@ -104,6 +109,11 @@ struct bicadmm_ctx {
   GlobalState* gs = nullptr;
   Resid* trace = nullptr;
   int* d_err = nullptr;
+  // objective F(z): compacted nonzero features, their count, per-CTA partial sums, and
+  // out[0] = F(z), out[1] = ||z||^2
+  int *obj_idx = nullptr, *obj_cnt = nullptr;
+  double *obj_part = nullptr, *obj_out = nullptr;
+  int obj_blocks = 0;
   std::vector<void*> allocs;
 
   // polish buffers (allocated on first use)
@@ -212,12 +222,12 @@ int launch_pass_rv(bicadmm_ctx* h, bool with_consensus) {
     CK(allow_max_dynamic_smem(kern));
     attr_set = true;
   }
-  PassGeometry geo{h->d_shard_row0, h->d_panel_start, h->N, h->P_panels};
+  PassGeometry geo{h->d_shard_row0, h->d_panel_start, h->N, h->P_panels, h->stall_panel};
   kern<<<h->G + (with_consensus ? 1 : 0), kPassThreads, h->pass_smem, h->stream>>>(
       static_cast<const TA*>(h->A), h->lda, static_cast<const TM*>(h->xlo),
       static_cast<const TM*>(h->b), static_cast<TM*>(h->omega), static_cast<TM*>(h->nu),
       static_cast<TM*>(h->slots), h->cta_stats, geo, h->S, h->p.loss, static_cast<TM>(h->M),
-      static_cast<TM>(h->p.rho_l), h->p.newton_iters, h->d_err, kWaitLimitCycles,
+      static_cast<TM>(h->p.rho_l), h->p.newton_iters, h->d_err, h->wait_limit,
       consensus_args(h, with_consensus));
   CK(cudaGetLastError());
   return BICADMM_OK;
@@ -270,7 +280,7 @@ int launch_pass_k_v(bicadmm_ctx* h, bool with_consensus, int op, int* blocks) {
       CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, kPassThreads, h->pass_smem));
       return BICADMM_OK;
     }
-    PassGeometry geo{h->d_shard_row0, h->d_panel_start, h->N, h->P_panels};
+    PassGeometry geo{h->d_shard_row0, h->d_panel_start, h->N, h->P_panels, -1};
     kern<<<h->G + (with_consensus ? 1 : 0), kPassThreads, h->pass_smem, h->stream>>>(
         static_cast<const TA*>(h->A), h->lda, static_cast<const TM*>(h->xlo), h->ldx, h->K,
         static_cast<const TM*>(h->b), static_cast<TM*>(h->omega), static_cast<TM*>(h->nu),
@@ -311,7 +321,7 @@ int launch_pass_tc_c(bicadmm_ctx* h, bool with_consensus, int op, int* blocks) {
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, kTcThreads, h->pass_smem));
     return BICADMM_OK;
   }
-  PassGeometry geo{h->d_shard_row0, h->d_panel_start, h->N, h->P_panels};
+  PassGeometry geo{h->d_shard_row0, h->d_panel_start, h->N, h->P_panels, -1};
   kern<<<h->G + (with_consensus ? 1 : 0), kTcThreads, h->pass_smem, h->stream>>>(
       h->tmap, h->lda, h->wpk, h->ldx, h->K,
       static_cast<const float*>(h->b), static_cast<float*>(h->omega), static_cast<float*>(h->nu),
@@ -522,7 +532,43 @@ int check_device_error(bicadmm_ctx* h) {
   return fail(h, BICADMM_ERR_CUDA, "unknown device error " + std::to_string(e));
 }
 
-int fill_info(bicadmm_ctx* h, bicadmm_info* info) {
+// F(z) of problem (p:SML) at the current consensus iterate, in FP64 (objective.cuh).  Its
+// three launches are diagnostics: they are not counted in h->launches.
+template <typename TA, typename TM>
+int launch_obj_rows(bicadmm_ctx* h) {
+  if (h->K == 1)
+    k_obj_rows<TA, TM, 1><<<h->obj_blocks, kObjThreads, 0, h->stream>>>(
+        static_cast<const TA*>(h->A), h->lda, static_cast<const TM*>(h->b), h->z, h->obj_idx,
+        h->obj_cnt, h->p.m, 1, h->p.loss, h->obj_part);
+  else
+    k_obj_rows<TA, TM, 16><<<h->obj_blocks, kObjThreads, 0, h->stream>>>(
+        static_cast<const TA*>(h->A), h->lda, static_cast<const TM*>(h->b), h->z, h->obj_idx,
+        h->obj_cnt, h->p.m, h->K, h->p.loss, h->obj_part);
+  CK(cudaGetLastError());
+  return BICADMM_OK;
+}
+
+int compute_objective(bicadmm_ctx* h, double* out) {
+  k_obj_compact<1024><<<1, 1024, 0, h->stream>>>(h->z, h->p.n, h->K, h->obj_idx, h->obj_cnt,
+                                                  h->obj_out);
+  CK(cudaGetLastError());
+  int rc;
+  if (h->asz == 8) rc = launch_obj_rows<double, double>(h);
+  else if (h->asz == 4) rc = launch_obj_rows<float, float>(h);
+  else rc = launch_obj_rows<__nv_bfloat16, float>(h);
+  if (rc != BICADMM_OK) return rc;
+  k_obj_final<256><<<1, 256, 0, h->stream>>>(h->obj_part, h->obj_blocks, h->p.gamma, h->obj_out);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out, h->obj_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  return BICADMM_OK;
+}
+
+int fill_info(bicadmm_ctx* h, bicadmm_info* info, bool objective = true) {
+  double obj = 0.0;
+  if (objective) {
+    const int rc = compute_objective(h, &obj);
+    if (rc != BICADMM_OK) return rc;
+  }
   GlobalState g;
   CK(cudaMemcpyAsync(&g, h->gs, sizeof(g), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -542,6 +588,7 @@ int fill_info(bicadmm_ctx* h, bicadmm_info* info) {
     info->p_rel = rec.p_rel; info->d_rel = rec.d_rel; info->b_rel = rec.b_rel;
     info->i_rel = rec.i_rel;
   }
+  info->objective = obj;
   return check_device_error(h);
 }
 
@@ -772,6 +819,11 @@ int allocate(bicadmm_ctx* h) {
   AL(h->gs, sizeof(GlobalState));
   AL(h->trace, kTraceCap * sizeof(Resid));
   AL(h->d_err, sizeof(int));
+  h->obj_blocks = std::max(1, h->num_sms) * 4;
+  AL(h->obj_idx, h->p.n * sizeof(int));
+  AL(h->obj_cnt, sizeof(int));
+  AL(h->obj_part, static_cast<size_t>(h->obj_blocks) * sizeof(double));
+  AL(h->obj_out, 2 * sizeof(double));
 #undef AL
   auto up = [&](void* dst, const void* src, size_t bytes) {
     return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->stream);
@@ -1829,7 +1881,7 @@ int bicadmm_setup(bicadmm_t h, const void* A, int32_t A_dtype, int64_t lda, int3
 
 // Capture graph_iters outer iterations of the handle into a CUDA graph (the launches are
 // recorded, not run; the counters are restored).
-int capture_graph(bicadmm_ctx* h) {
+static int capture_graph(bicadmm_ctx* h) {
   const int64_t l0 = h->launches, i0 = h->iters_done;
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
@@ -1852,7 +1904,13 @@ int capture_graph(bicadmm_ctx* h) {
   return BICADMM_OK;
 }
 
+static int step_impl(bicadmm_t h, int32_t n_iters, bicadmm_info* info, bool objective);
+
 int bicadmm_step(bicadmm_t h, int32_t n_iters, bicadmm_info* info) {
+  return step_impl(h, n_iters, info, true);
+}
+
+static int step_impl(bicadmm_t h, int32_t n_iters, bicadmm_info* info, bool objective) {
   if (!h) return BICADMM_ERR_ARG;
   if (!h->ready) return fail(h, BICADMM_ERR_STATE, "bicadmm_step before a successful bicadmm_setup");
   if (n_iters < 0) return fail(h, BICADMM_ERR_ARG, "n_iters must be >= 0");
@@ -1877,7 +1935,7 @@ int bicadmm_step(bicadmm_t h, int32_t n_iters, bicadmm_info* info) {
   if (done < n_iters)
     rc = h->esz == 8 ? run_iterations<double>(h, n_iters - done) : run_iterations<float>(h, n_iters - done);
   if (rc != BICADMM_OK) return rc;
-  if (info) return fill_info(h, info);
+  if (info) return fill_info(h, info, objective);
   return BICADMM_OK;
 }
 
@@ -1903,7 +1961,7 @@ int bicadmm_solve(bicadmm_t h, bicadmm_info* info) {
   h->converged = false;
   while (done < h->p.max_iters) {
     const int k = std::min(h->p.check_every, h->p.max_iters - done);
-    int rc = bicadmm_step(h, k, &loc);
+    int rc = step_impl(h, k, &loc, false);
     if (rc != BICADMM_OK) return rc;
     done += k;
     const double mx = std::max(std::max(loc.p_rel, loc.d_rel), std::max(loc.b_rel, loc.i_rel));
@@ -2084,6 +2142,18 @@ int bicadmm_get_kernel_times(bicadmm_t h, double* ms_out, int64_t* launches_out,
     h->ev_used = 0;
     h->ev_kind.clear();
   }
+  return BICADMM_OK;
+}
+
+int bicadmm_inject_pass_stall(bicadmm_t h, int64_t panel, int64_t wait_limit_cycles) {
+  if (!h) return BICADMM_ERR_ARG;
+  if (panel >= 0 && (!h->ready || h->K != 1 || panel >= h->P_panels))
+    return fail(h, BICADMM_ERR_ARG, "stall panel must be a panel of a set-up K = 1 handle");
+  if (panel >= 0 && wait_limit_cycles < 1000)
+    return fail(h, BICADMM_ERR_ARG, "wait limit must be at least 1000 cycles");
+  if (panel >= 0 && h->graph) return fail(h, BICADMM_ERR_STATE, "not with graph replay");
+  h->stall_panel = panel >= 0 ? panel : -1;
+  h->wait_limit = panel >= 0 ? static_cast<long long>(wait_limit_cycles) : kWaitLimitCycles;
   return BICADMM_OK;
 }
 

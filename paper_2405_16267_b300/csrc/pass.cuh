@@ -100,6 +100,7 @@ struct PassGeometry {
   const int64_t* panel_start;  // N + 1 first panel index of each shard
   int N;
   int64_t P;                   // total panels
+  int64_t stall_panel;         // test hook: this panel's load is never posted (-1: none)
 };
 
 // Locate panel p: its shard i (searching forward from `hint`), first row and row count.
@@ -174,6 +175,7 @@ k_fused_pass(const TA* __restrict__ A, int64_t lda, const TM* __restrict__ xlo_i
     int nrows;
     locate_panel<R>(geo, p_begin + k, issue_shard, row0, nrows);
     const int st = static_cast<int>(k % S);
+    if (p_begin + k == geo.stall_panel) return;  // test hook: no transaction, no copy
     const uint32_t bytes = static_cast<uint32_t>(nrows * lda * sizeof(TA));
     mbar_arrive_expect_tx(&bars[st], bytes);
     bulk_copy_g2s(stages + st * stage_elems, A + row0 * lda, bytes, &bars[st]);
@@ -238,11 +240,15 @@ k_fused_pass(const TA* __restrict__ A, int64_t lda, const TM* __restrict__ xlo_i
     const uint32_t parity = static_cast<uint32_t>((k / S) & 1);
     const bool ok = mbar_wait_bounded(&bars[st], parity, wait_limit);
     if (__syncthreads_or(!ok)) {
-      // Give up: report, then let the copies already in flight land before exiting.
+      // Give up: report, then let every copy in flight land before exiting (each with the
+      // full wait limit, whatever limit the pass ran with; a panel whose load was never
+      // posted has nothing to wait for).
       if (tid == 0) {
         set_err(err, DEV_TIMEOUT_PASS);
-        for (int64_t q = k; q < n_issued; ++q)
-          mbar_wait_bounded(&bars[q % S], static_cast<uint32_t>((q / S) & 1), wait_limit);
+        for (int64_t q = k; q < n_issued; ++q) {
+          if (p_begin + q == geo.stall_panel) continue;
+          mbar_wait_bounded(&bars[q % S], static_cast<uint32_t>((q / S) & 1), kWaitLimitCycles);
+        }
       }
       return;
     }

@@ -56,3 +56,35 @@ def compare_state(st, o, tol, support_exact=True):
         # the nonzero pattern of s (the selected top-kappa set) matches exactly
         assert np.array_equal(st["s"] != 0, o.s != 0)
     return errs
+
+
+def consensus_state(solver):
+    """The n-space part of a Solver's state (x, u, z, s and the scalars t, v, tau); leaves
+    out the m-space omega/nu, which are large at full size."""
+    N, n = solver.N, solver.n * solver.K
+    sc = bc.get_state(solver.h, bc.FIELD_SCALARS, 3)
+    return dict(x=bc.get_state(solver.h, bc.FIELD_X, N * n).reshape(N, n),
+                u=bc.get_state(solver.h, bc.FIELD_U, N * n).reshape(N, n),
+                z=bc.get_state(solver.h, bc.FIELD_Z, n), s=bc.get_state(solver.h, bc.FIELD_S, n),
+                t=sc[0], v=sc[1], tau=sc[2])
+
+
+def check_consensus_step(prev, cur, N, rho_c, rho_b, kappa, tol=1e-9):
+    """One outer iteration's global step against the oracle, element by element: the GPU's
+    own w = mean_i(x_i^{k+1} + u_i^k), s^k and v^k go through ref.zt_step (eq.
+    global-z-t-updae) and its z^{k+1}, t^{k+1} through ref.s_step (eq. s-update-final); z, t,
+    tau, s and v (eq. v-update) must agree, and s must select the same entries.  Returns tau."""
+    w = (cur["x"] + prev["u"]).mean(axis=0)
+    z, t, tau = ref.zt_step(w, prev["s"], prev["v"], N, rho_c, rho_b)
+    zs = max(float(np.max(np.abs(z))), 1e-300)
+    assert float(np.max(np.abs(cur["z"] - z))) <= tol * zs, "z"
+    assert abs(cur["t"] - t) <= tol * max(abs(t), zs), ("t", cur["t"], t)
+    assert abs(cur["tau"] - tau) <= tol * max(abs(tau), 1e-12), ("tau", cur["tau"], tau)
+    s = ref.s_step(cur["z"], cur["t"], prev["v"], kappa)
+    assert np.array_equal(s != 0, cur["s"] != 0), "selected entries of s"
+    assert float(np.max(np.abs(cur["s"] - s))) <= 1e-12, "s"
+    v = prev["v"] + float(cur["z"] @ cur["s"]) - cur["t"]
+    assert abs(cur["v"] - v) <= tol * max(abs(v), abs(cur["t"]), 1e-12), ("v", cur["v"], v)
+    np.testing.assert_allclose(cur["u"], prev["u"] + cur["x"] - cur["z"][None, :], rtol=0,
+                               atol=1e-12 * max(1.0, float(np.max(np.abs(cur["x"])))))
+    return tau

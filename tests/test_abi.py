@@ -45,12 +45,38 @@ def test_binding_covers_every_declared_symbol():
     assert set(declared_functions()) <= bound
 
 
-def test_struct_layouts_match_header(lib):
-    # default_params writes every field; sizes are checked against the C struct via offsets
+def _c_layout(struct, fields):
+    """sizeof and offsetof of a header struct, from a C program compiled against the header."""
+    import shutil
+    import subprocess
+    import tempfile
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    body = "".join('  printf("%%s %%zu\\n", "%s", offsetof(%s, %s));\n' % (f, struct, f) for f in fields)
+    src = ("#include <stddef.h>\n#include <stdio.h>\n#include \"bicadmm.h\"\nint main(void) {\n"
+           '  printf("sizeof %%zu\\n", sizeof(%s));\n%s  return 0;\n}\n' % (struct, body))
+    with tempfile.TemporaryDirectory() as d:
+        c, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        with open(c, "w") as f:
+            f.write(src)
+        subprocess.run([cc, "-I", os.path.dirname(HEADER), c, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    return {k: int(v) for k, v in (line.split() for line in out.splitlines())}
+
+
+@pytest.mark.parametrize("struct,cls", [("bicadmm_params", "Params"), ("bicadmm_info", "Info"),
+                                        ("bicadmm_server_params", "ServerParams")])
+def test_struct_layouts_match_header(lib, struct, cls):
+    """Every field of the ctypes mirror sits at the offset the C header gives it."""
+    py = getattr(bc, cls)
+    names = [name for name, _ in py._fields_]
+    want = _c_layout(struct, names)
+    assert ctypes.sizeof(py) == want["sizeof"]
+    for name in names:
+        assert getattr(py, name).offset == want[name], name
     p = bc.default_params()
     assert p.gamma == 10.0 and p.rho_c == 1.0 and p.inner_iters == 1 and p.K == 1
-    assert ctypes.sizeof(bc.Params) == 112
-    assert ctypes.sizeof(bc.Info) == 104
 
 
 @pytest.mark.parametrize("field,value,code", [

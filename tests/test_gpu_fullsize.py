@@ -15,6 +15,8 @@ from oracle import bicadmm_ref as ref
 from paper_2405_16267_b300 import bicadmm as bc
 from paper_2405_16267_b300 import synth
 
+from gpu_util import check_consensus_step, consensus_state
+
 pytestmark = pytest.mark.gpu
 
 TOL32 = 1e-4
@@ -35,13 +37,17 @@ def run():
         st1 = s.state()
         s.step(1)
         st2 = s.state()
+        cons = [consensus_state(s)]          # iteration 2
+        for _ in range(6):                   # iterations 3..8
+            s.step(1)
+            cons.append(consensus_state(s))
     r0, r1 = synth.split_ranges(wl["m"], wl["N"])[0]
     A0 = A[r0:r1].astype(np.float64)
-    return wl, b, A0, st1, st2, (r0, r1)
+    return wl, b, A0, st1, st2, (r0, r1), cons
 
 
 def test_iteration1_omega_every_row(run):
-    wl, b, A0, st1, st2, _ = run
+    wl, b, A0, st1, st2, _, _cons = run
     want = ref.omega_prox(ref.LOSS_LOGISTIC, np.zeros_like(b), b, wl["M"], wl["rho"])
     assert np.max(np.abs(st1["omega"] - want)) <= TOL32 * np.max(np.abs(want))
     np.testing.assert_allclose(st1["nu"], -st1["omega"], rtol=0, atol=TOL32 * np.max(np.abs(want)))
@@ -49,7 +55,7 @@ def test_iteration1_omega_every_row(run):
 
 
 def test_iteration2_shard0_against_oracle(run):
-    wl, b, A0, st1, st2, (r0, r1) = run
+    wl, b, A0, st1, st2, (r0, r1), _cons = run
     o = ref.BiCADMM(A0, b[r0:r1], ref.LOSS_LOGISTIC, 1, wl["M"], wl["kappa"], gamma=wl["gamma"],
                     rho_c=wl["rho"], n_shards_total=wl["N"])
     o.x_step_shard(0)          # iteration 1 (z = u = 0)
@@ -61,7 +67,7 @@ def test_iteration2_shard0_against_oracle(run):
 
 
 def test_iteration2_consensus_properties(run):
-    wl, b, A0, st1, st2, _ = run
+    wl, b, A0, st1, st2, _, _cons = run
     z, s, x, u = st2["z"], st2["s"], st2["x"], st2["u"]
     kappa = wl["kappa"]
     # u after iteration 2 = u1 + x2 - z2 with u1 = 0
@@ -84,3 +90,16 @@ def test_iteration2_consensus_properties(run):
     np.testing.assert_allclose(z, zz, rtol=0, atol=1e-9 * max(1.0, np.abs(w).max()))
     if tau > 0:
         assert abs(t - np.abs(z).sum()) <= 1e-9 * max(1.0, t)
+
+
+def test_consensus_against_oracle_iterations_3_to_8(run):
+    """The global step at full size, element by element against the oracle's (z,t) and s
+    steps fed with the GPU's own w, s^k and v^k (eqs. global-z-t-updae, s-update-final,
+    v-update), from iteration 3 on, where s^k != 0 and the breakpoints of h are nontrivial."""
+    wl, *_, cons = run
+    taus = []
+    for k in range(1, len(cons)):
+        assert np.any(cons[k - 1]["s"] != 0), "s^k must be nonzero from iteration 2 on"
+        taus.append(check_consensus_step(cons[k - 1], cons[k], wl["N"], wl["rho"], 0.5 * wl["rho"],
+                                         wl["kappa"]))
+    assert max(taus) > 0.0, "the l1 constraint was never active"
