@@ -52,10 +52,16 @@ enum {
 
 /* Precision of the stored A and of the per-row arithmetic on the A products.
  * FP64: everything in FP64.  FP32: A, A x and A'd in FP32; the n-space state, the block
- * factors and all residuals stay in FP64.  BF16: A stored in BF16 (rounded to nearest
- * even at setup; half the bytes of FP32), its products accumulated in FP32, everything
- * else as in FP32 mode.  The Gram matrices, factors and polish use the stored (rounded) A. */
-enum { BICADMM_PREC_FP64 = 0, BICADMM_PREC_FP32 = 1, BICADMM_PREC_BF16 = 2 };
+ * factors and all residuals stay in FP64; the Gram matrices A_ij'A_ij of the setup run on
+ * the tensor cores in TF32 with each element split into a TF32 pair hi + lo (three
+ * products per pair, about 22 bits of A), accumulated in FP32.  BF16: A stored in BF16
+ * (rounded to nearest even at setup; half the bytes of FP32), its products accumulated in
+ * FP32, everything else as in FP32 mode.  TF32: A stored in 32-bit words rounded to TF32
+ * (10 mantissa bits, nearest even) at setup, the precision the tensor cores multiply in;
+ * one TF32 product per pair forms the Gram matrices exactly in the FP32 accumulator; the
+ * rest as in FP32 mode (the A x and A'd GEMVs of K = 1 read 4 bytes per element on the
+ * CUDA cores either way).  The Gram matrices, factors and polish use the stored (rounded) A. */
+enum { BICADMM_PREC_FP64 = 0, BICADMM_PREC_FP32 = 1, BICADMM_PREC_BF16 = 2, BICADMM_PREC_TF32 = 3 };
 
 /* Element type of caller buffers passed to bicadmm_setup(). */
 enum { BICADMM_DTYPE_F64 = 0, BICADMM_DTYPE_F32 = 1, BICADMM_DTYPE_BF16 = 2 };
@@ -119,7 +125,7 @@ typedef struct {
                                (step/solve; the objective's kernels are not counted)   */
   double objective;      /* F(z) = sum_r l(a_r z; b_r) + ||z||^2 / (2 gamma), problem
                             (p:SML) of Sec. 2 at the consensus iterate z, with the stored
-                            (rounded) A and every product and sum in FP64.  Computed on the
+                            (rounded) A and b and every product and sum in FP64.  Computed on the
                             device when info is returned (three small launches; a row
                             product runs only over the features where z is nonzero).     */
 } bicadmm_info;

@@ -15,7 +15,7 @@ import numpy as np
 from .build_lib import LIB
 
 LOSS_SQUARED, LOSS_LOGISTIC, LOSS_SOFTMAX, LOSS_SQHINGE = 0, 1, 2, 3
-PREC_FP64, PREC_FP32, PREC_BF16 = 0, 1, 2
+PREC_FP64, PREC_FP32, PREC_BF16, PREC_TF32 = 0, 1, 2, 3
 DTYPE_F64, DTYPE_F32, DTYPE_BF16 = 0, 1, 2
 FIELD_X, FIELD_U, FIELD_Z, FIELD_S, FIELD_OMEGA, FIELD_NU, FIELD_SCALARS, FIELD_P = range(8)
 

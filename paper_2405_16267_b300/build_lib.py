@@ -50,8 +50,9 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if not force and up_to_date():
         return LIB
     os.makedirs(LIBDIR, exist_ok=True)
+    tmp = "%s.tmp.%d" % (LIB, os.getpid())  # concurrent builds never share a partial file
     cmd = [nvcc(), *ARCH, *FLAGS, "-I", INCLUDE, "-I", CSRC, *extra,
-           *sorted(glob.glob(os.path.join(CSRC, "*.cu"))), "-o", LIB + ".tmp"]
+           *sorted(glob.glob(os.path.join(CSRC, "*.cu"))), "-o", tmp]
     if verbose:
         print(" ".join(cmd), flush=True)
     started = time.time()
@@ -59,7 +60,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if res.returncode != 0:
         sys.stderr.write(res.stdout + res.stderr)
         raise RuntimeError("nvcc failed building libbicadmm.so")
-    os.replace(LIB + ".tmp", LIB)
+    os.replace(tmp, LIB)
     # Stamp the library with the time the compiler started, so a source edited while it ran
     # is seen as newer than the library and triggers the next build.
     os.utime(LIB, (started, started))

@@ -30,7 +30,7 @@
 #include "multiclass.cuh"
 #include "mc_tc.cuh"
 #include "objective.cuh"
-#include "gram_tc.cuh"
+#include "gram_tf32.cuh"
 #include "pass.cuh"
 #include "polish.cuh"
 #include "setup.cuh"
@@ -80,6 +80,8 @@ struct bicadmm_ctx {
   int KC = 1;         // compile-time class bucket of the K > 1 kernels
   int64_t ldx = 0;    // n-space row stride, lda K
   bool use_tc = false;  // BF16 softmax: tensor-core A pass (k_fused_pass_tc)
+  bool tf32 = false;    // BICADMM_PREC_TF32: 32-bit storage of A rounded to TF32 (p.precision
+                        // then reads FP32, whose kernels serve it unchanged)
   CUtensorMap tmap;     // 2D map of A (BF16, 64 x 128 boxes, 128-byte swizzle) for it
   double c0 = 0.0;
   size_t esz = 8;  // bytes per m-space / n-space low-precision element (TM)
@@ -595,7 +597,7 @@ int fill_info(bicadmm_ctx* h, bicadmm_info* info, bool objective = true) {
 int validate(const bicadmm_params* p, std::string& why) {
   if (!p) { why = "params is NULL"; return BICADMM_ERR_ARG; }
   if (p->loss != BICADMM_LOSS_SQUARED && p->loss != BICADMM_LOSS_LOGISTIC && p->loss != BICADMM_LOSS_SQHINGE && p->loss != BICADMM_LOSS_SOFTMAX) { why = "unknown loss"; return BICADMM_ERR_ARG; }
-  if (p->precision != BICADMM_PREC_FP64 && p->precision != BICADMM_PREC_FP32 && p->precision != BICADMM_PREC_BF16) { why = "unknown precision"; return BICADMM_ERR_ARG; }
+  if (p->precision != BICADMM_PREC_FP64 && p->precision != BICADMM_PREC_FP32 && p->precision != BICADMM_PREC_BF16 && p->precision != BICADMM_PREC_TF32) { why = "unknown precision"; return BICADMM_ERR_ARG; }
   if (p->m < 1 || p->n < 1) { why = "m and n must be >= 1"; return BICADMM_ERR_ARG; }
   if (p->loss == BICADMM_LOSS_SOFTMAX ? (p->K < 2 || p->K > 16) : p->K != 1) { why = "K must be 2..16 for softmax and 1 otherwise"; return BICADMM_ERR_ARG; }
   if (p->N_shards < 1 || p->N_shards > p->m) { why = "need 1 <= N_shards <= m"; return BICADMM_ERR_ARG; }
@@ -929,35 +931,55 @@ int build_factors(bicadmm_ctx* h, const std::function<int(int)>* load_shard = nu
   if (e != cudaSuccess) { cudaGetLastError(); return fail(h, BICADMM_ERR_OOM, "Gram buffer allocation failed"); }
 
   int rc = BICADMM_OK;
-  GramItem* d_items = nullptr;
-  if constexpr (std::is_same<TA, __nv_bfloat16>::value) {
-    // tensor cores: (shard, block, 128-column strip, 256-column chunk) items over each
-    // block's 64-aligned column window, chunk/strip pairs that touch the upper triangle
-    std::vector<GramItem> items;
+  Gram32Item* d_items32 = nullptr;
+  if constexpr (!std::is_same<TA, double>::value) {
+    // tensor cores, kind::tf32 (gram_tf32.cuh): (shard, block, 128-column strip, 128-column
+    // chunk) items over each block's own columns, chunks at or right of the strip.  FP32
+    // storage splits A into TF32 hi + lo (three products); TF32 storage (rounded first) and
+    // BF16 storage (exact in TF32) take one product.
+    std::vector<Gram32Item> items;
     std::vector<size_t> first(h->N + 1, 0);  // items of shard i: [first[i], first[i + 1])
     for (int i = 0; i < h->N; ++i) {
       first[i] = items.size();
       for (int j = 0; j < h->M; ++j) {
-        const int c0 = h->blk_col0[j], c1 = h->blk_col0[j + 1];
-        const int w = ((c1 + 63) & ~63) - (c0 & ~63);
-        for (int a = 0; a < (w + 127) / 128; ++a)
-          for (int bq = 0; bq < (w + 255) / 256; ++bq)
-            if (256 * bq + 256 > 128 * a) items.push_back(GramItem{i, j, a, bq});
+        const int nj = h->blk_col0[j + 1] - h->blk_col0[j];
+        for (int a = 0; a < (nj + 127) / 128; ++a)
+          for (int bq = a; bq < (nj + 127) / 128; ++bq) items.push_back(Gram32Item{i, j, a, bq});
       }
     }
     first[h->N] = items.size();
-    e = cudaMalloc(&d_items, items.size() * sizeof(GramItem));
+    constexpr bool kBf16 = std::is_same<TA, __nv_bfloat16>::value;
+    const int terms = (kBf16 || h->tf32) ? 1 : 3;
+    e = cudaMalloc(&d_items32, std::max<size_t>(items.size(), 1) * sizeof(Gram32Item));
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(GramItem), cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = allow_max_dynamic_smem(k_gram_tc);
-    // one launch for all shards, or one per shard after its rows have arrived
+      e = cudaMemcpyAsync(d_items32, items.data(), items.size() * sizeof(Gram32Item), cudaMemcpyHostToDevice, h->stream);
+    const size_t sm = gram_tf32_smem(128, terms);
+    if (e == cudaSuccess)
+      e = terms == 3 ? cudaFuncSetAttribute(k_gram_tf32<3, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm))
+                     : cudaFuncSetAttribute(k_gram_tf32<1, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
+    // one launch for all shards, or one per shard after its rows have arrived (TF32 storage:
+    // the rows are rounded first)
     for (int i = 0; e == cudaSuccess && rc == BICADMM_OK && i < (load_shard ? h->N : 1); ++i) {
       const size_t i0 = load_shard ? first[i] : 0, i1 = load_shard ? first[i + 1] : items.size();
       if (load_shard) rc = (*load_shard)(i);
-      if (rc == BICADMM_OK && i1 > i0) {
-        k_gram_tc<<<static_cast<unsigned>(i1 - i0), kGramThreads, gram_tc_smem(), h->stream>>>(
-            h->tmap, d_items + i0, h->d_shard_row0, h->d_blk_col0, G, h->d_G_off, h->M, h->d_err,
-            kWaitLimitCycles);
+      if constexpr (!kBf16) {
+        if (rc == BICADMM_OK && h->tf32) {
+          const int64_t r0 = load_shard ? h->shard_row0[i] : 0, r1 = load_shard ? h->shard_row0[i + 1] : h->p.m;
+          const unsigned grid = static_cast<unsigned>(std::min<int64_t>(((r1 - r0) * h->lda + 255) / 256, 8192));
+          k_round_tf32<<<grid, 256, 0, h->stream>>>(reinterpret_cast<float*>(h->A), h->lda, r0, r1);
+          e = cudaGetLastError();
+          h->launches += 1;
+        }
+      }
+      if (e == cudaSuccess && rc == BICADMM_OK && i1 > i0) {
+        const unsigned grid = static_cast<unsigned>(i1 - i0);
+        const TA* Ap = static_cast<const TA*>(h->A);
+        if (terms == 3)
+          k_gram_tf32<3, TA><<<grid, kG32Threads, sm, h->stream>>>(Ap, h->lda, d_items32 + i0, h->d_shard_row0,
+              h->d_blk_col0, G, h->d_G_off, h->M, h->d_err, kWaitLimitCycles);
+        else
+          k_gram_tf32<1, TA><<<grid, kG32Threads, sm, h->stream>>>(Ap, h->lda, d_items32 + i0, h->d_shard_row0,
+              h->d_blk_col0, G, h->d_G_off, h->M, h->d_err, kWaitLimitCycles);
         e = cudaGetLastError();
         h->launches += 1;
       }
@@ -976,7 +998,7 @@ int build_factors(bicadmm_ctx* h, const std::function<int(int)>* load_shard = nu
   if (rc != BICADMM_OK) {
     cudaStreamSynchronize(h->stream);
     cudaFree(G);
-    if (d_items) cudaFree(d_items);
+    if (d_items32) cudaFree(d_items32);
     return rc;
   }
   // Blocked factorisation when an NB-column panel of the widest block fits in shared memory:
@@ -1056,7 +1078,7 @@ int build_factors(bicadmm_ctx* h, const std::function<int(int)>* load_shard = nu
   if (rc == BICADMM_OK && e2 != cudaSuccess) rc = fail(h, BICADMM_ERR_CUDA, std::string("factor sync: ") + cudaGetErrorString(e2));
   cudaFree(G);
   if (YT) cudaFree(YT);
-  if (d_items) cudaFree(d_items);
+  if (d_items32) cudaFree(d_items32);
   if (rc != BICADMM_OK) return rc;
   return check_device_error(h);
 }
@@ -1816,6 +1838,10 @@ int bicadmm_create(const bicadmm_params* params, void* stream, bicadmm_t* out) {
   if (rc != BICADMM_OK) { g_create_error = why; return rc; }
   bicadmm_ctx* h = new bicadmm_ctx();
   h->p = *params;
+  if (h->p.precision == BICADMM_PREC_TF32) {
+    h->tf32 = true;
+    h->p.precision = BICADMM_PREC_FP32;
+  }
   if (h->p.rho_b == 0.0) h->p.rho_b = 0.5 * h->p.rho_c;
   if (h->p.rho_l == 0.0) h->p.rho_l = h->p.rho_c;
   h->stream = static_cast<cudaStream_t>(stream);
@@ -1828,8 +1854,8 @@ int bicadmm_create(const bicadmm_params* params, void* stream, bicadmm_t* out) {
   }
   rc = build_geometry(h);
   if (rc == BICADMM_OK) rc = allocate(h);
-  // BF16 storage: the 2D tensor map of A serves the tensor-core Gram (and the softmax pass)
-  if (rc == BICADMM_OK && (h->use_tc || h->p.precision == BICADMM_PREC_BF16)) rc = make_tmap(h);
+  // the 2D tensor map of A serves the tensor-core softmax pass
+  if (rc == BICADMM_OK && h->use_tc) rc = make_tmap(h);
   if (rc == BICADMM_OK) rc = reset_state(h);
   if (rc != BICADMM_OK) {
     g_create_error = h->err;

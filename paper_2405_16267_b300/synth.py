@@ -360,3 +360,13 @@ def round_to_bf16(A: np.ndarray) -> np.ndarray:
     lsb = (u >> 16) & 1
     r = ((u + 0x7FFF + lsb) >> 16) << 16
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def round_to_tf32(A: np.ndarray) -> np.ndarray:
+    """TF32-rounded copy of A (10 mantissa bits; round to nearest, ties to even, from the
+    FP32 value) upcast back to FP64: the exact values a TF32-storage run sees."""
+    f = np.ascontiguousarray(A, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 13) & 1
+    r = ((u + 0xFFF + lsb) >> 13) << 13
+    return (r & 0xFFFFFFFF).astype(np.uint32).view(np.float32).astype(np.float64)

@@ -10,7 +10,7 @@ def run_gpu(P, iters, precision=bc.PREC_FP64, J=1, A=None, b=None, rho_c=None, *
     import torch
     A = P.A if A is None else A
     b = P.b if b is None else b
-    if precision in (bc.PREC_FP32, bc.PREC_BF16) and not isinstance(A, torch.Tensor):
+    if precision in (bc.PREC_FP32, bc.PREC_BF16, bc.PREC_TF32) and not isinstance(A, torch.Tensor):
         A = np.asarray(A, dtype=np.float32)
     stream = torch.cuda.current_stream()
     with bc.Solver(A, b, loss=P.loss, N=P.N, M=P.M, kappa=P.kappa, gamma=P.gamma,

@@ -71,13 +71,13 @@ def test_consensus_large_n_with_ties(case):
     w2[tie] = w1[tie]                   # the tie group stays tied in the second call
     dev = torch.device("cuda")
     z = torch.zeros(n, dtype=torch.float64, device=dev)
-    s = torch.tensor(s0, device=dev)
-    tvt = torch.tensor([0.0, v0, 0.0, 0.0], device=dev)
+    s = torch.tensor(s0, dtype=torch.float64, device=dev)
+    tvt = torch.tensor([0.0, v0, 0.0, 0.0], dtype=torch.float64, device=dev)
     v = v0
     s_prev = s0
     for call, w in enumerate((w1, w2)):
         wz, wt, wtau = ref.zt_step(w, s_prev, v, N, rho_c, rho_b)
-        bc.consensus_step_noalloc(torch.tensor(w, device=dev), z, s, tvt, kappa, N, rho_c, rho_b)
+        bc.consensus_step_noalloc(torch.tensor(w, dtype=torch.float64, device=dev), z, s, tvt, kappa, N, rho_c, rho_b)
         torch.cuda.synchronize()
         zg, sg, tv = z.cpu().numpy(), s.cpu().numpy(), tvt.cpu().numpy()
         assert tv[3] == 0.0, "device status"

@@ -1,6 +1,6 @@
 """info.objective: F(z) = sum_r l(a_r z; b_r) + ||z||^2 / (2 gamma) of problem (p:SML)
 (Sec. 2) at the GPU's consensus iterate z, computed on the device in FP64, against the
-oracle's objective evaluated on that same z with the stored (rounded) A.
+oracle's objective evaluated on that same z with the stored (rounded) A and b.
 
 The zero start (no nonzero feature), a dense z (the l1 constraint inactive) and a
 thresholded, sparse z (after many iterations) take different paths through the feature
@@ -30,6 +30,9 @@ def _check(P, precision, iters_list, K=1, **extra):
     import torch
     A = P.A if precision == bc.PREC_FP64 else np.asarray(P.A, dtype=np.float32)
     As = _stored(P.A, precision)
+    # b is stored in the arithmetic type too (FP32 unless FP64): targets are rounded,
+    # labels and class indices are exact
+    bs = P.b if precision == bc.PREC_FP64 else np.asarray(P.b, dtype=np.float32).astype(np.float64)
     seen_nnz = []
     with bc.Solver(A, P.b, loss=P.loss, N=P.N, M=P.M, kappa=P.kappa, gamma=P.gamma,
                    rho_c=P.rho, precision=precision, K=K, stream=torch.cuda.current_stream(),
@@ -39,7 +42,7 @@ def _check(P, precision, iters_list, K=1, **extra):
             info = s.step(it - done)
             done = it
             z = s.state()["z"]
-            want = ref.objective(P.loss, As, P.b, z, P.gamma, K=K)
+            want = ref.objective(P.loss, As, bs, z, P.gamma, K=K)
             nnz = int(np.count_nonzero(z))
             seen_nnz.append(nnz)
             assert abs(info.objective - want) <= TOL * max(abs(want), 1.0), \

@@ -1,6 +1,7 @@
 """The setup's block inverses (rho_l A_ij'A_ij + c0 I)^-1 of the x_ij solve (eq. p:GPU;x)
 against the oracle's factorisation of the same matrices, in every storage precision: FP64
-and FP32 Gram matrices on the CUDA cores, BF16 on the tensor cores (column windows that
+Gram matrices on the CUDA cores, FP32 (TF32 hi/lo pairs) and TF32 on the tensor cores in
+kind::tf32 (blocks of any width and column offset), BF16 on the tensor cores (column windows that
 start off the 64-column grid, blocks wider than one 256-column chunk, shards whose length
 is not a multiple of the 64-row stage, a shard shorter than one stage), and blocks wide
 enough for the narrower Cholesky panels and for the column-by-column fallback."""
@@ -27,11 +28,11 @@ CASES = [  # (m, n, N, M, K)
 # relative error per unit condition number of the block matrix: FP64 arithmetic; FP32
 # storage of P (and FP32 partial sums of the products: CUDA cores flush to FP64 every 256
 # rows, the tensor cores accumulate a shard in FP32)
-TOL = {bc.PREC_FP64: 1e-13, bc.PREC_FP32: 3e-6, bc.PREC_BF16: 3e-6}
+TOL = {bc.PREC_FP64: 1e-13, bc.PREC_FP32: 3e-6, bc.PREC_BF16: 3e-6, bc.PREC_TF32: 3e-6}
 
 
 @pytest.mark.parametrize("case", CASES)
-@pytest.mark.parametrize("precision", [bc.PREC_FP64, bc.PREC_FP32, bc.PREC_BF16])
+@pytest.mark.parametrize("precision", [bc.PREC_FP64, bc.PREC_FP32, bc.PREC_BF16, bc.PREC_TF32])
 def test_block_inverses_match_oracle(case, precision):
     m, n, N, M, K = case
     if K == 1:
@@ -43,6 +44,8 @@ def test_block_inverses_match_oracle(case, precision):
         A = A.astype(np.float32).astype(np.float64)
     elif precision == bc.PREC_BF16:
         A = synth.round_to_bf16(P.A)
+    elif precision == bc.PREC_TF32:
+        A = synth.round_to_tf32(P.A)
     o = ref.BiCADMM(A, P.b, P.loss, P.N, P.M, P.kappa, gamma=P.gamma, rho_c=P.rho, K=K)
     A_in = P.A if precision == bc.PREC_FP64 else P.A.astype(np.float32)
     with bc.Solver(A_in, P.b, loss=P.loss, N=P.N, M=P.M, kappa=P.kappa, gamma=P.gamma,
