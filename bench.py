@@ -615,10 +615,23 @@ def run_serve(args, rank, world):
         srv.run()
         res = [srv.result(i) for i in ids]
         st = srv.stats()
+        tim = [srv.timing(i) for i, r in zip(ids, res) if r["status"] == 0]
+        prof = srv.timing(-1)
     clk = clocks.stop()
     ok = [r for r in res if r["status"] == 0]
     lat = np.array([r["done"] - r["arrival"] for r in ok])
     wait = np.array([r["admitted"] - r["arrival"] for r in ok])
+
+    def pct(v):
+        v = np.asarray(v)
+        return {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99))}
+    # where a request's time goes: queued, its own setup, iterating in batched rounds (shared
+    # with the others), and retirement (objective, polish, copy-out)
+    breakdown = {"queue_s": pct([t["admitted"] - t["arrival"] for t in tim]),
+                 "setup_s": pct([t["setup_done"] - t["admitted"] for t in tim]),
+                 "rounds_s": pct([t["retiring"] - t["setup_done"] for t in tim]),
+                 "retire_s": pct([t["done"] - t["retiring"] for t in tim]),
+                 "rounds_per_request": pct([t["rounds"] for t in tim])}
     span = max(r["done"] for r in res) - min(r["arrival"] for r in res)
     return {
         "metric": "solves/s (serving, continuous batching)", "value": len(ok) / span,
@@ -636,6 +649,9 @@ def run_serve(args, rank, world):
         "queue_wait_s": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
         "completed": len(ok), "failed": len(res) - len(ok),
         "converged": int(sum(r["info"].converged for r in ok)),
+        "request_breakdown": breakdown,
+        "server_loop_s": {k: prof[k] for k in ("rebuild_s", "round_wait_s", "admit_s", "retire_s")},
+        "batch_rebuilds": int(prof["rebuilds"]),
         "server": st, "input_generation_s": t_gen, "clocks": clk,
         "gpu_launches": int(st["launches"]),
     }

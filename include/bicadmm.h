@@ -300,7 +300,12 @@ int bicadmm_estimate_bytes(const bicadmm_params* params, int64_t* device_bytes,
  *     reached max_iters is polished (when `polish`), copied to host and its memory freed.
  * Each request's iterates are those of solving it alone up to rounding (the batch only
  * regroups partial sums).  The caller keeps A and b of a request valid until it finishes.
- * All requests use the server's precision and inner_iters = 1.  Single host thread. */
+ * All requests use the server's precision and inner_iters = 1.
+ * Threads: bicadmm_server_run works on one host thread; bicadmm_server_submit, _set_open,
+ * _result, _timing, _stats and _clock may be called from other threads at the same time
+ * (requests that arrive while a run loops are admitted by it).  Create and destroy are not
+ * concurrent with anything else.  Errors of submit and result are returned as codes only
+ * (no last-error text, which belongs to the run thread). */
 typedef struct bicadmm_server_ctx* bicadmm_server_t;
 typedef struct {
   int64_t hbm_budget_bytes;  /* device bytes the active requests may hold              */
@@ -317,6 +322,18 @@ int bicadmm_server_submit(bicadmm_server_t s, const bicadmm_params* p, const voi
                           int32_t A_dtype, int64_t lda, int32_t A_on_device, const void* b,
                           int32_t b_dtype, int32_t b_on_device, double arrival, int64_t* id_out);
 int bicadmm_server_run(bicadmm_server_t s, double until, int64_t* completed_out);
+/* open != 0: bicadmm_server_run does not return when nothing is active or waiting; it waits
+ * for submissions (polling every 0.5 ms) until its `until` has passed or open is set to 0
+ * (from any thread).  open = 0 (the default): it returns once every submitted request has
+ * finished. */
+int bicadmm_server_set_open(bicadmm_server_t s, int32_t open);
+/* Time breakdown.  id >= 0 (a finished request; ERR_STATE before): out[7] = arrival,
+ * admission (its create + setup start), setup end, retirement start (objective, polish,
+ * copy-out), completion, all seconds on the server's clock, then its iterations and the
+ * batched rounds it took part in.  id = -1: out[7] = batch rebuilds (the active set
+ * changed), seconds rebuilding, seconds waiting for rounds on the device, seconds admitting
+ * (create + setup), seconds retiring, rounds, and the server's clock. */
+int bicadmm_server_timing(bicadmm_server_t s, int64_t id, double* out);
 /* Result of a finished request: x (n doubles; polished if the server polishes), support
  * (kappa indices), info, and times_out[3] = arrival, admission, completion.  Returns the
  * request's own status when it failed. */

@@ -106,6 +106,8 @@ SIGNATURES = [
                                              ctypes.c_int32, ctypes.c_double,
                                              ctypes.POINTER(ctypes.c_int64)]),
     ("bicadmm_server_run", ctypes.c_int, [_VP, ctypes.c_double, ctypes.POINTER(ctypes.c_int64)]),
+    ("bicadmm_server_set_open", ctypes.c_int, [_VP, ctypes.c_int32]),
+    ("bicadmm_server_timing", ctypes.c_int, [_VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]),
     ("bicadmm_server_result", ctypes.c_int, [_VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
                                              ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
                                              ctypes.POINTER(Info), ctypes.POINTER(ctypes.c_double)]),
@@ -412,8 +414,28 @@ class Server:
         code = lib().bicadmm_server_result(self.s, int(rid), x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                           n, sup.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                           ctypes.byref(inf), t)
-        self._keep.pop(rid, None)
+        if code != -4:  # finished (or failed): the server no longer reads its A and b
+            self._keep.pop(rid, None)
         return dict(status=code, x=x, support=sup, info=inf, arrival=t[0], admitted=t[1], done=t[2])
+
+    def set_open(self, flag=True):
+        """While open, run() keeps waiting for submissions (from other threads) until its
+        `until` has passed or the server is closed again."""
+        _scheck(lib().bicadmm_server_set_open(self.s, int(bool(flag))), self.s)
+
+    TIMING = ("arrival", "admitted", "setup_done", "retiring", "done", "iters", "rounds")
+    PROFILE = ("rebuilds", "rebuild_s", "round_wait_s", "admit_s", "retire_s", "rounds", "clock")
+
+    def timing(self, rid=-1):
+        """Per request (rid >= 0, finished): arrival, admission (setup start), setup end,
+        retirement start, completion (server clock, s), iterations and rounds.  rid = -1: the
+        server's batch rebuilds and seconds spent rebuilding, waiting for rounds, admitting
+        and retiring, its rounds and clock."""
+        out = (ctypes.c_double * 7)()
+        code = lib().bicadmm_server_timing(self.s, int(rid), out)
+        if code != 0:
+            raise BicadmmError(code, "request not finished" if code == -4 else "bad id")
+        return dict(zip(self.PROFILE if rid < 0 else self.TIMING, list(out)))
 
     def stats(self):
         c = (ctypes.c_int64 * 5)()

@@ -13,6 +13,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <memory>
+#include <mutex>
 #include <functional>
 #include <chrono>
 #include <cmath>
@@ -203,6 +206,9 @@ ConsensusArgs consensus_args(bicadmm_ctx* h, bool enabled) {
   a.rho_b = h->p.rho_b;
   a.err = h->d_err;
   a.enabled = enabled ? 1 : 0;
+  // the pass kernels launch with pass_smem bytes of dynamic shared memory, which their
+  // consensus CTA (it stages no panels) may fill with top-kappa candidates
+  a.cand_bytes = static_cast<int64_t>(h->pass_smem);
   return a;
 }
 
@@ -2358,30 +2364,46 @@ struct ServerReq {
   const void* b = nullptr;
   int32_t A_dtype = 0, b_dtype = 0, A_dev = 0, b_dev = 0;
   int64_t lda = 0;
-  double arrival = 0.0, admitted = -1.0, done = -1.0;
+  // arrival; admission (= setup start); setup end; retirement start (polish, copy-out);
+  // completion: seconds on the server's clock, -1 until reached
+  double arrival = 0.0, admitted = -1.0, setup_done = -1.0, retiring = -1.0, done = -1.0;
   bicadmm_t h = nullptr;
   int64_t bytes = 0;
-  int iters = 0;
+  int iters = 0, rounds = 0;
   int status = BICADMM_OK;
   std::vector<double> x;
   std::vector<int64_t> support;
   bicadmm_info info{};
 };
 
+// Request records live behind stable pointers: another host thread may submit (append a
+// record, under mu) while run() works on the records it holds.  Fields of a request are
+// written by the thread in run() only; its completion time is published under mu after
+// its results, and bicadmm_server_result reads them under mu once it sees it.
 struct bicadmm_server_ctx {
   bicadmm_server_params sp{};
   cudaStream_t round_stream = nullptr, setup_stream = nullptr;
-  std::vector<ServerReq> reqs;
-  std::deque<int64_t> waiting;   // FIFO of submitted, not yet admitted requests
-  std::vector<int64_t> active;
+  std::mutex mu;                                 // guards reqs (the vector), waiting, completed
+  std::vector<std::unique_ptr<ServerReq>> reqs;
+  std::deque<int64_t> waiting;   // submitted, not yet admitted, ordered by arrival
+  std::vector<int64_t> active;   // run() thread only
   bicadmm_batch_t batch = nullptr;
   bool dirty = true;
+  std::atomic<int> open{0};      // run() waits for submissions while set
   int64_t bytes_in_use = 0, peak_bytes = 0;
   int64_t rounds = 0, completed = 0, launches = 0;
+  // where the host loop's time goes (seconds): batch rebuilds and their count, waiting for
+  // rounds on the device, admissions (create + setup), retirements (polish + copy-out)
+  double rebuild_s = 0.0, round_wait_s = 0.0, admit_s = 0.0, retire_s = 0.0;
+  int64_t rebuilds = 0;
   std::chrono::steady_clock::time_point t0;
   std::string err;
   double now() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  ServerReq* req(int64_t id) {
+    std::lock_guard<std::mutex> g(mu);
+    return reqs[static_cast<size_t>(id)].get();
   }
 };
 
@@ -2400,29 +2422,39 @@ void server_drop_batch(bicadmm_server_ctx* s) {
   s->dirty = true;
 }
 
-// Admit arrived requests in FIFO order while the device-memory budget and slot count allow.
+// Publish a request's completion (after its results are written).
+void server_finish(bicadmm_server_ctx* s, ServerReq& r) {
+  std::lock_guard<std::mutex> g(s->mu);
+  r.done = s->now();
+  ++s->completed;
+}
+
+// Admit arrived requests in arrival order while the device-memory budget and slot count allow.
 int server_admit(bicadmm_server_ctx* s) {
   const double t = s->now();
-  while (!s->waiting.empty() && static_cast<int>(s->active.size()) < s->sp.max_active) {
-    ServerReq& r = s->reqs[s->waiting.front()];
-    if (r.arrival > t) break;
+  while (static_cast<int>(s->active.size()) < s->sp.max_active) {
+    int64_t id;
+    {
+      std::lock_guard<std::mutex> g(s->mu);
+      if (s->waiting.empty()) break;
+      id = s->waiting.front();
+      if (s->reqs[static_cast<size_t>(id)]->arrival > t) break;
+    }
+    ServerReq& r = *s->req(id);
     int64_t need = 0, extra = 0;
     int rc = bicadmm_estimate_bytes(&r.p, &need, &extra);
-    if (rc != BICADMM_OK) {  // an invalid request fails alone
+    if (rc == BICADMM_OK && need + extra > s->sp.hbm_budget_bytes) rc = BICADMM_ERR_OOM;
+    if (rc != BICADMM_OK) {  // an invalid or never-fitting request fails alone
       r.status = rc;
-      r.done = t;
-      s->waiting.pop_front();
-      ++s->completed;
-      continue;
-    }
-    if (need + extra > s->sp.hbm_budget_bytes) {
-      r.status = BICADMM_ERR_OOM;
-      r.done = t;
-      s->waiting.pop_front();
-      ++s->completed;
+      {
+        std::lock_guard<std::mutex> g(s->mu);
+        s->waiting.pop_front();
+      }
+      server_finish(s, r);
       continue;
     }
     if (s->bytes_in_use + need + extra > s->sp.hbm_budget_bytes) break;  // wait for memory
+    const double t_adm = s->now();
     bicadmm_t h = nullptr;
     rc = bicadmm_create(&r.p, s->setup_stream, &h);
     if (rc == BICADMM_OK) {
@@ -2435,19 +2467,23 @@ int server_admit(bicadmm_server_ctx* s) {
     } else {
       s->err = g_create_error;
     }
-    s->waiting.pop_front();
+    {
+      std::lock_guard<std::mutex> g(s->mu);
+      s->waiting.pop_front();
+    }
+    r.admitted = t_adm;
+    r.setup_done = s->now();
+    s->admit_s += r.setup_done - t_adm;
     if (rc != BICADMM_OK) {
       r.status = rc;
-      r.done = s->now();
-      ++s->completed;
+      server_finish(s, r);
       continue;
     }
     r.h = h;
     r.bytes = need;
-    r.admitted = t;
     s->bytes_in_use += need;
     s->peak_bytes = std::max(s->peak_bytes, s->bytes_in_use + extra);
-    s->active.push_back(static_cast<int64_t>(&r - s->reqs.data()));
+    s->active.push_back(id);
     s->dirty = true;
   }
   return BICADMM_OK;
@@ -2457,9 +2493,9 @@ int server_admit(bicadmm_server_ctx* s) {
 int server_retire(bicadmm_server_ctx* s) {
   std::vector<int64_t> still, finished;
   for (int64_t id : s->active) {
-    ServerReq& r = s->reqs[id];
+    ServerReq& r = *s->req(id);
     bicadmm_info inf;
-    int rc = fill_info(r.h, &inf);
+    int rc = fill_info(r.h, &inf, false);
     const double mx = std::max(std::max(inf.p_rel, inf.d_rel), std::max(inf.b_rel, inf.i_rel));
     const bool conv = r.iters > 1 && mx <= r.p.tol_rel;
     if (rc != BICADMM_OK || conv || r.iters >= r.p.max_iters) {
@@ -2472,9 +2508,17 @@ int server_retire(bicadmm_server_ctx* s) {
     }
   }
   if (finished.empty()) return BICADMM_OK;
+  const double t_ret = s->now();
   server_drop_batch(s);  // the batch references the handles
   for (int64_t id : finished) {
-    ServerReq& r = s->reqs[id];
+    ServerReq& r = *s->req(id);
+    r.retiring = s->now();
+    if (r.status == BICADMM_OK) {
+      // the objective at the final iterate (FP64, on the device), then the model
+      bicadmm_info inf;
+      r.status = fill_info(r.h, &inf, true);
+      r.info.objective = inf.objective;
+    }
     if (r.status == BICADMM_OK) {
       r.x.assign(r.p.n, 0.0);
       r.support.assign(r.p.kappa, 0);
@@ -2484,9 +2528,9 @@ int server_retire(bicadmm_server_ctx* s) {
     bicadmm_destroy(r.h);
     r.h = nullptr;
     s->bytes_in_use -= r.bytes;
-    r.done = s->now();
-    ++s->completed;
+    server_finish(s, r);
   }
+  s->retire_s += s->now() - t_ret;
   s->active = still;
   return BICADMM_OK;
 }
@@ -2521,27 +2565,33 @@ int bicadmm_server_submit(bicadmm_server_t s, const bicadmm_params* p, const voi
                           int32_t A_dtype, int64_t lda, int32_t A_on_device, const void* b,
                           int32_t b_dtype, int32_t b_on_device, double arrival, int64_t* id_out) {
   if (!s) return BICADMM_ERR_ARG;
-  if (!p || !A || !b || !id_out) return sfail(s, BICADMM_ERR_ARG, "p, A, b and id_out are required");
-  if (p->precision != s->sp.precision) return sfail(s, BICADMM_ERR_ARG, "request precision differs from the server's");
-  if (p->inner_iters != 1) return sfail(s, BICADMM_ERR_UNSUPPORTED, "served requests use inner_iters = 1");
-  if (p->K != 1) return sfail(s, BICADMM_ERR_UNSUPPORTED, "served requests take K = 1");
-  ServerReq r;
-  r.p = *p;
-  r.A = A;
-  r.b = b;
-  r.A_dtype = A_dtype;
-  r.b_dtype = b_dtype;
-  r.A_dev = A_on_device;
-  r.b_dev = b_on_device;
-  r.lda = lda;
-  r.arrival = arrival;
+  if (!p || !A || !b || !id_out) return BICADMM_ERR_ARG;
+  if (p->precision != s->sp.precision) return BICADMM_ERR_ARG;
+  if (p->inner_iters != 1 || p->K != 1) return BICADMM_ERR_UNSUPPORTED;
+  std::unique_ptr<ServerReq> r(new ServerReq());
+  r->p = *p;
+  r->A = A;
+  r->b = b;
+  r->A_dtype = A_dtype;
+  r->b_dtype = b_dtype;
+  r->A_dev = A_on_device;
+  r->b_dev = b_on_device;
+  r->lda = lda;
+  r->arrival = arrival;
+  std::lock_guard<std::mutex> g(s->mu);
   s->reqs.push_back(std::move(r));
   const int64_t id = static_cast<int64_t>(s->reqs.size()) - 1;
   // keep the waiting list ordered by arrival (stable for equal times)
   auto it = s->waiting.end();
-  while (it != s->waiting.begin() && s->reqs[*(it - 1)].arrival > arrival) --it;
+  while (it != s->waiting.begin() && s->reqs[static_cast<size_t>(*(it - 1))]->arrival > arrival) --it;
   s->waiting.insert(it, id);
   *id_out = id;
+  return BICADMM_OK;
+}
+
+int bicadmm_server_set_open(bicadmm_server_t s, int32_t open) {
+  if (!s) return BICADMM_ERR_ARG;
+  s->open.store(open ? 1 : 0);
   return BICADMM_OK;
 }
 
@@ -2551,49 +2601,78 @@ int bicadmm_server_run(bicadmm_server_t s, double until, int64_t* completed_out)
   for (;;) {
     if ((rc = server_admit(s)) != BICADMM_OK) return rc;
     if (s->active.empty()) {
-      if (s->waiting.empty()) break;
-      const double next = s->reqs[s->waiting.front()].arrival;
+      double next = -1.0;
+      {
+        std::lock_guard<std::mutex> g(s->mu);
+        if (!s->waiting.empty()) next = s->reqs[static_cast<size_t>(s->waiting.front())]->arrival;
+      }
+      if (next < 0.0) {  // nothing submitted is waiting
+        if (!s->open.load() || s->now() > until) break;
+        std::this_thread::sleep_for(std::chrono::duration<double>(0.0005));
+        continue;
+      }
       if (next > until) break;
       const double wait = next - s->now();
       if (wait > 0) std::this_thread::sleep_for(std::chrono::duration<double>(std::min(wait, 0.001)));
       continue;
     }
     if (s->dirty || !s->batch) {
+      const double t_rb = s->now();
       server_drop_batch(s);
       std::vector<bicadmm_t> hs;
-      for (int64_t id : s->active) hs.push_back(s->reqs[id].h);
+      for (int64_t id : s->active) hs.push_back(s->req(id)->h);
       rc = bicadmm_batch_create(hs.data(), static_cast<int32_t>(hs.size()), s->round_stream,
                                 s->sp.use_graph ? BICADMM_BATCH_GRAPH : 0, &s->batch);
       if (rc != BICADMM_OK) return sfail(s, rc, std::string("batch: ") + g_create_error);
       s->dirty = false;
+      s->rebuild_s += s->now() - t_rb;
+      ++s->rebuilds;
     }
     // a round: as many iterations as the closest request to its cap still needs (<= the
     // round length), so every request stops exactly at its iteration cap
     int k = s->sp.iters_per_round;
-    for (int64_t id : s->active) k = std::min(k, s->reqs[id].p.max_iters - s->reqs[id].iters);
+    for (int64_t id : s->active) {
+      const ServerReq& r = *s->req(id);
+      k = std::min(k, r.p.max_iters - r.iters);
+    }
     k = std::max(k, 1);
     int64_t launches = 0;
     if ((rc = bicadmm_batch_step(s->batch, k, &launches)) != BICADMM_OK) return sfail(s, rc, s->batch->err);
     s->launches += static_cast<int64_t>(s->batch->launches_per_iter) * k;
-    for (int64_t id : s->active) s->reqs[id].iters += k;
+    for (int64_t id : s->active) {
+      ServerReq& r = *s->req(id);
+      r.iters += k;
+      ++r.rounds;
+    }
     ++s->rounds;
     // new arrivals are set up (setup stream) while the round runs on the device
     if ((rc = server_admit(s)) != BICADMM_OK) return rc;
+    const double t_w = s->now();
     if (cudaStreamSynchronize(s->round_stream) != cudaSuccess) return sfail(s, BICADMM_ERR_CUDA, "round failed");
+    s->round_wait_s += s->now() - t_w;
     if ((rc = server_retire(s)) != BICADMM_OK) return rc;
-    if (s->active.empty() && s->waiting.empty()) break;
+    bool idle;
+    {
+      std::lock_guard<std::mutex> g(s->mu);
+      idle = s->active.empty() && s->waiting.empty();
+    }
+    if (idle && (!s->open.load() || s->now() > until)) break;
     if (s->now() > until && s->active.empty()) break;
   }
-  if (completed_out) *completed_out = s->completed;
+  if (completed_out) {
+    std::lock_guard<std::mutex> g(s->mu);
+    *completed_out = s->completed;
+  }
   return BICADMM_OK;
 }
 
 int bicadmm_server_result(bicadmm_server_t s, int64_t id, double* x_host, int64_t len,
                           int64_t* support_out, bicadmm_info* info, double* times_out) {
   if (!s) return BICADMM_ERR_ARG;
-  if (id < 0 || id >= static_cast<int64_t>(s->reqs.size())) return sfail(s, BICADMM_ERR_ARG, "unknown request id");
-  const ServerReq& r = s->reqs[id];
-  if (r.done < 0) return sfail(s, BICADMM_ERR_STATE, "request not finished");
+  std::lock_guard<std::mutex> g(s->mu);
+  if (id < 0 || id >= static_cast<int64_t>(s->reqs.size())) return BICADMM_ERR_ARG;
+  const ServerReq& r = *s->reqs[static_cast<size_t>(id)];
+  if (r.done < 0) return BICADMM_ERR_STATE;
   if (times_out) {
     times_out[0] = r.arrival;
     times_out[1] = r.admitted;
@@ -2602,16 +2681,43 @@ int bicadmm_server_result(bicadmm_server_t s, int64_t id, double* x_host, int64_
   if (info) *info = r.info;
   if (r.status != BICADMM_OK) return r.status;
   if (x_host) {
-    if (len != r.p.n) return sfail(s, BICADMM_ERR_ARG, "x_host must hold n doubles");
+    if (len != r.p.n) return BICADMM_ERR_ARG;
     std::copy(r.x.begin(), r.x.end(), x_host);
   }
   if (support_out) std::copy(r.support.begin(), r.support.end(), support_out);
   return BICADMM_OK;
 }
 
+int bicadmm_server_timing(bicadmm_server_t s, int64_t id, double* out) {
+  if (!s || !out) return BICADMM_ERR_ARG;
+  std::lock_guard<std::mutex> g(s->mu);
+  if (id < 0) {
+    out[0] = static_cast<double>(s->rebuilds);
+    out[1] = s->rebuild_s;
+    out[2] = s->round_wait_s;
+    out[3] = s->admit_s;
+    out[4] = s->retire_s;
+    out[5] = static_cast<double>(s->rounds);
+    out[6] = s->now();
+    return BICADMM_OK;
+  }
+  if (id >= static_cast<int64_t>(s->reqs.size())) return BICADMM_ERR_ARG;
+  const ServerReq& r = *s->reqs[static_cast<size_t>(id)];
+  if (r.done < 0) return BICADMM_ERR_STATE;
+  out[0] = r.arrival;
+  out[1] = r.admitted;
+  out[2] = r.setup_done;
+  out[3] = r.retiring;
+  out[4] = r.done;
+  out[5] = static_cast<double>(r.iters);
+  out[6] = static_cast<double>(r.rounds);
+  return BICADMM_OK;
+}
+
 int bicadmm_server_stats(bicadmm_server_t s, int64_t* counters_out) {
   if (!s) return BICADMM_ERR_ARG;
   if (counters_out) {
+    std::lock_guard<std::mutex> g(s->mu);
     counters_out[0] = static_cast<int64_t>(s->reqs.size());
     counters_out[1] = s->completed;
     counters_out[2] = s->rounds;
@@ -2624,8 +2730,8 @@ int bicadmm_server_stats(bicadmm_server_t s, int64_t* counters_out) {
 int bicadmm_server_destroy(bicadmm_server_t s) {
   if (!s) return BICADMM_OK;
   server_drop_batch(s);
-  for (ServerReq& r : s->reqs)
-    if (r.h) bicadmm_destroy(r.h);
+  for (auto& r : s->reqs)
+    if (r->h) bicadmm_destroy(r->h);
   cudaStreamDestroy(s->round_stream);
   cudaStreamDestroy(s->setup_stream);
   delete s;

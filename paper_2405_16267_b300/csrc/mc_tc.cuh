@@ -267,14 +267,14 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
                 float* __restrict__ slots, double* __restrict__ cta_stats, PassGeometry geo,
                 float Mf, float rho_l, int newton_iters, int* __restrict__ err,
                 long long wait_limit, ConsensusArgs cons) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
   if (cons.enabled && blockIdx.x == gridDim.x - 1) {
-    consensus_block<kTcThreads, kConsMW>(cons);
+    consensus_block<kTcThreads, kConsMW>(cons, smem_raw);  // its dynamic smem holds the top-kappa candidates
     return;
   }
   constexpr int S = kTcStages;
   constexpr uint32_t IDESC_FWD = idesc_bf16(64, 32, false, false);
   constexpr uint32_t IDESC_BWD = idesc_bf16(128, 16, true, false);
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   unsigned char* ring = base;

@@ -195,14 +195,14 @@ k_fused_pass_k(const TA* __restrict__ A, int64_t lda, const TM* __restrict__ xlo
   static_assert(R <= NT / 16, "one half-warp per panel row in the epilogue");
   constexpr int C = ClassPad<KC>::C;
   constexpr int LOGC = C == 4 ? 2 : (C == 8 ? 3 : 4);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   if (cons.enabled && blockIdx.x == gridDim.x - 1) {
-    consensus_block<NT, kConsMW>(cons);
+    consensus_block<NT, kConsMW>(cons, smem_raw);  // its dynamic smem holds the top-kappa candidates
     return;
   }
   using V = typename Vec16<TA>::type;
   constexpr int VE = Vec16<TA>::n;
   constexpr int NW = NT / 32;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
 
   const int64_t nvec = lda / VE;
   const size_t stage_elems = static_cast<size_t>(R) * lda;

@@ -117,24 +117,52 @@ k_xupd(const TP* __restrict__ P, const int64_t* __restrict__ P_off,
 // unsigned integers), then rank the entries equal to the threshold by index with a
 // block-wide scan.  Each thread owns a contiguous chunk of at most 32*MW indices and gets
 // its selection as a bit mask.  key[] is global scratch of n entries.
+// With ccap > 0, ckey is shared memory for ccap keys: the nonzero keys are gathered there
+// (in any order: the digit counts do not depend on it) and, when they fit, the radix passes
+// count only them.  A zero key is selected only when fewer than kappa keys are nonzero, and
+// then it is the threshold itself (the first kappa - nnz zeros by index); z after the l1
+// projection is mostly zero, so the passes touch a small fraction of the entries.
 template <int GT, int MW>
 __device__ void block_topk_select(const double* __restrict__ z, uint64_t* __restrict__ key,
                                   int64_t n, int64_t kappa, uint32_t (&sel)[MW],
-                                  int64_t& chunk_begin, int& chunk_len) {
+                                  int64_t& chunk_begin, int& chunk_len,
+                                  uint64_t* ckey = nullptr, int64_t ccap = 0) {
   __shared__ unsigned int hist[256];
   __shared__ long long sh[2];
   __shared__ unsigned int wsum[32];
+  __shared__ unsigned int ncand_s;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int64_t r = tid; r < n; r += GT) key[r] = __double_as_longlong(fabs(z[r]));
+  if (tid == 0) ncand_s = 0u;
   __syncthreads();
+  for (int64_t r = tid; r < n; r += GT) {
+    const uint64_t k = __double_as_longlong(fabs(z[r]));
+    key[r] = k;
+    if (ccap > 0 && k != 0) {
+      const unsigned int pos = atomicAdd(&ncand_s, 1u);
+      if (pos < ccap) ckey[pos] = k;
+    }
+  }
+  __syncthreads();
+  const int64_t ncand = ncand_s;
+  const bool compact = ccap > 0 && ncand <= ccap;
   uint64_t prefix = 0, mask = 0;
   int64_t remaining = kappa;
-  for (int shift = 56; shift >= 0; shift -= 8) {
+  // fewer nonzero keys than kappa: every one of them is taken, and the threshold is 0
+  const bool all_nonzero = compact && ncand < kappa;
+  if (all_nonzero) remaining = kappa - ncand;
+  for (int shift = 56; shift >= 0 && !all_nonzero; shift -= 8) {
     for (int b = tid; b < 256; b += GT) hist[b] = 0;
     __syncthreads();
-    for (int64_t r = tid; r < n; r += GT) {
-      const uint64_t k = key[r];
-      if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+    if (compact) {
+      for (int64_t r = tid; r < ncand; r += GT) {
+        const uint64_t k = ckey[r];
+        if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+      }
+    } else {
+      for (int64_t r = tid; r < n; r += GT) {
+        const uint64_t k = key[r];
+        if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+      }
     }
     __syncthreads();
     if (warp == 0) {
@@ -238,10 +266,12 @@ struct ConsensusArgs {
   int* err;
   int enabled;       // used by the fused pass: 1 = its last CTA runs this step
   int prepared;      // 1: w, tau_r, c_arr, e_arr were formed by k_consensus_prep
+  int64_t cand_bytes;  // dynamic shared memory the running CTA may use for top-kappa
+                       // candidates (0: none; the select then reads every key each pass)
 };
 
 template <int GT, int MW>
-__device__ void consensus_block(const ConsensusArgs& a) {
+__device__ void consensus_block(const ConsensusArgs& a, unsigned char* dyn_smem = nullptr) {
   __shared__ double red[32 * 4];
   const int tid = threadIdx.x;
   const int64_t n = a.n;
@@ -319,22 +349,34 @@ __device__ void consensus_block(const ConsensusArgs& a) {
 
   // z = S_tau(w + tau s) (z = w when the constraint is inactive); norms for t and d_r.
   double a4[4] = {0.0, 0.0, 0.0, 0.0};  // ||z||_1, s'w, ||z - z_prev||^2, ||z||^2
+  // FP64 instructions are the scarce resource of this single CTA (each occupies the SM's
+  // FP64 pipe for many cycles), and after the projection most entries stay zero: an entry
+  // with s_r = 0 and |w_r| <= tau is zero without arithmetic (an integer compare of bit
+  // patterns), and entries zero before and after add exact zeros to every sum (skipped, so
+  // the sums are those of the full loop).
+  const long long taub = __double_as_longlong(tau);
+  const bool tpos = tau > 0.0;
   for (int64_t r = tid; r < n; r += GT) {
     const double wr = a.w[r], sr = a.s[r];
-    double zn;
-    if (tau > 0.0) {
-      const double y = wr + tau * sr;
-      const double mg = fabs(y) - tau;
-      zn = mg > 0.0 ? dsign(y) * mg : 0.0;
+    const double zo = a.z[r];
+    const bool s_zero = (__double_as_longlong(sr) << 1) == 0;
+    double zn = 0.0;
+    if (tpos) {
+      if (!(s_zero && (__double_as_longlong(wr) & 0x7FFFFFFFFFFFFFFFll) <= taub)) {
+        const double y = wr + tau * sr;
+        const double mg = fabs(y) - tau;
+        zn = mg > 0.0 ? dsign(y) * mg : 0.0;
+      }
     } else {
       zn = wr;
+      if (!s_zero) a4[1] += sr * wr;
     }
-    const double zo = a.z[r];
-    a4[0] += fabs(zn);
-    a4[1] += sr * wr;
-    a4[2] += (zn - zo) * (zn - zo);
-    a4[3] += zn * zn;
-    a.z[r] = zn;
+    if (((__double_as_longlong(zn) | __double_as_longlong(zo)) << 1) != 0) {
+      a4[0] += fabs(zn);
+      a4[2] += (zn - zo) * (zn - zo);
+      a4[3] += zn * zn;
+      a.z[r] = zn;
+    }
   }
   block_sum<4>(a4, red);
   const double t = tau > 0.0 ? a4[0] : a4[1] + v;
@@ -343,7 +385,9 @@ __device__ void consensus_block(const ConsensusArgs& a) {
   int64_t cb;
   int cl;
   uint32_t sel[MW];
-  block_topk_select<GT, MW>(a.z, a.key, n, a.kappa, sel, cb, cl);
+  block_topk_select<GT, MW>(a.z, a.key, n, a.kappa, sel, cb, cl,
+                            reinterpret_cast<uint64_t*>(dyn_smem),
+                            dyn_smem ? a.cand_bytes / static_cast<int64_t>(sizeof(uint64_t)) : 0);
   double a1b[1] = {0.0};
   for (int q = 0; q < cl; ++q)
     if (sel[q >> 5] >> (q & 31) & 1u) a1b[0] += fabs(a.z[cb + q]);
@@ -356,10 +400,14 @@ __device__ void consensus_block(const ConsensusArgs& a) {
   }
   double a1c[1] = {0.0};
   for (int q = 0; q < cl; ++q) {
-    const double zr = a.z[cb + q];
-    const double sn = (sel[q >> 5] >> (q & 31) & 1u) ? scale * dsign(zr) : 0.0;
-    a.s[cb + q] = sn;
-    a1c[0] += zr * sn;
+    if (sel[q >> 5] >> (q & 31) & 1u) {
+      const double zr = a.z[cb + q];
+      const double sn = scale * dsign(zr);
+      a.s[cb + q] = sn;
+      a1c[0] += zr * sn;
+    } else {
+      a.s[cb + q] = 0.0;  // an unselected entry adds an exact zero to z's
+    }
   }
   block_sum<1>(a1c, red);
   const double g = a1c[0] - t;

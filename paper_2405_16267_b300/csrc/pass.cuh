@@ -139,14 +139,14 @@ k_fused_pass(const TA* __restrict__ A, int64_t lda, const TM* __restrict__ xlo_i
   const XT* xlo = reinterpret_cast<const XT*>(xlo_in);
   // With cons.enabled the last CTA runs the global (z, t, s, v) step of this outer
   // iteration, which needs only x and u, concurrently with the A stream of the others.
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   if (cons.enabled && blockIdx.x == gridDim.x - 1) {
-    consensus_block<NT, kConsMW>(cons);
+    consensus_block<NT, kConsMW>(cons, smem_raw);  // its dynamic smem holds the top-kappa candidates
     return;
   }
   using V = typename Vec16<TA>::type;
   constexpr int VE = Vec16<TA>::n;
   constexpr int NW = NT / 32;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
 
   const int64_t nvec = lda / VE;
   const size_t stage_elems = static_cast<size_t>(R) * lda;

@@ -98,3 +98,45 @@ def test_tolerance_stop_in_server():
         r = srv.result(rid)
     assert r["status"] == 0 and r["info"].converged == 1 and r["info"].iters < 2000
     assert set(r["support"].tolist()) == set(np.flatnonzero(P.x_star).tolist())
+
+
+def test_submissions_from_another_thread_while_running():
+    """Requests submitted by another host thread while run() loops are admitted into the
+    running batch; each result equals the same request solved alone; the per-request time
+    breakdown is ordered and the server reports its rebuilds and rounds."""
+    import threading
+    import time
+    reqs = _requests(seed=7)[:5]
+    kw = lambda P, iters: dict(loss=P.loss, precision=bc.PREC_FP64, N_shards=P.N, M_blocks=P.M,
+                               kappa=P.kappa, gamma=P.gamma, rho_c=P.rho, max_iters=iters,
+                               tol_rel=0.0)
+    with bc.Server(hbm_budget_bytes=8 << 30, max_active=16, iters_per_round=5,
+                   precision=bc.PREC_FP64, use_graph=True) as srv:
+        srv.set_open(True)
+        P0, it0 = reqs[0]
+        ids = [srv.submit(P0.A, P0.b, arrival=srv.clock(), **kw(P0, it0))]
+        done = []
+        runner = threading.Thread(target=lambda: done.append(srv.run(until=srv.clock() + 120)))
+        runner.start()
+        for P, iters in reqs[1:]:
+            time.sleep(0.01)
+            ids.append(srv.submit(P.A, P.b, arrival=srv.clock(), **kw(P, iters)))
+        deadline = time.time() + 120
+        while time.time() < deadline and any(srv.result(i)["status"] == -4 for i in ids):
+            time.sleep(0.005)
+        srv.set_open(False)
+        runner.join(timeout=120)
+        assert not runner.is_alive() and done == [len(ids)]
+        res = [srv.result(i) for i in ids]
+        times = [srv.timing(i) for i in ids]
+        prof = srv.timing(-1)
+    for (P, iters), r, t in zip(reqs, res, times):
+        assert r["status"] == 0 and r["info"].iters == iters
+        x_alone, supp_alone = _alone(P, iters, bc.PREC_FP64)
+        assert list(r["support"]) == list(supp_alone)
+        assert rel_err(r["x"], x_alone) <= 1e-9
+        assert t["arrival"] <= t["admitted"] <= t["setup_done"] <= t["retiring"] <= t["done"]
+        assert t["iters"] == iters and t["rounds"] >= 1
+    # a request submitted while the loop ran shared it with an earlier one
+    assert any(b["admitted"] > a["admitted"] and b["admitted"] < a["done"] for a in times for b in times)
+    assert prof["rebuilds"] >= 1 and prof["rounds"] >= 2 and prof["admit_s"] > 0
