@@ -165,14 +165,14 @@ class ClockSampler:
 # DRAM traffic of one pass launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of a 20000-row launch of the same kernel, scaled by rows to the
 # 200000-row launch.  Reported only while the kernel sources are the captured ones.
-PASS_TRAFFIC = {"sources_sha256": "ced2df2fe87b27133f65bd54317ccedf76e2cb66c4548e0f13994549b7446295", "bytes_per_launch": 4.0626e9,
+PASS_TRAFFIC = {"sources_sha256": "d76dc9e818585cae45568e9de75a0b020bcfe8be61b41278d27a17831f0720ee", "bytes_per_launch": 4.0509e+09,
                 "capture": "profiles/k_fused_pass_sparse_logistic_200000x5000_fp32.md"}
 PASS_SOURCES = ["paper_2405_16267_b300/csrc/pass.cuh", "paper_2405_16267_b300/csrc/nspace.cuh",
                 "paper_2405_16267_b300/csrc/common.cuh"]
 
 
 # The same for the tensor-core softmax pass (60000-row capture scaled to 500000 rows).
-TC_TRAFFIC = {"sources_sha256": "9b0526507586922457d9ddccce1ff8f7a59db02f3453bf448c4e7e49c91bf91f", "bytes_per_launch": 2.4625e9,
+TC_TRAFFIC = {"sources_sha256": "2ae5a3bcb40b637ec22f7539fb1b7212a3cf8d98d73e2bf393b9e029742ec9da", "bytes_per_launch": 2.4517e+09,
               "capture": "profiles/k_fused_pass_tc_sparse_softmax_500000x2000x10_bf16.md"}
 TC_SOURCES = ["paper_2405_16267_b300/csrc/mc_tc.cuh", "paper_2405_16267_b300/csrc/nspace.cuh",
               "paper_2405_16267_b300/csrc/common.cuh", "paper_2405_16267_b300/csrc/pass.cuh"]

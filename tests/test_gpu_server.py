@@ -107,6 +107,7 @@ def test_submissions_from_another_thread_while_running():
     import threading
     import time
     reqs = _requests(seed=7)[:5]
+    reqs[0] = (reqs[0][0], 1000)  # long enough to still be running when the others arrive
     kw = lambda P, iters: dict(loss=P.loss, precision=bc.PREC_FP64, N_shards=P.N, M_blocks=P.M,
                                kappa=P.kappa, gamma=P.gamma, rho_c=P.rho, max_iters=iters,
                                tol_rel=0.0)
@@ -119,7 +120,7 @@ def test_submissions_from_another_thread_while_running():
         runner = threading.Thread(target=lambda: done.append(srv.run(until=srv.clock() + 120)))
         runner.start()
         for P, iters in reqs[1:]:
-            time.sleep(0.01)
+            time.sleep(0.002)
             ids.append(srv.submit(P.A, P.b, arrival=srv.clock(), **kw(P, iters)))
         deadline = time.time() + 120
         while time.time() < deadline and any(srv.result(i)["status"] == -4 for i in ids):
