@@ -348,7 +348,8 @@ const char* bicadmm_server_last_error(bicadmm_server_t s);
 int bicadmm_destroy(bicadmm_t h);
 
 /* Text of the last error on this handle ("" if none); valid until the next call on h.
- * With h == NULL returns the last error of a failed bicadmm_create(). */
+ * With h == NULL returns the last error of a failed bicadmm_create() on the calling host
+ * thread. */
 const char* bicadmm_last_error(bicadmm_t h);
 
 #ifdef __cplusplus

@@ -58,7 +58,8 @@ constexpr int kMaxPolishKappa = 1024;
 
 int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
-std::string g_create_error;
+// Text of the last failed create (or batch / server create) on this host thread.
+thread_local std::string g_create_error;
 
 }  // namespace
 
