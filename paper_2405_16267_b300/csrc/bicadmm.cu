@@ -939,6 +939,69 @@ int build_factors(bicadmm_ctx* h, const std::function<int(int)>* load_shard = nu
 
   int rc = BICADMM_OK;
   Gram32Item* d_items32 = nullptr;
+
+  // Blocked factorisation when an NB-column panel of the widest block fits in shared memory:
+  // Cholesky, Y = L^-1 by columns, P = Y'Y by tiles (n^3/2 FMAs per block); otherwise the
+  // column-by-column kernels (Cholesky, then both triangular solves per column of P).
+  int nb_panel = 0;
+  for (int cand : {32, 16, 8})
+    if (static_cast<size_t>(cand) * (h->max_nj + 1) * sizeof(double) <= (200u << 10)) { nb_panel = cand; break; }
+  double* YT = nullptr;
+  if (nb_panel > 0) {
+    e = cudaMalloc(&YT, std::max<int64_t>(h->G_total, 1) * sizeof(double));
+    if (e != cudaSuccess) { cudaGetLastError(); YT = nullptr; nb_panel = 0; e = cudaSuccess; }
+  }
+  const size_t chol_sm = static_cast<size_t>(nb_panel) * (h->max_nj + 1) * sizeof(double);
+  const int inv_warps = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(8, (200 << 10) / (8 * h->max_nj))));
+  const size_t inv_sm = static_cast<size_t>(inv_warps) * h->max_nj * sizeof(double);
+  if (nb_panel > 0) {
+    if (nb_panel == 32) e = cudaFuncSetAttribute(k_chol_blk<kCholThreads, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(chol_sm));
+    else if (nb_panel == 16) e = cudaFuncSetAttribute(k_chol_blk<kCholThreads, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(chol_sm));
+    else e = cudaFuncSetAttribute(k_chol_blk<kCholThreads, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(chol_sm));
+    if (e == cudaSuccess && inv_sm > 48 * 1024)
+      e = cudaFuncSetAttribute(k_inv_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(inv_sm));
+  }
+  // The blocked factorisation of shards [s0, s0 + ns) on stream st: every kernel finds its
+  // block through G_off / P_off, so the shard range is an offset of those tables.
+  auto factor_shards = [&](int s0, int ns, cudaStream_t st) -> cudaError_t {
+    const int64_t* goff = h->d_G_off + static_cast<int64_t>(s0) * h->M;
+    const int64_t* poff = h->d_P_off + static_cast<int64_t>(s0) * h->M;
+    const unsigned nb = static_cast<unsigned>(ns * h->M);
+    if (nb_panel == 32) k_chol_blk<kCholThreads, 32><<<nb, kCholThreads, chol_sm, st>>>(G, goff, h->d_blk_col0, h->M, h->p.rho_l, h->c0, h->d_err);
+    else if (nb_panel == 16) k_chol_blk<kCholThreads, 16><<<nb, kCholThreads, chol_sm, st>>>(G, goff, h->d_blk_col0, h->M, h->p.rho_l, h->c0, h->d_err);
+    else k_chol_blk<kCholThreads, 8><<<nb, kCholThreads, chol_sm, st>>>(G, goff, h->d_blk_col0, h->M, h->p.rho_l, h->c0, h->d_err);
+    cudaError_t ee = cudaGetLastError();
+    if (ee != cudaSuccess) return ee;
+    k_inv_fwd<<<dim3(nb, (h->max_nj + inv_warps - 1) / inv_warps), 32 * inv_warps, inv_sm, st>>>(G, goff, h->d_blk_col0, h->M, YT);
+    if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
+    const int T = (h->max_nj + 63) / 64;
+    k_yty<TM><<<dim3(T * (T + 1) / 2, h->M, ns), 256, 0, st>>>(YT, goff, h->d_blk_col0, h->d_blk_ldp, h->M,
+                                                                 static_cast<TM*>(h->Pm), poff);
+    h->launches += 3;
+    return cudaGetLastError();
+  };
+  // With the host pipeline (shards arriving one by one), each shard is factorised as soon as
+  // its Gram matrices are formed, on its own side stream (up to 16, then round robin), so the
+  // FP64 factorisation (a block's Cholesky is one CTA at one SM's FP64 rate, about 17 ms for
+  // 625 columns) overlaps the copies of later shards and only the last shard's follows them.
+  constexpr int kFactorStreams = 16;
+  const bool per_shard = load_shard != nullptr && nb_panel > 0 && h->N > 1;
+  cudaStream_t fst[kFactorStreams] = {};
+  std::vector<cudaEvent_t> fev;
+  const int nfs = per_shard ? std::min(kFactorStreams, h->N) : 0;
+  for (int q = 0; q < nfs && e == cudaSuccess; ++q) e = cudaStreamCreateWithFlags(&fst[q], cudaStreamNonBlocking);
+  auto after_gram = [&](int i) -> cudaError_t {
+    if (!per_shard) return cudaSuccess;
+    cudaEvent_t ev;
+    cudaError_t ee = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (ee != cudaSuccess) return ee;
+    fev.push_back(ev);
+    if ((ee = cudaEventRecord(ev, h->stream)) != cudaSuccess) return ee;
+    cudaStream_t st = fst[i % nfs];
+    if ((ee = cudaStreamWaitEvent(st, ev, 0)) != cudaSuccess) return ee;
+    return factor_shards(i, 1, st);
+  };
+
   if constexpr (!std::is_same<TA, double>::value) {
     // tensor cores, kind::tf32 (gram_tf32.cuh): (shard, block, 128-column strip, 128-column
     // chunk) items over each block's own columns, chunks at or right of the strip.  FP32
@@ -990,6 +1053,7 @@ int build_factors(bicadmm_ctx* h, const std::function<int(int)>* load_shard = nu
         e = cudaGetLastError();
         h->launches += 1;
       }
+      if (e == cudaSuccess && rc == BICADMM_OK && load_shard) e = after_gram(i);
     }
   } else {
     const int T = (h->max_nj + 63) / 64;
@@ -1000,59 +1064,30 @@ int build_factors(bicadmm_ctx* h, const std::function<int(int)>* load_shard = nu
                                                    h->d_blk_col0, G, h->d_G_off, h->M, load_shard ? i : 0);
       e = cudaGetLastError();
       h->launches += 1;
+      if (e == cudaSuccess && load_shard) e = after_gram(i);
     }
   }
   if (rc != BICADMM_OK) {
     cudaStreamSynchronize(h->stream);
+    for (cudaStream_t st : fst)
+      if (st) { cudaStreamSynchronize(st); cudaStreamDestroy(st); }
+    for (cudaEvent_t ev : fev) cudaEventDestroy(ev);
     cudaFree(G);
+    if (YT) cudaFree(YT);
     if (d_items32) cudaFree(d_items32);
     return rc;
   }
-  // Blocked factorisation when an NB-column panel of the widest block fits in shared memory:
-  // Cholesky, Y = L^-1 by columns, P = Y'Y by tiles (n^3/2 FMAs per block); otherwise the
-  // column-by-column kernels (Cholesky, then both triangular solves per column of P).
-  int nb_panel = 0;
-  for (int cand : {32, 16, 8})
-    if (static_cast<size_t>(cand) * (h->max_nj + 1) * sizeof(double) <= (200u << 10)) { nb_panel = cand; break; }
-  double* YT = nullptr;
-  if (e == cudaSuccess && nb_panel > 0) {
-    e = cudaMalloc(&YT, std::max<int64_t>(h->G_total, 1) * sizeof(double));
-    if (e != cudaSuccess) { cudaGetLastError(); YT = nullptr; nb_panel = 0; e = cudaSuccess; }
-  }
-  if (e == cudaSuccess && nb_panel > 0) {
-    const size_t sm = static_cast<size_t>(nb_panel) * (h->max_nj + 1) * sizeof(double);
-#define CHOL_BLK(NBV)                                                                               \
-  {                                                                                                 \
-    auto kc = k_chol_blk<kCholThreads, NBV>;                                                        \
-    e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)); \
-    if (e == cudaSuccess) {                                                                         \
-      kc<<<h->N * h->M, kCholThreads, sm, h->stream>>>(G, h->d_G_off, h->d_blk_col0, h->M,          \
-                                                    h->p.rho_l, h->c0, h->d_err);                   \
-      e = cudaGetLastError();                                                                       \
-    }                                                                                               \
-  }
-    if (nb_panel == 32) CHOL_BLK(32) else if (nb_panel == 16) CHOL_BLK(16) else CHOL_BLK(8)
-#undef CHOL_BLK
-    h->launches += 1;
-    if (e == cudaSuccess) {
-      const int warps = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(8, (200 << 10) / (8 * h->max_nj))));
-      const size_t smy = static_cast<size_t>(warps) * h->max_nj * sizeof(double);
-      if (smy > 48 * 1024) e = cudaFuncSetAttribute(k_inv_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smy));
-      if (e == cudaSuccess) {
-        const dim3 grid(h->N * h->M, (h->max_nj + warps - 1) / warps);
-        k_inv_fwd<<<grid, 32 * warps, smy, h->stream>>>(G, h->d_G_off, h->d_blk_col0, h->M, YT);
-        e = cudaGetLastError();
-      }
-      h->launches += 1;
+  if (per_shard) {
+    // the handle's stream waits for every shard's factorisation
+    for (int q = 0; q < nfs && e == cudaSuccess; ++q) {
+      cudaEvent_t ev;
+      e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e != cudaSuccess) break;
+      fev.push_back(ev);
+      if ((e = cudaEventRecord(ev, fst[q])) == cudaSuccess) e = cudaStreamWaitEvent(h->stream, ev, 0);
     }
-    if (e == cudaSuccess) {
-      const int T = (h->max_nj + 63) / 64;
-      const dim3 grid(T * (T + 1) / 2, h->M, h->N);
-      k_yty<TM><<<grid, 256, 0, h->stream>>>(YT, h->d_G_off, h->d_blk_col0, h->d_blk_ldp, h->M,
-                                             static_cast<TM*>(h->Pm), h->d_P_off);
-      e = cudaGetLastError();
-      h->launches += 1;
-    }
+  } else if (e == cudaSuccess && nb_panel > 0) {
+    e = factor_shards(0, h->N, h->stream);
   } else {
     if (e == cudaSuccess) {
       auto kc = k_chol<kCholThreads>;
@@ -1083,6 +1118,9 @@ int build_factors(bicadmm_ctx* h, const std::function<int(int)>* load_shard = nu
   if (e != cudaSuccess) rc = fail(h, BICADMM_ERR_CUDA, std::string("factor kernels: ") + cudaGetErrorString(e));
   cudaError_t e2 = cudaStreamSynchronize(h->stream);
   if (rc == BICADMM_OK && e2 != cudaSuccess) rc = fail(h, BICADMM_ERR_CUDA, std::string("factor sync: ") + cudaGetErrorString(e2));
+  for (cudaStream_t st : fst)
+    if (st) { cudaStreamSynchronize(st); cudaStreamDestroy(st); }
+  for (cudaEvent_t ev : fev) cudaEventDestroy(ev);
   cudaFree(G);
   if (YT) cudaFree(YT);
   if (d_items32) cudaFree(d_items32);
