@@ -11,8 +11,10 @@ global (z,t,s,v) step, dual update).  `value` is outer iterations per second wit
 resident in HBM; `e2e` is the same metric through the public C ABI from pinned host
 buffers (create + setup + K iterations + get_x, H2D of A and b inside the timed region).
 
-The default line also carries `legs.softmax`: the 500000 x 2000 x 10 BF16 softmax workload's
-value, tensor-core pass roofline and end-to-end figure (skip with --no-legs).
+The default line also carries `legs.softmax` (the 500000 x 2000 x 10 BF16 softmax workload's
+value, tensor-core pass roofline and end-to-end figure) and `legs.path` (10 logistic
+instances at kappa 20..800 on one 500000 x 2000 BF16 A, one tensor-core pass per sweep for
+all of them, against one single-kappa handle); skip both with --no-legs.
 
 --impl reference times the FP64 CPU oracle on a bounded sample (one of the 16 shards): its
 steps are shard iterations (steps x ms_per_step = the time spent) and its value is the
@@ -57,7 +59,7 @@ def parse():
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance leg")
     ap.add_argument("--no-legs", action="store_true",
                     help="default workload only: skip the softmax leg added to its line")
-    ap.add_argument("--workload", default="logistic", choices=["logistic", "softmax", "batch", "serve"],
+    ap.add_argument("--workload", default="logistic", choices=["logistic", "softmax", "batch", "serve", "path"],
                     help="softmax: 500000 x 2000 BF16, 10 classes (tensor-core pass); "
                          "batch: 256 uneven instances advanced by batched launches; "
                          "serve: a Poisson stream of solves through the serving loop")
@@ -479,6 +481,101 @@ def softmax_leg(args):
     return {k: r[k] for k in keep if k in r}
 
 
+PATH = dict(name="logistic_path10_500000x2000_bf16", m=500000, n=2000, nnz=50, corr=0.3, noise=0.5,
+            N=32, M=4, kappa=50, rho=0.5, gamma=10.0, seed=0,
+            kappas=[20, 35, 50, 75, 100, 150, 200, 300, 500, 800])
+
+
+def run_path(args, rank, world):
+    """A sparsity path: 10 instances of sparse logistic regression (A 500000 x 2000, Toeplitz
+    feature correlation, 50-sparse model, stored in BF16), kappa from 20 to 800, solved
+    together on one copy of A (bicadmm_create_path): each inner sweep's products for all 10
+    are one tensor-core pass (A X and A'D as skinny GEMMs).  A step advances every instance
+    by one outer iteration.  The same data solved by one single-kappa handle gives the
+    per-instance cost without sharing."""
+    import torch
+    from paper_2405_16267_b300 import bicadmm as bc
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = dict(PATH)
+    if args.m:
+        wl["m"] = args.m
+    A_np, b_np, _ = generate(wl)
+    A_pin = torch.from_numpy(A_np).to(torch.bfloat16).pin_memory()
+    b_pin = torch.from_numpy(b_np).pin_memory()
+    del A_np
+    stream = torch.cuda.current_stream(dev)
+    R = len(wl["kappas"])
+    common = dict(loss=bc.LOSS_LOGISTIC, N=wl["N"], M=wl["M"], gamma=wl["gamma"], rho_c=wl["rho"],
+                  precision=bc.PREC_BF16, stream=stream)
+
+    def timed(step, steps):
+        step(args.warmup)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    clocks = ClockSampler(local)
+    time.sleep(0.15)
+    ps = bc.PathSolver(A_pin, b_pin, kappas=wl["kappas"], **common)
+    bc.set_profiling(ps.h, 1)
+    info0 = ps.step(0)
+    ms = timed(lambda k: ps.step(k, info=False), args.steps)
+    pass_ms, pass_launches = bc.get_pass_time(ps.h)
+    info1 = ps.step(0)
+    launches = info1.kernel_launches - info0.kernel_launches
+    ps.close()
+    one = bc.Solver(A_pin, b_pin, kappa=wl["kappa"], **common)
+    ms_one = timed(lambda k: one.step(k, info=False), args.steps)
+    one.close()
+    clk = clocks.stop()
+    hbm, peak_kind = peaks()
+    m, n = wl["m"], wl["n"]
+    pass_bytes = m * n * 2 + m * (4 + 16 * R)  # A once (BF16), b, omega and nu (R floats) in and out
+    avg_pass_s = pass_ms / 1000.0 / max(pass_launches, 1)
+    achieved = pass_bytes / avg_pass_s / 1e9
+    per_step = ms / args.steps
+    return {
+        "metric": METRIC + " (every instance of the path)", "value": args.steps / (ms / 1000.0),
+        "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16", "data": "synthetic (seeded; Toeplitz-correlated A, planted 50-sparse model)",
+        "config": {"workload": wl["name"], "m": m, "n": n, "N_shards": wl["N"], "M_blocks": wl["M"],
+                   "kappas": wl["kappas"], "instances": R, "rho": wl["rho"], "gamma": wl["gamma"],
+                   "loss": "logistic", "A_dtype": "bf16",
+                   "l2": "inputs larger than L2 (A is %.1f GB)" % (m * n * 2 / 1e9)},
+        "instance_iters_per_s": R * args.steps / (ms / 1000.0),
+        "single_kappa_handle": {"ms_per_step": ms_one / args.steps,
+                                "iters_per_s": args.steps / (ms_one / 1000.0)},
+        "speedup_vs_separate_handles": R * (ms_one / args.steps) / per_step,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "kernel": "k_fused_pass_tc",
+                     "peak_kind": peak_kind + " copy bandwidth",
+                     "algorithmic_bytes_per_launch": pass_bytes, "avg_launch_ms": avg_pass_s * 1e3,
+                     "launches_timed": pass_launches},
+        "clocks": clk, "gpu_launches": int(launches),
+    }
+
+
+def path_leg(args):
+    """The sparsity-path workload's figures (one tensor-core pass for 10 instances), measured in
+    the default run: its value, per-instance rate, speedup over separate handles, roofline."""
+    import copy
+    a = copy.copy(args)
+    a.steps = min(args.steps, 100)
+    a.warmup = max(args.warmup, 3)
+    r = run_path(a, 0, 1)
+    keep = ("metric", "value", "unit", "steps", "ms_per_step", "config", "instance_iters_per_s",
+            "single_kappa_handle", "speedup_vs_separate_handles", "roofline", "gpu_launches")
+    return {k: r[k] for k in keep if k in r}
+
+
 def run_oracle_softmax(wl, steps, budget_s=30.0):
     """The FP64 oracle on shard 0 of the softmax workload (BF16-rounded A, as the GPU path
     sees it); one full iteration extrapolated as N times one shard's iteration."""
@@ -814,6 +911,8 @@ def main():
         res = run_batch(args, rank, world)
     elif args.workload == "serve":
         res = run_serve(args, rank, world)
+    elif args.workload == "path":
+        res = run_path(args, rank, world)
     elif args.workload == "softmax":
         res = run_softmax(args, rank, world)
         if rank == 0 and not args.no_cpu_baseline and world == 1:
@@ -826,7 +925,12 @@ def main():
         if rank == 0 and not args.no_cpu_baseline and world == 1:
             res["cpu_baseline"] = run_oracle_sample(dict(WORKLOAD), steps=8, warmup=1, budget_s=20.0)
         if world == 1 and not args.no_legs and args.m is None:
-            res["legs"] = {"softmax": softmax_leg(args)}
+            res["legs"] = {}
+            for name, leg in (("softmax", softmax_leg), ("path", path_leg)):
+                try:
+                    res["legs"][name] = leg(args)
+                except Exception as exc:  # a leg never costs the headline line
+                    res["legs"][name] = {"error": "%s: %s" % (type(exc).__name__, exc)}
     if world > 1 and args.impl == "gpu":
         import torch.distributed as dist
         dist.destroy_process_group()

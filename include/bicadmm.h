@@ -142,6 +142,30 @@ int bicadmm_default_params(bicadmm_params* p);
  * a loss or width this build does not implement. */
 int bicadmm_create(const bicadmm_params* params, void* stream, bicadmm_t* out);
 
+/* A sparsity path (not part of the paper; the paper's kappa of eq. (p:SML) is what a user
+ * sweeps): `count` = 2..16 instances of one problem that differ only in kappa (kappas[q],
+ * 1 <= kappas[q] <= n), solved together on one copy of A.  *params describes the shared
+ * problem (loss squared, logistic or squared hinge, K = 1; params->kappa is ignored) and
+ * n * count <= 32768.  The instances are the columns of the multi-column kernels: one pass
+ * over A per inner sweep forms A X and A'D for all of them (skinny GEMMs; on the tensor
+ * cores for BF16 storage and n <= 2048, as the softmax pass), each row's omega prox of eq.
+ * (p:GPU;omega) runs per column, the block solve of eq. (p:GPU;x) takes the count right-hand
+ * sides, and each instance has its own consensus step (its own kappa, t, v, residual
+ * records), run by its own CTA.  Setup, step, solve, set_graph, get_state (x, u, z, s as n x
+ * count, feature-major: entry (c, q) at c count + q) and destroy work as for any handle; step
+ * and solve report instance 0 in *info and solve stops when every instance meets tol_rel.
+ * The shard sums p_r and the inner residual i_r cover every instance together.  Each
+ * instance's iterates are those of its own handle up to rounding of the shared sums.
+ * bicadmm_path_info fills *info for one instance (with its objective); bicadmm_path_get_x
+ * copies its z (n doubles) and, when support_out is non-NULL, its kappas[q] largest |z|
+ * (ascending indices, ties to the lowest).  bicadmm_get_x with polished = 1 or a support is
+ * ERR_UNSUPPORTED on a path (no polish for paths in this build). */
+int bicadmm_create_path(const bicadmm_params* params, int32_t count, const int64_t* kappas,
+                        void* stream, bicadmm_t* out);
+int bicadmm_path_info(bicadmm_t h, int32_t instance, bicadmm_info* info);
+int bicadmm_path_get_x(bicadmm_t h, int32_t instance, double* x_host, int64_t len,
+                       int64_t* support_out);
+
 /* Load the data and build the per-block factors; resets the iteration state to zero.
  * A: m rows of n values with row stride lda (elements, lda >= n), type A_dtype, in host
  *    memory (A_on_device = 0) or device memory (1).  b: m values of type b_dtype (targets

@@ -85,6 +85,11 @@ SIGNATURES = [
     ("bicadmm_get_trace", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
                                          ctypes.POINTER(ctypes.c_int64)]),
     ("bicadmm_inject_pass_stall", ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int64]),
+    ("bicadmm_create_path", ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.c_int64), _VP, ctypes.POINTER(_VP)]),
+    ("bicadmm_path_info", ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(Info)]),
+    ("bicadmm_path_get_x", ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     ("bicadmm_consensus_step_noalloc", ctypes.c_int,
      [_VP, _VP, _VP, _VP, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
       ctypes.c_double, _VP]),
@@ -462,6 +467,84 @@ def destroy(h):
 def last_error(h=None) -> str:
     msg = lib().bicadmm_last_error(h)
     return msg.decode() if msg else ""
+
+
+def create_path(params: Params, kappas, stream=None):
+    """A sparsity path: len(kappas) instances of one problem (see include/bicadmm.h)."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    k = (ctypes.c_int64 * len(kappas))(*[int(v) for v in kappas])
+    h = _VP()
+    _check(lib().bicadmm_create_path(ctypes.byref(params), len(kappas), k, _VP(stream or 0),
+                                     ctypes.byref(h)))
+    return h
+
+
+class PathSolver:
+    """Owner of a path handle: the instances of one problem at the given kappas, solved
+    together on one copy of A."""
+
+    def __init__(self, A, b, *, loss, N, M, kappas, gamma=10.0, rho_c=1.0, rho_b=0.0,
+                 rho_l=0.0, precision=PREC_FP64, stream=None, **extra):
+        m, n = A.shape
+        self.n, self.m, self.N, self.kappas = int(n), int(m), int(N), [int(k) for k in kappas]
+        self.params = default_params(loss=loss, precision=precision, m=m, n=n, N_shards=N,
+                                     M_blocks=M, kappa=1, gamma=gamma, rho_c=rho_c,
+                                     rho_b=rho_b, rho_l=rho_l, **extra)
+        self.h = create_path(self.params, self.kappas, stream)
+        try:
+            setup(self.h, A, b)
+        except Exception:
+            destroy(self.h)
+            self.h = None
+            raise
+
+    def step(self, n_iters, info=True):
+        return step(self.h, n_iters, info)
+
+    def solve(self):
+        return solve(self.h)
+
+    def info(self, q):
+        inf = Info()
+        _check(lib().bicadmm_path_info(self.h, int(q), ctypes.byref(inf)), self.h)
+        return inf
+
+    def x(self, q, with_support=False):
+        """Instance q's z (n entries) and, optionally, its kappa-support."""
+        x = np.zeros(self.n)
+        sup = np.zeros(self.kappas[q], dtype=np.int64) if with_support else None
+        sp = sup.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)) if with_support else None
+        _check(lib().bicadmm_path_get_x(self.h, int(q), x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        self.n, sp), self.h)
+        return (x, sup) if with_support else x
+
+    def state(self, q):
+        """Instance q's x (N x n), u (N x n), z, s (n each) from the feature-major state."""
+        R = len(self.kappas)
+        N, n = self.N, self.n
+        X = get_state(self.h, FIELD_X, N * n * R).reshape(N, n, R)
+        U = get_state(self.h, FIELD_U, N * n * R).reshape(N, n, R)
+        Z = get_state(self.h, FIELD_Z, n * R).reshape(n, R)
+        S = get_state(self.h, FIELD_S, n * R).reshape(n, R)
+        return dict(x=X[:, :, q].copy(), u=U[:, :, q].copy(), z=Z[:, q].copy(), s=S[:, q].copy())
+
+    def close(self):
+        if self.h:
+            destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Solver:

@@ -86,6 +86,14 @@ struct bicadmm_ctx {
   bool use_tc = false;  // BF16 softmax: tensor-core A pass (k_fused_pass_tc)
   bool tf32 = false;    // BICADMM_PREC_TF32: 32-bit storage of A rounded to TF32 (p.precision
                         // then reads FP32, whose kernels serve it unchanged)
+  // a sparsity path (bicadmm_create_path): K = ninst instances of one problem that differ in
+  // kappa, run as the K columns of the multi-column kernels; each has its own consensus CTA,
+  // scalars and residual records; z_cm, s_cm hold their z and s instance-major
+  bool path = false;
+  int ninst = 1;
+  std::vector<int64_t> kappas;
+  int64_t* d_kappas = nullptr;
+  double *z_cm = nullptr, *s_cm = nullptr;
   CUtensorMap tmap;     // 2D map of A (BF16, 64 x 128 boxes, 128-byte swizzle) for it
   double c0 = 0.0;
   size_t esz = 8;  // bytes per m-space / n-space low-precision element (TM)
@@ -210,6 +218,15 @@ ConsensusArgs consensus_args(bicadmm_ctx* h, bool enabled) {
   // the pass kernels launch with pass_smem bytes of dynamic shared memory, which their
   // consensus CTA (it stages no panels) may fill with top-kappa candidates
   a.cand_bytes = static_cast<int64_t>(h->pass_smem);
+  if (h->path) {  // instance q: n entries of the instance-major arrays from q n
+    a.z = h->z_cm;
+    a.s = h->s_cm;
+    a.n = h->p.n;
+    a.kappa = h->kappas[0];
+    a.ninst = h->ninst;
+    a.inst_n = h->p.n;
+    a.kappas = h->d_kappas;
+  }
   return a;
 }
 
@@ -232,7 +249,7 @@ int launch_pass_rv(bicadmm_ctx* h, bool with_consensus) {
     attr_set = true;
   }
   PassGeometry geo{h->d_shard_row0, h->d_panel_start, h->N, h->P_panels, h->stall_panel};
-  kern<<<h->G + (with_consensus ? 1 : 0), kPassThreads, h->pass_smem, h->stream>>>(
+  kern<<<h->G + (with_consensus ? h->ninst : 0), kPassThreads, h->pass_smem, h->stream>>>(
       static_cast<const TA*>(h->A), h->lda, static_cast<const TM*>(h->xlo),
       static_cast<const TM*>(h->b), static_cast<TM*>(h->omega), static_cast<TM*>(h->nu),
       static_cast<TM*>(h->slots), h->cta_stats, geo, h->S, h->p.loss, static_cast<TM>(h->M),
@@ -290,12 +307,12 @@ int launch_pass_k_v(bicadmm_ctx* h, bool with_consensus, int op, int* blocks) {
       return BICADMM_OK;
     }
     PassGeometry geo{h->d_shard_row0, h->d_panel_start, h->N, h->P_panels, -1};
-    kern<<<h->G + (with_consensus ? 1 : 0), kPassThreads, h->pass_smem, h->stream>>>(
+    kern<<<h->G + (with_consensus ? h->ninst : 0), kPassThreads, h->pass_smem, h->stream>>>(
         static_cast<const TA*>(h->A), h->lda, static_cast<const TM*>(h->xlo), h->ldx, h->K,
         static_cast<const TM*>(h->b), static_cast<TM*>(h->omega), static_cast<TM*>(h->nu),
         static_cast<TM*>(h->slots), h->cta_stats, geo, h->S, static_cast<TM>(h->M),
         static_cast<TM>(h->p.rho_l), h->p.newton_iters, h->d_err, kWaitLimitCycles,
-        consensus_args(h, with_consensus));
+        consensus_args(h, with_consensus), h->path ? h->p.loss : -1);
     CK(cudaGetLastError());
     return BICADMM_OK;
   }
@@ -331,12 +348,12 @@ int launch_pass_tc_c(bicadmm_ctx* h, bool with_consensus, int op, int* blocks) {
     return BICADMM_OK;
   }
   PassGeometry geo{h->d_shard_row0, h->d_panel_start, h->N, h->P_panels, -1};
-  kern<<<h->G + (with_consensus ? 1 : 0), kTcThreads, h->pass_smem, h->stream>>>(
+  kern<<<h->G + (with_consensus ? h->ninst : 0), kTcThreads, h->pass_smem, h->stream>>>(
       h->tmap, h->lda, h->wpk, h->ldx, h->K,
       static_cast<const float*>(h->b), static_cast<float*>(h->omega), static_cast<float*>(h->nu),
       static_cast<float*>(h->slots), h->cta_stats, geo, static_cast<float>(h->M),
       static_cast<float>(h->p.rho_l), h->p.newton_iters, h->d_err, kWaitLimitCycles,
-      consensus_args(h, with_consensus));
+      consensus_args(h, with_consensus), h->path ? h->p.loss : -1);
   CK(cudaGetLastError());
   return BICADMM_OK;
 }
@@ -500,7 +517,12 @@ int run_iterations(bicadmm_ctx* h, int n_iters) {
       // The last sweep's pass also runs the global step in its spare CTA; its target w
       // is formed here by all SMs.
       const bool last = jj == h->p.inner_iters - 1;
-      if (last && h->K > 1) {
+      if (last && h->path) {
+        k_consensus_prep_path<<<static_cast<unsigned>((n + 255) / 256), 256, 0, h->stream>>>(
+            h->x, h->u, h->s_cm, h->w, h->tau_r, h->c_arr, h->e_arr, N, h->p.n, h->K, lda);
+        CK(cudaGetLastError());
+        h->launches += 1;
+      } else if (last && h->K > 1) {
         k_consensus_prep<<<static_cast<unsigned>((n + 255) / 256), 256, 0, h->stream>>>(
             h->x, h->u, h->s, h->w, h->tau_r, h->c_arr, h->e_arr, N, n, lda);
         CK(cudaGetLastError());
@@ -511,13 +533,19 @@ int run_iterations(bicadmm_ctx* h, int n_iters) {
       if (rc != BICADMM_OK) return rc;
       if ((rc = prof_end(h, KIND_PASS)) != BICADMM_OK) return rc;
       h->launches += 2;
+      if (last && h->path) {  // the instances' z and s back to the feature-major layout
+        k_path_to_feature_major<<<static_cast<unsigned>((n + 255) / 256), 256, 0, h->stream>>>(
+            h->z_cm, h->s_cm, h->z, h->s, h->p.n, h->K);
+        CK(cudaGetLastError());
+        h->launches += 1;
+      }
     }
     int rc;
     if ((rc = prof_begin(h, KIND_DUAL)) != BICADMM_OK) return rc;
     k_dual<TM, kDualThreads><<<dual_grid, kDualThreads, 0, h->stream>>>(
         h->u, h->x, h->z, static_cast<const TM*>(h->slots), h->d_slot_lo, h->d_slot_hi, h->r,
         h->p.rho_l, h->c0, h->dual_part, h->cta_stats, h->G, h->gs, h->trace, kTraceCap, N, n,
-        lda, h->p.rho_c, h->d_err);
+        lda, h->p.rho_c, h->d_err, h->ninst);
     CK(cudaGetLastError());
     if ((rc = prof_end(h, KIND_DUAL)) != BICADMM_OK) return rc;
     h->launches += 1;
@@ -544,27 +572,29 @@ int check_device_error(bicadmm_ctx* h) {
 // F(z) of problem (p:SML) at the current consensus iterate, in FP64 (objective.cuh).  Its
 // three launches are diagnostics: they are not counted in h->launches.
 template <typename TA, typename TM>
-int launch_obj_rows(bicadmm_ctx* h) {
-  if (h->K == 1)
+int launch_obj_rows(bicadmm_ctx* h, const double* z, int K) {
+  if (K == 1)
     k_obj_rows<TA, TM, 1><<<h->obj_blocks, kObjThreads, 0, h->stream>>>(
-        static_cast<const TA*>(h->A), h->lda, static_cast<const TM*>(h->b), h->z, h->obj_idx,
+        static_cast<const TA*>(h->A), h->lda, static_cast<const TM*>(h->b), z, h->obj_idx,
         h->obj_cnt, h->p.m, 1, h->p.loss, h->obj_part);
   else
     k_obj_rows<TA, TM, 16><<<h->obj_blocks, kObjThreads, 0, h->stream>>>(
-        static_cast<const TA*>(h->A), h->lda, static_cast<const TM*>(h->b), h->z, h->obj_idx,
-        h->obj_cnt, h->p.m, h->K, h->p.loss, h->obj_part);
+        static_cast<const TA*>(h->A), h->lda, static_cast<const TM*>(h->b), z, h->obj_idx,
+        h->obj_cnt, h->p.m, K, h->p.loss, h->obj_part);
   CK(cudaGetLastError());
   return BICADMM_OK;
 }
 
-int compute_objective(bicadmm_ctx* h, double* out) {
-  k_obj_compact<1024><<<1, 1024, 0, h->stream>>>(h->z, h->p.n, h->K, h->obj_idx, h->obj_cnt,
-                                                  h->obj_out);
+// inst: the instance of a path (its z, one column); the handle's z otherwise.
+int compute_objective(bicadmm_ctx* h, double* out, int inst = 0) {
+  const double* z = h->path ? h->z_cm + static_cast<int64_t>(inst) * h->p.n : h->z;
+  const int K = h->path ? 1 : h->K;
+  k_obj_compact<1024><<<1, 1024, 0, h->stream>>>(z, h->p.n, K, h->obj_idx, h->obj_cnt, h->obj_out);
   CK(cudaGetLastError());
   int rc;
-  if (h->asz == 8) rc = launch_obj_rows<double, double>(h);
-  else if (h->asz == 4) rc = launch_obj_rows<float, float>(h);
-  else rc = launch_obj_rows<__nv_bfloat16, float>(h);
+  if (h->asz == 8) rc = launch_obj_rows<double, double>(h, z, K);
+  else if (h->asz == 4) rc = launch_obj_rows<float, float>(h, z, K);
+  else rc = launch_obj_rows<__nv_bfloat16, float>(h, z, K);
   if (rc != BICADMM_OK) return rc;
   k_obj_final<256><<<1, 256, 0, h->stream>>>(h->obj_part, h->obj_blocks, h->p.gamma, h->obj_out);
   CK(cudaGetLastError());
@@ -572,14 +602,16 @@ int compute_objective(bicadmm_ctx* h, double* out) {
   return BICADMM_OK;
 }
 
-int fill_info(bicadmm_ctx* h, bicadmm_info* info, bool objective = true) {
+int fill_info(bicadmm_ctx* h, bicadmm_info* info, bool objective = true, int inst = 0) {
   double obj = 0.0;
   if (objective) {
-    const int rc = compute_objective(h, &obj);
+    const int rc = compute_objective(h, &obj, inst);
     if (rc != BICADMM_OK) return rc;
   }
   GlobalState g;
-  CK(cudaMemcpyAsync(&g, h->gs, sizeof(g), cudaMemcpyDeviceToHost, h->stream));
+  const GlobalState* gsrc = h->gs + inst;
+  const Resid* tbase = h->trace + static_cast<int64_t>(inst) * kTraceCap;
+  CK(cudaMemcpyAsync(&g, gsrc, sizeof(g), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   std::memset(info, 0, sizeof(*info));
   info->iters = static_cast<int32_t>(g.iter);
@@ -590,7 +622,7 @@ int fill_info(bicadmm_ctx* h, bicadmm_info* info, bool objective = true) {
   info->kernel_launches = h->launches;
   if (g.iter > 0) {
     Resid rec;
-    CK(cudaMemcpyAsync(&rec, h->trace + (g.iter - 1) % kTraceCap, sizeof(rec),
+    CK(cudaMemcpyAsync(&rec, tbase + (g.iter - 1) % kTraceCap, sizeof(rec),
                        cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     info->p_r = rec.p_r; info->d_r = rec.d_r; info->b_r = rec.b_r; info->i_r = rec.i_r;
@@ -742,8 +774,8 @@ int build_geometry(bicadmm_ctx* h) {
   }
   if (rc != BICADMM_OK) return rc;
   if (occ < 1) return fail(h, BICADMM_ERR_UNSUPPORTED, "A-pass variant cannot be resident on an SM");
-  // One resident slot is kept for the consensus CTA that rides on the last pass.
-  const int64_t slots_total = static_cast<int64_t>(occ) * h->num_sms - 1;
+  // One resident slot is kept for each consensus CTA that rides on the last pass.
+  const int64_t slots_total = static_cast<int64_t>(occ) * h->num_sms - h->ninst;
   if (slots_total < 1) return fail(h, BICADMM_ERR_UNSUPPORTED, "A-pass needs at least two resident CTAs");
   // At least 4 panels per CTA: a shard's A'd partial sums are spread over one slot per CTA
   // that touches it, and every x-update right-hand side sums them (small problems had
@@ -825,8 +857,13 @@ int allocate(bicadmm_ctx* h) {
   AL(h->d_blk_ldp, h->blk_ldp.size() * sizeof(int));
   AL(h->d_slot_lo, N * sizeof(int));
   AL(h->d_slot_hi, N * sizeof(int));
-  AL(h->gs, sizeof(GlobalState));
-  AL(h->trace, kTraceCap * sizeof(Resid));
+  AL(h->gs, static_cast<size_t>(h->ninst) * sizeof(GlobalState));
+  AL(h->trace, static_cast<size_t>(h->ninst) * kTraceCap * sizeof(Resid));
+  if (h->path) {
+    AL(h->z_cm, h->p.n * h->K * sizeof(double));
+    AL(h->s_cm, h->p.n * h->K * sizeof(double));
+    AL(h->d_kappas, h->ninst * sizeof(int64_t));
+  }
   AL(h->d_err, sizeof(int));
   h->obj_blocks = std::max(1, h->num_sms) * 4;
   AL(h->obj_idx, h->p.n * sizeof(int));
@@ -845,6 +882,7 @@ int allocate(bicadmm_ctx* h) {
   CK(up(h->d_blk_ldp, h->blk_ldp.data(), h->blk_ldp.size() * sizeof(int)));
   CK(up(h->d_slot_lo, h->slot_lo.data(), N * sizeof(int)));
   CK(up(h->d_slot_hi, h->slot_hi.data(), N * sizeof(int)));
+  if (h->path) CK(up(h->d_kappas, h->kappas.data(), h->ninst * sizeof(int64_t)));
   CK(cudaStreamSynchronize(h->stream));
   return BICADMM_OK;
 }
@@ -864,8 +902,12 @@ int reset_state(bicadmm_ctx* h) {
   CK(cudaMemsetAsync(h->s, 0, lda * sizeof(double), h->stream));
   CK(cudaMemsetAsync(h->w, 0, lda * sizeof(double), h->stream));
   CK(cudaMemsetAsync(h->cta_stats, 0, static_cast<size_t>(h->G) * 4 * sizeof(double), h->stream));
-  CK(cudaMemsetAsync(h->gs, 0, sizeof(GlobalState), h->stream));
-  CK(cudaMemsetAsync(h->trace, 0, kTraceCap * sizeof(Resid), h->stream));
+  CK(cudaMemsetAsync(h->gs, 0, static_cast<size_t>(h->ninst) * sizeof(GlobalState), h->stream));
+  CK(cudaMemsetAsync(h->trace, 0, static_cast<size_t>(h->ninst) * kTraceCap * sizeof(Resid), h->stream));
+  if (h->path) {
+    CK(cudaMemsetAsync(h->z_cm, 0, h->p.n * h->K * sizeof(double), h->stream));
+    CK(cudaMemsetAsync(h->s_cm, 0, h->p.n * h->K * sizeof(double), h->stream));
+  }
   CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
   h->iters_done = 0;
   h->converged = false;
@@ -920,7 +962,7 @@ int load_matrix(bicadmm_ctx* h, const void* src, int dtype, int64_t lda_src, int
 // Softmax: every b_r must be an integral class index in [0, K).
 template <typename TM>
 int check_labels(bicadmm_ctx* h) {
-  if (h->K == 1) return BICADMM_OK;
+  if (h->K == 1 || h->path) return BICADMM_OK;
   const unsigned grid = static_cast<unsigned>(std::min<int64_t>((h->p.m + 255) / 256, 4096));
   k_check_labels<TM><<<grid, 256, 0, h->stream>>>(static_cast<const TM*>(h->b), h->p.m, h->K, h->d_err);
   CK(cudaGetLastError());
@@ -1874,15 +1916,8 @@ int bicadmm_estimate_bytes(const bicadmm_params* params, int64_t* device_bytes,
   return BICADMM_OK;
 }
 
-int bicadmm_create(const bicadmm_params* params, void* stream, bicadmm_t* out) {
-  g_create_error.clear();
-  if (!out) { g_create_error = "out is NULL"; return BICADMM_ERR_ARG; }
-  *out = nullptr;
-  std::string why;
-  int rc = validate(params, why);
-  if (rc != BICADMM_OK) { g_create_error = why; return rc; }
-  bicadmm_ctx* h = new bicadmm_ctx();
-  h->p = *params;
+// The part of create shared by single handles and paths: h->p (and the path fields) set.
+static int create_handle(bicadmm_ctx* h, void* stream, bicadmm_t* out) {
   if (h->p.precision == BICADMM_PREC_TF32) {
     h->tf32 = true;
     h->p.precision = BICADMM_PREC_FP32;
@@ -1897,7 +1932,7 @@ int bicadmm_create(const bicadmm_params* params, void* stream, bicadmm_t* out) {
     delete h;
     return BICADMM_ERR_CUDA;
   }
-  rc = build_geometry(h);
+  int rc = build_geometry(h);
   if (rc == BICADMM_OK) rc = allocate(h);
   // the 2D tensor map of A serves the tensor-core softmax pass
   if (rc == BICADMM_OK && h->use_tc) rc = make_tmap(h);
@@ -1910,6 +1945,79 @@ int bicadmm_create(const bicadmm_params* params, void* stream, bicadmm_t* out) {
   }
   *out = h;
   return BICADMM_OK;
+}
+
+int bicadmm_create(const bicadmm_params* params, void* stream, bicadmm_t* out) {
+  g_create_error.clear();
+  if (!out) { g_create_error = "out is NULL"; return BICADMM_ERR_ARG; }
+  *out = nullptr;
+  std::string why;
+  int rc = validate(params, why);
+  if (rc != BICADMM_OK) { g_create_error = why; return rc; }
+  bicadmm_ctx* h = new bicadmm_ctx();
+  h->p = *params;
+  return create_handle(h, stream, out);
+}
+
+int bicadmm_create_path(const bicadmm_params* params, int32_t count, const int64_t* kappas,
+                        void* stream, bicadmm_t* out) {
+  g_create_error.clear();
+  if (!out) { g_create_error = "out is NULL"; return BICADMM_ERR_ARG; }
+  *out = nullptr;
+  if (!params || !kappas) { g_create_error = "params and kappas are required"; return BICADMM_ERR_ARG; }
+  if (count < 2 || count > 16) { g_create_error = "a path holds 2..16 instances"; return BICADMM_ERR_ARG; }
+  if (params->loss == BICADMM_LOSS_SOFTMAX || params->K != 1) {
+    g_create_error = "a path runs a one-column loss (K = 1: squared, logistic, squared hinge)";
+    return BICADMM_ERR_ARG;
+  }
+  int64_t kmax = 0;
+  for (int q = 0; q < count; ++q) {
+    if (kappas[q] < 1 || kappas[q] > params->n) { g_create_error = "need 1 <= kappa <= n for every instance"; return BICADMM_ERR_ARG; }
+    kmax = std::max(kmax, kappas[q]);
+  }
+  bicadmm_params v = *params;
+  v.kappa = kmax;
+  std::string why;
+  int rc = validate(&v, why);
+  if (rc != BICADMM_OK) { g_create_error = why; return rc; }
+  if (params->n * count > kMaxN) { g_create_error = "n times the instance count must be <= 32768"; return BICADMM_ERR_UNSUPPORTED; }
+  bicadmm_ctx* h = new bicadmm_ctx();
+  h->p = v;
+  h->p.K = count;  // the instances are the columns of the multi-column kernels
+  h->path = true;
+  h->ninst = count;
+  h->kappas.assign(kappas, kappas + count);
+  return create_handle(h, stream, out);
+}
+
+int bicadmm_path_info(bicadmm_t h, int32_t instance, bicadmm_info* info) {
+  if (!h || !info) return BICADMM_ERR_ARG;
+  if (!h->path || instance < 0 || instance >= h->ninst) return fail(h, BICADMM_ERR_ARG, "not an instance of a path");
+  if (!h->ready) return fail(h, BICADMM_ERR_STATE, "bicadmm_path_info before setup");
+  int rc = fill_info(h, info, true, instance);
+  info->converged = h->converged ? 1 : 0;
+  return rc;
+}
+
+int bicadmm_path_get_x(bicadmm_t h, int32_t instance, double* x_host, int64_t len, int64_t* support_out) {
+  if (!h) return BICADMM_ERR_ARG;
+  if (!h->path || instance < 0 || instance >= h->ninst) return fail(h, BICADMM_ERR_ARG, "not an instance of a path");
+  if (!h->ready) return fail(h, BICADMM_ERR_STATE, "bicadmm_path_get_x before setup");
+  if (!x_host || len != h->p.n) return fail(h, BICADMM_ERR_ARG, "x_host must hold n doubles");
+  const double* zq = h->z_cm + static_cast<int64_t>(instance) * h->p.n;
+  CK(cudaMemcpyAsync(x_host, zq, h->p.n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (support_out) {
+    const int64_t kq = h->kappas[static_cast<size_t>(instance)];
+    if (!h->supp) {
+      int rc = dev_alloc(h, &h->supp, h->p.kappa * sizeof(int64_t));  // p.kappa: the largest
+      if (rc != BICADMM_OK) return rc;
+    }
+    k_support<1024, 1><<<1, 1024, 0, h->stream>>>(zq, h->key, h->p.n, kq, h->supp);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(support_out, h->supp, kq * sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return check_device_error(h);
 }
 
 int bicadmm_setup(bicadmm_t h, const void* A, int32_t A_dtype, int64_t lda, int32_t A_on_device,
@@ -2035,7 +2143,12 @@ int bicadmm_solve(bicadmm_t h, bicadmm_info* info) {
     int rc = step_impl(h, k, &loc, false);
     if (rc != BICADMM_OK) return rc;
     done += k;
-    const double mx = std::max(std::max(loc.p_rel, loc.d_rel), std::max(loc.b_rel, loc.i_rel));
+    double mx = std::max(std::max(loc.p_rel, loc.d_rel), std::max(loc.b_rel, loc.i_rel));
+    for (int q = 1; q < h->ninst; ++q) {  // a path stops when every instance has
+      bicadmm_info lq;
+      if ((rc = fill_info(h, &lq, false, q)) != BICADMM_OK) return rc;
+      mx = std::max(mx, std::max(std::max(lq.p_rel, lq.d_rel), std::max(lq.b_rel, lq.i_rel)));
+    }
     if (mx <= h->p.tol_rel) { h->converged = true; break; }
   }
   loc.converged = h->converged ? 1 : 0;
@@ -2053,6 +2166,8 @@ int bicadmm_get_x(bicadmm_t h, double* x_host, int64_t len, int32_t polished, in
   if (!x_host || len != nK) return fail(h, BICADMM_ERR_ARG, "x_host must hold n K doubles");
   if (polished && h->p.kappa > kMaxPolishKappa)
     return fail(h, BICADMM_ERR_UNSUPPORTED, "polish supports kappa <= 1024");
+  if (h->path && (polished || support_out))
+    return fail(h, BICADMM_ERR_UNSUPPORTED, "a path's instances are read with bicadmm_path_get_x (no polish)");
   if (!polished) {
     CK(cudaMemcpyAsync(x_host, h->z, nK * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     if (support_out) {

@@ -266,10 +266,12 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
                 const float* __restrict__ b, float* __restrict__ omega, float* __restrict__ nu,
                 float* __restrict__ slots, double* __restrict__ cta_stats, PassGeometry geo,
                 float Mf, float rho_l, int newton_iters, int* __restrict__ err,
-                long long wait_limit, ConsensusArgs cons) {
+                long long wait_limit, ConsensusArgs cons, int path_loss) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  if (cons.enabled && blockIdx.x == gridDim.x - 1) {
-    consensus_block<kTcThreads, kConsMW>(cons, smem_raw);  // its dynamic smem holds the top-kappa candidates
+  // the last consensus_ctas(cons) CTAs run the global step (one per instance of a path)
+  if (cons.enabled && blockIdx.x >= gridDim.x - consensus_ctas(cons)) {
+    const int q = blockIdx.x - (gridDim.x - consensus_ctas(cons));
+    consensus_block<kTcThreads, kConsMW>(consensus_instance(cons, q), smem_raw);  // its dynamic smem holds the top-kappa candidates
     return;
   }
   constexpr int S = kTcStages;
@@ -292,7 +294,7 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
   float* red = reinterpret_cast<float*>(counts + 2);               // [4 warps][3]
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int c = blockIdx.x, G = gridDim.x - (cons.enabled ? 1 : 0);
+  const int c = blockIdx.x, G = gridDim.x - consensus_ctas(cons);
   const int64_t p_begin = static_cast<int64_t>(c) * geo.P / G;
   const int64_t p_end = static_cast<int64_t>(c + 1) * geo.P / G;
   const int np = static_cast<int>(p_end - p_begin);
@@ -487,6 +489,7 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
     // prefetched row data of the next panel
     float nur[KC], wv[KC];
     int y = 0;
+    float yb = 0.f;
     auto prefetch = [&](int k) {
       int64_t row0 = 0;
       int nrows = 0, sh;
@@ -501,6 +504,7 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
         wv[q] = (valid && q < K) ? omega[(row0 + r) * K + q] : 0.f;
       }
       y = valid ? static_cast<int>(b[row0 + r]) : 0;
+      yb = valid ? b[row0 + r] : 0.f;
     };
     prefetch(0);
     for (int k = 0; k < np && eok; ++k) {
@@ -516,6 +520,7 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
         const bool valid = has_row && r < nrows;
         float Axb[KC], aa[KC], w[KC], nk[KC];
         const int yk = y;
+        const float ybk = yb;
 #pragma unroll
         for (int q = 0; q < KC; ++q) {
           Axb[q] = (__uint_as_float(v[q]) + __uint_as_float(vl[q])) / Mf;
@@ -524,7 +529,15 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
           aa[q] = Axb[q] + nk[q];
         }
         prefetch(k + 1);  // the next panel's rows: the loads overlap the prox
-        if (valid) softmax_prox_row<KC>(w, aa, yk, K, Mf, rho_l, newton_iters);
+        if (valid) {
+          if (path_loss < 0) {
+            softmax_prox_row<KC>(w, aa, yk, K, Mf, rho_l, newton_iters);
+          } else {  // a path: K instances, each column its own scalar prox on target b_r
+#pragma unroll
+            for (int q = 0; q < KC; ++q)
+              if (q < K) w[q] = omega_prox<float>(path_loss, aa[q], ybk, Mf, rho_l, newton_iters, w[q]);
+          }
+        }
         unsigned char* dbuf = ds + (k & 1) * 4096;
 #pragma unroll
         for (int q = 0; q < 16; ++q) {

@@ -191,13 +191,15 @@ k_fused_pass_k(const TA* __restrict__ A, int64_t lda, const TM* __restrict__ xlo
                int K, const TM* __restrict__ b, TM* __restrict__ omega, TM* __restrict__ nu,
                TM* __restrict__ slots, double* __restrict__ cta_stats, PassGeometry geo, int S,
                TM Mf, TM rho_l, int newton_iters, int* __restrict__ err, long long wait_limit,
-               ConsensusArgs cons) {
+               ConsensusArgs cons, int path_loss) {
   static_assert(R <= NT / 16, "one half-warp per panel row in the epilogue");
   constexpr int C = ClassPad<KC>::C;
   constexpr int LOGC = C == 4 ? 2 : (C == 8 ? 3 : 4);
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  if (cons.enabled && blockIdx.x == gridDim.x - 1) {
-    consensus_block<NT, kConsMW>(cons, smem_raw);  // its dynamic smem holds the top-kappa candidates
+  // the last consensus_ctas(cons) CTAs run the global step (one per instance of a path)
+  if (cons.enabled && blockIdx.x >= gridDim.x - consensus_ctas(cons)) {
+    const int q = blockIdx.x - (gridDim.x - consensus_ctas(cons));
+    consensus_block<NT, kConsMW>(consensus_instance(cons, q), smem_raw);  // its dynamic smem holds the top-kappa candidates
     return;
   }
   using V = typename Vec16<TA>::type;
@@ -212,7 +214,7 @@ k_fused_pass_k(const TA* __restrict__ A, int64_t lda, const TM* __restrict__ xlo
   TM* d_s = red + R * NW * C;                  // [R][C]
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int c = blockIdx.x, G = gridDim.x - (cons.enabled ? 1 : 0);
+  const int c = blockIdx.x, G = gridDim.x - consensus_ctas(cons);
   const int64_t p_begin = static_cast<int64_t>(c) * geo.P / G;
   const int64_t p_end = static_cast<int64_t>(c + 1) * geo.P / G;
   const int64_t np = p_end - p_begin;
@@ -338,7 +340,11 @@ k_fused_pass_k(const TA* __restrict__ A, int64_t lda, const TM* __restrict__ xlo
       }
       const TM Axb = tot / Mf;
       const int y = static_cast<int>(y_r);
-      const TM om = softmax_prox<TM>(hw, act, cls == y, Axb + nu_r, Mf, rho_l, newton_iters, om_r);
+      // softmax: the row's K-vector prox; a path (path_loss >= 0): K instances, each lane's
+      // column its own scalar prox on the row's target (path_loss is uniform: no divergence)
+      const TM om = path_loss < 0
+                        ? softmax_prox<TM>(hw, act, cls == y, Axb + nu_r, Mf, rho_l, newton_iters, om_r)
+                        : (act ? omega_prox<TM>(path_loss, Axb + nu_r, y_r, Mf, rho_l, newton_iters, om_r) : TM(0));
       TM dval = TM(0);
       if (act) {
         const TM nun = nu_r + Axb - om;

@@ -268,7 +268,29 @@ struct ConsensusArgs {
   int prepared;      // 1: w, tau_r, c_arr, e_arr were formed by k_consensus_prep
   int64_t cand_bytes;  // dynamic shared memory the running CTA may use for top-kappa
                        // candidates (0: none; the select then reads every key each pass)
+  // Several instances on one A (a sparsity path, see bicadmm_create_path): ninst > 1
+  // consensus CTAs, instance q working on w, z, s, tau_r, c_arr, e_arr, key + q * inst_n
+  // (instance-major slices of n entries), its own kappas[q], gs + q and trace + q * trace_cap.
+  int ninst;           // 0 or 1: one instance (the fields above as they are)
+  int64_t inst_n;
+  const int64_t* kappas;
 };
+
+// The consensus arguments of instance q of a path (q = 0 and a single instance: unchanged).
+__device__ __forceinline__ ConsensusArgs consensus_instance(const ConsensusArgs& c, int q) {
+  ConsensusArgs a = c;
+  if (c.ninst > 1) {
+    const int64_t o = static_cast<int64_t>(q) * c.inst_n;
+    a.w += o; a.z += o; a.s += o; a.tau_r += o; a.c_arr += o; a.e_arr += o; a.key += o;
+    a.gs += q;
+    a.trace += static_cast<int64_t>(q) * c.trace_cap;
+    a.kappa = c.kappas[q];
+  }
+  return a;
+}
+__device__ __forceinline__ int consensus_ctas(const ConsensusArgs& c) {
+  return c.enabled ? (c.ninst > 1 ? c.ninst : 1) : 0;
+}
 
 template <int GT, int MW>
 __device__ void consensus_block(const ConsensusArgs& a, unsigned char* dyn_smem = nullptr) {
@@ -460,6 +482,39 @@ static __global__ void k_consensus_prep(const double* __restrict__ x, const doub
   tau_r[r] = wr == 0.0 ? 0.0 : (sg * sr < 1.0 ? fabs(wr) / (1.0 - sg * sr) : HUGE_VAL);
 }
 
+// A path (several instances on one A, K = their count): the same per-entry work, written
+// instance-major (instance q's n entries contiguous, from q n), which is the layout its
+// consensus CTAs work on; x and u are feature-major (entry (c, q) at c K + q), s instance-major.
+static __global__ void k_consensus_prep_path(const double* __restrict__ x, const double* __restrict__ u,
+                                             const double* __restrict__ s_cm, double* __restrict__ w_cm,
+                                             double* __restrict__ tau_r, double* __restrict__ c_arr,
+                                             double* __restrict__ e_arr, int N, int64_t n, int K,
+                                             int64_t ldx) {
+  const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= n * K) return;
+  const int64_t q = r / n, c = r - q * n, o = c * K + q;
+  double acc = 0.0;
+  for (int i = 0; i < N; ++i) acc += x[i * ldx + o] + u[i * ldx + o];
+  const double wr = acc / N;
+  w_cm[r] = wr;
+  const double sr = s_cm[r], sg = dsign(wr);
+  c_arr[r] = sr * wr - fabs(wr);
+  e_arr[r] = (sr - sg) * (sr - sg);
+  tau_r[r] = wr == 0.0 ? 0.0 : (sg * sr < 1.0 ? fabs(wr) / (1.0 - sg * sr) : HUGE_VAL);
+}
+
+// A path: the consensus CTAs' z and s (instance-major) to the feature-major layout the
+// x-update and the duals read.
+static __global__ void k_path_to_feature_major(const double* __restrict__ z_cm,
+                                               const double* __restrict__ s_cm, double* __restrict__ z,
+                                               double* __restrict__ s, int64_t n, int K) {
+  const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= n * K) return;
+  const int64_t q = r / n, c = r - q * n;
+  z[c * K + q] = z_cm[r];
+  s[c * K + q] = s_cm[r];
+}
+
 // ------------------------------------------------------------------------------ k_dual
 // Grid (chunks, N), DT threads.  End of an outer iteration: u_i += x_i - z (eq. u-update),
 // per-(shard, chunk) sums of ||x_i - z||^2 and ||x_i||^2, and the right-hand side of the next
@@ -519,7 +574,8 @@ k_dual(double* __restrict__ u, const double* __restrict__ x, const double* __res
        const TM* __restrict__ slots, const int* __restrict__ slot_lo,
        const int* __restrict__ slot_hi, double* __restrict__ r, double rho_l, double c0,
        double* __restrict__ part, const double* __restrict__ cta_stats, int G, GlobalState* gs,
-       Resid* trace, int trace_cap, int N, int64_t n, int64_t lda, double rho_c, int* err) {
+       Resid* trace, int trace_cap, int N, int64_t n, int64_t lda, double rho_c, int* err,
+       int ninst) {
   __shared__ double red[32 * 2];
   __shared__ bool last;
   const int i = blockIdx.y, nch = gridDim.x;
@@ -553,14 +609,30 @@ k_dual(double* __restrict__ u, const double* __restrict__ x, const double* __res
   {
     const double pr = fs[0], nx = fs[1], q0 = fs[2], q1 = fs[3], q2 = fs[4];
     if (threadIdx.x == 0) {
-      Resid& rec = trace[gs->iter % trace_cap];
-      rec.p_r = pr;
-      rec.p_rel = pr / fmax(fmax(nx, N * rec.znorm), 1e-30);
-      rec.i_r = sqrt(q0);
-      rec.i_rel = sqrt(q0) / fmax(fmax(sqrt(q1), sqrt(q2)), 1e-30);
-      const double chk = rec.p_r + rec.d_r + rec.b_r + rec.i_r + rec.t + rec.v;
-      if (!isfinite(chk)) set_err(err, DEV_NONFINITE);
-      gs->iter += 1;
+      // A path (ninst > 1): the shard sums and the inner residual cover every instance's
+      // column (one record each gets them, with ||z|| over all instances); one instance:
+      // its own record.
+      const int nq = ninst > 1 ? ninst : 1;
+      double zn = trace[gs->iter % trace_cap].znorm;
+      if (nq > 1) {
+        double zn2 = 0.0;
+        for (int q = 0; q < nq; ++q) {
+          const double zq = trace[static_cast<int64_t>(q) * trace_cap + gs[q].iter % trace_cap].znorm;
+          zn2 += zq * zq;
+        }
+        zn = sqrt(zn2);
+      }
+      for (int q = 0; q < nq; ++q) {
+        GlobalState* g = gs + q;
+        Resid& rec = trace[static_cast<int64_t>(q) * trace_cap + g->iter % trace_cap];
+        rec.p_r = pr;
+        rec.p_rel = pr / fmax(fmax(nx, N * zn), 1e-30);
+        rec.i_r = sqrt(q0);
+        rec.i_rel = sqrt(q0) / fmax(fmax(sqrt(q1), sqrt(q2)), 1e-30);
+        const double chk = rec.p_r + rec.d_r + rec.b_r + rec.i_r + rec.t + rec.v;
+        if (!isfinite(chk)) set_err(err, DEV_NONFINITE);
+        g->iter += 1;
+      }
       gs->ticket = 0;
     }
   }

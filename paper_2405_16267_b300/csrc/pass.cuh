@@ -140,8 +140,10 @@ k_fused_pass(const TA* __restrict__ A, int64_t lda, const TM* __restrict__ xlo_i
   // With cons.enabled the last CTA runs the global (z, t, s, v) step of this outer
   // iteration, which needs only x and u, concurrently with the A stream of the others.
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  if (cons.enabled && blockIdx.x == gridDim.x - 1) {
-    consensus_block<NT, kConsMW>(cons, smem_raw);  // its dynamic smem holds the top-kappa candidates
+  // the last consensus_ctas(cons) CTAs run the global step (one per instance of a path)
+  if (cons.enabled && blockIdx.x >= gridDim.x - consensus_ctas(cons)) {
+    const int q = blockIdx.x - (gridDim.x - consensus_ctas(cons));
+    consensus_block<NT, kConsMW>(consensus_instance(cons, q), smem_raw);  // its dynamic smem holds the top-kappa candidates
     return;
   }
   using V = typename Vec16<TA>::type;
@@ -156,7 +158,7 @@ k_fused_pass(const TA* __restrict__ A, int64_t lda, const TM* __restrict__ xlo_i
   TM* d_s = red + R * NW;                     // [R]
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int c = blockIdx.x, G = gridDim.x - (cons.enabled ? 1 : 0);
+  const int c = blockIdx.x, G = gridDim.x - consensus_ctas(cons);
   const int64_t p_begin = static_cast<int64_t>(c) * geo.P / G;
   const int64_t p_end = static_cast<int64_t>(c + 1) * geo.P / G;
   const int64_t np = p_end - p_begin;
