@@ -167,17 +167,22 @@ class ClockSampler:
 # DRAM traffic of one pass launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of a 20000-row launch of the same kernel, scaled by rows to the
 # 200000-row launch.  Reported only while the kernel sources are the captured ones.
-PASS_TRAFFIC = {"sources_sha256": "d76dc9e818585cae45568e9de75a0b020bcfe8be61b41278d27a17831f0720ee", "bytes_per_launch": 4.0509e+09,
+PASS_TRAFFIC = {"sources_sha256": "6234c825340d3eca3ae24daa693e4da9772079735f7c7a85f0118a825418429f", "bytes_per_launch": 4.0490e+09,
                 "capture": "profiles/k_fused_pass_sparse_logistic_200000x5000_fp32.md"}
 PASS_SOURCES = ["paper_2405_16267_b300/csrc/pass.cuh", "paper_2405_16267_b300/csrc/nspace.cuh",
                 "paper_2405_16267_b300/csrc/common.cuh"]
 
 
 # The same for the tensor-core softmax pass (60000-row capture scaled to 500000 rows).
-TC_TRAFFIC = {"sources_sha256": "2ae5a3bcb40b637ec22f7539fb1b7212a3cf8d98d73e2bf393b9e029742ec9da", "bytes_per_launch": 2.4517e+09,
+TC_TRAFFIC = {"sources_sha256": "3431c4620b268f7c867ce0869d7721a15ad16dd3c0067029c07113c33634fcb4", "bytes_per_launch": 2.4525e+09,
               "capture": "profiles/k_fused_pass_tc_sparse_softmax_500000x2000x10_bf16.md"}
 TC_SOURCES = ["paper_2405_16267_b300/csrc/mc_tc.cuh", "paper_2405_16267_b300/csrc/nspace.cuh",
               "paper_2405_16267_b300/csrc/common.cuh", "paper_2405_16267_b300/csrc/pass.cuh"]
+
+# The same kernel on the sparsity path (10 logistic instances as its columns; 60000-row
+# capture scaled to 500000 rows).
+PATH_TRAFFIC = {"sources_sha256": "3431c4620b268f7c867ce0869d7721a15ad16dd3c0067029c07113c33634fcb4", "bytes_per_launch": 2.4435e+09,
+                "capture": "profiles/k_fused_pass_tc_logistic_path10_500000x2000_bf16.md"}
 
 
 def pass_sources_sha256(sources=None):
@@ -555,7 +560,9 @@ def run_path(args, rank, world):
                                 "iters_per_s": args.steps / (ms_one / 1000.0)},
         "speedup_vs_separate_handles": R * (ms_one / args.steps) / per_step,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "kernel": "k_fused_pass_tc",
+                     "frac": achieved / hbm,
+                     "traffic": pass_traffic(PATH_TRAFFIC, TC_SOURCES) if m == PATH["m"] else None,
+                     "kernel": "k_fused_pass_tc",
                      "peak_kind": peak_kind + " copy bandwidth",
                      "algorithmic_bytes_per_launch": pass_bytes, "avg_launch_ms": avg_pass_s * 1e3,
                      "launches_timed": pass_launches},

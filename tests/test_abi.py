@@ -106,6 +106,23 @@ def test_softmax_create_checks_without_gpu(lib, K, n, kappa, code):
     assert not h.value
 
 
+@pytest.mark.parametrize("kappas,loss,K,n,code", [
+    ([3], 0, 1, 100, -1),              # a path holds 2..16 instances
+    ([3] * 17, 0, 1, 100, -1),
+    ([0, 3], 0, 1, 100, -1),           # 1 <= kappa <= n for every instance
+    ([3, 101], 0, 1, 100, -1),
+    ([3, 4], 2, 3, 100, -1),           # one-column losses only (2: softmax)
+    ([3, 4], 0, 1, 20000, -7),         # n times the instance count <= 32768
+])
+def test_path_create_checks_without_gpu(lib, kappas, loss, K, n, code):
+    p = bc.default_params(m=50, n=n, N_shards=2, M_blocks=2, kappa=3, loss=loss, K=K)
+    k = (ctypes.c_int64 * len(kappas))(*kappas)
+    h = ctypes.c_void_p()
+    assert lib.bicadmm_create_path(ctypes.byref(p), len(kappas), k, None, ctypes.byref(h)) == code
+    assert not h.value
+    assert len(bc.last_error(None)) > 0
+
+
 def test_null_handle_calls_are_safe(lib):
     assert lib.bicadmm_destroy(None) == 0
     assert lib.bicadmm_step(None, 1, None) == -1
