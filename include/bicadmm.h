@@ -214,9 +214,11 @@ int bicadmm_get_x(bicadmm_t h, double* x_host, int64_t len, int32_t polished, in
 int bicadmm_get_state(bicadmm_t h, int32_t field, double* out_host, int64_t len);
 
 /* Per-iteration residual trace: copies the records of the last min(iterations, 4096,
- * max_records) outer iterations, oldest first, to out_host (14 doubles per record:
- * iteration, p_r, d_r, b_r, i_r, p_rel, d_rel, b_rel, i_rel, t, v, tau, ||z||, and the
- * number of Newton steps of the (z,t) root solve), and their count to *n_out.  The
+ * max_records) outer iterations, oldest first, to out_host (15 doubles per record:
+ * iteration, p_r, d_r, b_r, i_r, p_rel, d_rel, b_rel, i_rel, t, v, tau, ||z||, the number
+ * of Newton steps of the (z,t) root solve, and 1 when that step visited only the entry
+ * lists of the all-SM prep kernel (K > 1, warm-started), else 0), and their count to
+ * *n_out.  The
  * records are written on the device every iteration (Sec. 3, Termination) and read only
  * here.  Synchronises the stream. */
 int bicadmm_get_trace(bicadmm_t h, double* out_host, int64_t max_records, int64_t* n_out);

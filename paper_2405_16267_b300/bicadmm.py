@@ -229,7 +229,7 @@ def get_state(h, field, length):
 
 
 TRACE_FIELDS = ("iter", "p_r", "d_r", "b_r", "i_r", "p_rel", "d_rel", "b_rel", "i_rel", "t", "v",
-                "tau", "znorm", "zt_steps")
+                "tau", "znorm", "zt_steps", "zt_lists")
 
 
 def get_trace(h, max_records=4096):

@@ -127,6 +127,10 @@ struct bicadmm_ctx {
   // out[0] = F(z), out[1] = ||z||^2
   int *obj_idx = nullptr, *obj_cnt = nullptr;
   double *obj_part = nullptr, *obj_out = nullptr;
+  // entry lists of k_consensus_prep for the consensus CTA (K > 1): indices per instance
+  // (n K entries, instance-major for a path) and u_nb counts per instance
+  int *u_idx = nullptr, *u_cnt = nullptr;
+  int u_nb = 0;
   int obj_blocks = 0;
   std::vector<void*> allocs;
 
@@ -218,6 +222,11 @@ ConsensusArgs consensus_args(bicadmm_ctx* h, bool enabled) {
   // the pass kernels launch with pass_smem bytes of dynamic shared memory, which their
   // consensus CTA (it stages no panels) may fill with top-kappa candidates
   a.cand_bytes = static_cast<int64_t>(h->pass_smem);
+  if (a.prepared) {
+    a.u_idx = h->u_idx;
+    a.u_cnt = h->u_cnt;
+    a.u_nb = h->u_nb;
+  }
   if (h->path) {  // instance q: n entries of the instance-major arrays from q n
     a.z = h->z_cm;
     a.s = h->s_cm;
@@ -518,13 +527,16 @@ int run_iterations(bicadmm_ctx* h, int n_iters) {
       // is formed here by all SMs.
       const bool last = jj == h->p.inner_iters - 1;
       if (last && h->path) {
-        k_consensus_prep_path<<<static_cast<unsigned>((n + 255) / 256), 256, 0, h->stream>>>(
-            h->x, h->u, h->s_cm, h->w, h->tau_r, h->c_arr, h->e_arr, N, h->p.n, h->K, lda);
+        k_consensus_prep_path<<<dim3(static_cast<unsigned>(h->u_nb), static_cast<unsigned>(h->K)),
+                                kPrepBlock, 0, h->stream>>>(
+            h->x, h->u, h->s_cm, h->z_cm, h->w, h->tau_r, h->c_arr, h->e_arr, h->gs, h->u_idx,
+            h->u_cnt, N, h->p.n, h->K, lda);
         CK(cudaGetLastError());
         h->launches += 1;
       } else if (last && h->K > 1) {
-        k_consensus_prep<<<static_cast<unsigned>((n + 255) / 256), 256, 0, h->stream>>>(
-            h->x, h->u, h->s, h->w, h->tau_r, h->c_arr, h->e_arr, N, n, lda);
+        k_consensus_prep<<<static_cast<unsigned>(h->u_nb), kPrepBlock, 0, h->stream>>>(
+            h->x, h->u, h->s, h->z, h->w, h->tau_r, h->c_arr, h->e_arr, h->gs, h->u_idx, h->u_cnt,
+            N, n, lda);
         CK(cudaGetLastError());
         h->launches += 1;
       }
@@ -813,6 +825,7 @@ void handle_bytes(const bicadmm_ctx* h, int64_t* persistent, int64_t* setup_extr
   b += N * ldx * es + h->P_total * es;                  // xlo, P
   b += static_cast<int64_t>(N) * h->nslab * kTcWBytes;  // packed W (tensor-core pass)
   b += 3 * N * ldx * 8 + 7 * ldx * 8;                   // x, u, r; z, s, w, tau_r, c, e, key
+  if (h->K > 1) b += ldx * 4 + static_cast<int64_t>(h->ninst) * ((ldx + kPrepBlock - 1) / kPrepBlock + 1) * 4;  // entry lists
   b += static_cast<int64_t>(h->G) * 32 + N * h->dual_chunks * 16 + 4096 * 112 + 4096;
   // polish: supp, A_S, q, d1, d2, p, x_S, step, partials, H
   b += kappa * 8 + kappa * m * 8 + 4 * m * 8 + 2 * kappa * 8 + kPolishRowBlocks * 8 +
@@ -865,6 +878,12 @@ int allocate(bicadmm_ctx* h) {
     AL(h->d_kappas, h->ninst * sizeof(int64_t));
   }
   AL(h->d_err, sizeof(int));
+  if (h->K > 1) {
+    const int64_t n_inst = h->path ? h->p.n : h->p.n * h->K;
+    h->u_nb = static_cast<int>((n_inst + kPrepBlock - 1) / kPrepBlock);
+    AL(h->u_idx, static_cast<size_t>(h->p.n) * h->K * sizeof(int));
+    AL(h->u_cnt, static_cast<size_t>(h->ninst) * h->u_nb * sizeof(int));
+  }
   h->obj_blocks = std::max(1, h->num_sms) * 4;
   AL(h->obj_idx, h->p.n * sizeof(int));
   AL(h->obj_cnt, sizeof(int));
@@ -2288,12 +2307,13 @@ int bicadmm_get_trace(bicadmm_t h, double* out_host, int64_t max_records, int64_
   const int64_t cnt = std::min<int64_t>(avail, max_records);
   for (int64_t q = 0; q < cnt; ++q) {
     const Resid& r = recs[(g.iter - cnt + q) % kTraceCap];
-    double* o = out_host + q * 14;
+    double* o = out_host + q * 15;
     o[0] = static_cast<double>(r.iter);
     o[1] = r.p_r; o[2] = r.d_r; o[3] = r.b_r; o[4] = r.i_r;
     o[5] = r.p_rel; o[6] = r.d_rel; o[7] = r.b_rel; o[8] = r.i_rel;
     o[9] = r.t; o[10] = r.v; o[11] = r.tau; o[12] = r.znorm;
     o[13] = static_cast<double>(r.zt_steps);
+    o[14] = static_cast<double>(r.zt_lists);
   }
   if (n_out) *n_out = cnt;
   return check_device_error(h);

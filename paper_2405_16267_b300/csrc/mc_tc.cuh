@@ -271,7 +271,7 @@ k_fused_pass_tc(const __grid_constant__ CUtensorMap tmap, int64_t lda,
   // the last consensus_ctas(cons) CTAs run the global step (one per instance of a path)
   if (cons.enabled && blockIdx.x >= gridDim.x - consensus_ctas(cons)) {
     const int q = blockIdx.x - (gridDim.x - consensus_ctas(cons));
-    consensus_block<kTcThreads, kConsMW>(consensus_instance(cons, q), smem_raw);  // its dynamic smem holds the top-kappa candidates
+    consensus_block<kTcThreads, kConsMW, true>(consensus_instance(cons, q), smem_raw);  // its dynamic smem holds the top-kappa candidates
     return;
   }
   constexpr int S = kTcStages;

@@ -199,7 +199,7 @@ k_fused_pass_k(const TA* __restrict__ A, int64_t lda, const TM* __restrict__ xlo
   // the last consensus_ctas(cons) CTAs run the global step (one per instance of a path)
   if (cons.enabled && blockIdx.x >= gridDim.x - consensus_ctas(cons)) {
     const int q = blockIdx.x - (gridDim.x - consensus_ctas(cons));
-    consensus_block<NT, kConsMW>(consensus_instance(cons, q), smem_raw);  // its dynamic smem holds the top-kappa candidates
+    consensus_block<NT, kConsMW, true>(consensus_instance(cons, q), smem_raw);  // its dynamic smem holds the top-kappa candidates
     return;
   }
   using V = typename Vec16<TA>::type;

@@ -23,6 +23,7 @@ struct Resid {
   double t, v, tau, znorm;
   int64_t iter;
   int64_t zt_steps;
+  int64_t zt_lists;  // 1: the step visited only the prep kernel's entry lists
 };
 
 // Device-resident scalars of the global step.
@@ -274,6 +275,12 @@ struct ConsensusArgs {
   int ninst;           // 0 or 1: one instance (the fields above as they are)
   int64_t inst_n;
   const int64_t* kappas;
+  // Entry lists of k_consensus_prep (nullptr: none): for each block of kPrepBlock entries,
+  // u_cnt[b] entries of U = {r : tau_r > tau_prev or z_r != 0 or s_r != 0} at
+  // u_idx[b kPrepBlock ...] in index order; u_nb blocks per instance.
+  const int* u_idx;
+  const int* u_cnt;
+  int u_nb;
 };
 
 // The consensus arguments of instance q of a path (q = 0 and a single instance: unchanged).
@@ -285,6 +292,10 @@ __device__ __forceinline__ ConsensusArgs consensus_instance(const ConsensusArgs&
     a.gs += q;
     a.trace += static_cast<int64_t>(q) * c.trace_cap;
     a.kappa = c.kappas[q];
+    if (c.u_idx) {
+      a.u_idx += o;
+      a.u_cnt += static_cast<int64_t>(q) * c.u_nb;
+    }
   }
   return a;
 }
@@ -292,13 +303,303 @@ __device__ __forceinline__ int consensus_ctas(const ConsensusArgs& c) {
   return c.enabled ? (c.ninst > 1 ? c.ninst : 1) : 0;
 }
 
-template <int GT, int MW>
+// Entries per block of k_consensus_prep (its lists are per block of this many entries).
+constexpr int kPrepBlock = 256;
+
+// Exclusive prefix of x over the CTA's GT threads in thread order; *total gets the sum.
+// wtot: GT / 32 + 1 ints of shared memory.
+template <int GT>
+__device__ __forceinline__ int block_excl_scan(int x, int* wtot, int* total) {
+  constexpr int NW = GT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = x;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += y;
+  }
+  if (lane == 31) wtot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int t = lane < NW ? wtot[lane] : 0;
+    int ti = t;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, ti, off);
+      if (lane >= off) ti += y;
+    }
+    __syncwarp();
+    if (lane < NW) wtot[lane] = ti - t;
+    if (lane == 31) wtot[NW] = ti;
+  }
+  __syncthreads();
+  const int res = wtot[warp] + incl - x;
+  *total = wtot[NW];
+  __syncthreads();
+  return res;
+}
+
+// The record of the step (residual trace, t, v, tau) written by thread 0.
+__device__ __forceinline__ void consensus_record(const ConsensusArgs& a, double v, double t, double g,
+                                                 double tau, const double (&a4)[4], int64_t steps,
+                                                 int lists) {
+  const double vn = v + g;
+  Resid& rec = a.trace[a.gs->iter % a.trace_cap];
+  const double dz = sqrt(a4[2]), zn = sqrt(a4[3]);
+  rec.d_r = sqrt(static_cast<double>(a.N)) * a.rho_c * dz;
+  rec.b_r = fabs(g);
+  rec.d_rel = dz / fmax(zn, 1e-30);
+  rec.b_rel = fabs(g) / fmax(t, 1e-30);
+  rec.t = t;
+  rec.v = vn;
+  rec.tau = tau;
+  rec.znorm = zn;
+  rec.iter = a.gs->iter + 1;
+  rec.zt_steps = steps;
+  rec.zt_lists = lists;
+  a.gs->t = t;
+  a.gs->v = vn;
+  a.gs->tau = tau;
+}
+
+// The consensus step on the entry lists of k_consensus_prep.  With the previous root
+// tau_prev > 0, every entry outside U has s_r = 0, z_r = 0 and tau_r = |w_r| <= tau_prev; a
+// warm start from tau_prev (h(tau_prev) <= 0) only moves tau up, so such an entry stays at
+// z_r = S_tau(w_r) = 0 and s_r = 0 and adds nothing to any sum.  The step therefore visits U
+// alone: the root's sums over {tau_r > tau} (a subset of U), z and the norms on U, the
+// top-kappa select over U's nonzero z (ties by index: U is in index order), s on U.  Every
+// O(n) scan ran on all SMs in the prep kernel; here U (about the support size) is gathered
+// into shared memory with independent loads.  Returns false, having written nothing, when U
+// does not fit in `bytes` of shared memory or h(tau_prev) > 0; the caller then runs the
+// full-length step.  The arithmetic per entry is that of the full-length step.
+template <int GT>
+__device__ bool consensus_lists(const ConsensusArgs& a, unsigned char* smem, int64_t bytes,
+                                double v, double tau_prev, double beta, double* red) {
+  constexpr int NW = GT / 32;
+  __shared__ unsigned int hist[256];
+  __shared__ long long sh[2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = a.u_nb;
+  if (nb <= 0 || nb > GT) return false;
+  int* pref = reinterpret_cast<int*>(smem);  // nb + 1 list offsets
+  int* wtot = pref + GT + 1;                 // NW + 1
+  const int64_t head = (static_cast<int64_t>(GT + 1 + NW + 1) * 4 + 15) & ~15ll;
+  const int64_t cap = (bytes - head) / 60;   // 7 doubles and an index per entry
+  if (cap <= 0) return false;
+  int total = 0;
+  const int off = block_excl_scan<GT>(tid < nb ? a.u_cnt[tid] : 0, wtot, &total);
+  if (total > cap) return false;  // total is the same in every thread
+  if (tid < nb) pref[tid] = off;
+  if (tid == 0) pref[nb] = total;
+  __syncthreads();
+  double* U_tau = reinterpret_cast<double*>(smem + head);
+  double* U_c = U_tau + cap;   // c_r; after the root: 1.0 for a selected entry
+  double* U_e = U_c + cap;     // e_r
+  double* U_w = U_e + cap;
+  double* U_s = U_w + cap;
+  double* U_zo = U_s + cap;
+  double* U_zn = U_zo + cap;
+  int* U_idx = reinterpret_cast<int*>(U_zn + cap);
+  for (int b = warp; b < nb; b += NW) {
+    const int p0 = pref[b], cb = pref[b + 1] - p0;
+    const int* src = a.u_idx + static_cast<int64_t>(b) * kPrepBlock;
+    for (int j = lane; j < cb; j += 32) U_idx[p0 + j] = src[j];
+  }
+  __syncthreads();
+  // six independent gathers per entry, four entries per thread in flight
+  for (int i0 = tid; i0 < total; i0 += 4 * GT) {
+    int r[4];
+    double t4[4], c4[4], e4[4], w4[4], s4[4], z4[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r[k] = i0 + k * GT < total ? U_idx[i0 + k * GT] : -1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (r[k] >= 0) {
+        t4[k] = a.tau_r[r[k]];
+        c4[k] = a.c_arr[r[k]];
+        e4[k] = a.e_arr[r[k]];
+        w4[k] = a.w[r[k]];
+        s4[k] = a.s[r[k]];
+        z4[k] = a.z[r[k]];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (r[k] >= 0) {
+        const int i = i0 + k * GT;
+        U_tau[i] = t4[k];
+        U_c[i] = c4[k];
+        U_e[i] = e4[k];
+        U_w[i] = w4[k];
+        U_s[i] = s4[k];
+        U_zo[i] = z4[k];
+      }
+    }
+  }
+  __syncthreads();
+
+  // the root: sums of c_r, e_r and the count over {tau_r > at} (all in U for at >= tau_prev)
+  auto active_sums = [&](double at, double (&o)[3]) {
+    o[0] = o[1] = 0.0;
+    int cnt = 0;
+    const long long atb = __double_as_longlong(at);
+    for (int i = tid; i < total; i += GT) {
+      if (__double_as_longlong(U_tau[i]) > atb) {
+        o[0] += U_c[i];
+        o[1] += U_e[i];
+        ++cnt;
+      }
+    }
+    o[2] = static_cast<double>(cnt);
+    block_sum<3>(o, red);
+  };
+  double cur[3];
+  active_sums(tau_prev, cur);
+  if (!(v + cur[0] + (beta + cur[1]) * tau_prev <= 0.0)) return false;  // h(tau_prev) > 0
+  double tau = tau_prev;
+  int64_t steps = 0;
+  const int64_t max_steps = a.n + 2;
+  for (;;) {
+    const double tn = -(v + cur[0]) / (beta + cur[1]);
+    double nxt[3];
+    active_sums(tn, nxt);
+    ++steps;
+    tau = tn;
+    if (nxt[2] >= cur[2]) break;
+    cur[0] = nxt[0]; cur[1] = nxt[1]; cur[2] = nxt[2];
+    if (steps > max_steps) {
+      if (tid == 0) set_err(a.err, DEV_ZT_NOCONV);
+      break;
+    }
+  }
+
+  // z = S_tau(w + tau s) on U (tau >= tau_prev > 0); norms; nonzero keys counted
+  double a4[4] = {0.0, 0.0, 0.0, 0.0};  // ||z||_1, (unused), ||z - z_prev||^2, ||z||^2
+  const long long taub = __double_as_longlong(tau);
+  int ncl = 0;
+  for (int i = tid; i < total; i += GT) {
+    const double wr = U_w[i], sr = U_s[i], zo = U_zo[i];
+    const bool s_zero = (__double_as_longlong(sr) << 1) == 0;
+    double zn = 0.0;
+    if (!(s_zero && (__double_as_longlong(wr) & 0x7FFFFFFFFFFFFFFFll) <= taub)) {
+      const double y = wr + tau * sr;
+      const double mg = fabs(y) - tau;
+      zn = mg > 0.0 ? dsign(y) * mg : 0.0;
+    }
+    U_zn[i] = zn;
+    ncl += (__double_as_longlong(zn) << 1) != 0;
+    if (((__double_as_longlong(zn) | __double_as_longlong(zo)) << 1) != 0) {
+      a4[0] += fabs(zn);
+      a4[2] += (zn - zo) * (zn - zo);
+      a4[3] += zn * zn;
+      a.z[U_idx[i]] = zn;
+    }
+  }
+  block_sum<4>(a4, red);
+  const double t = a4[0];
+  int ncand = 0;
+  block_excl_scan<GT>(ncl, wtot, &ncand);
+
+  // top-kappa of |z| over the nonzero keys of U (a zero z_r gets s_r = 0 whether or not it
+  // is counted among the kappa); ties at the threshold by index, i.e. by position in U
+  const bool take_all = ncand <= a.kappa;
+  uint64_t prefix = 0, mask = 0;
+  int64_t remaining = a.kappa;
+  for (int shift = 56; shift >= 0 && !take_all; shift -= 8) {
+    for (int b = tid; b < 256; b += GT) hist[b] = 0;
+    __syncthreads();
+    for (int i = tid; i < total; i += GT) {
+      const uint64_t k = __double_as_longlong(fabs(U_zn[i]));
+      if (k != 0 && (k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      unsigned int cnt[8], tot = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) { cnt[q] = hist[255 - 8 * lane - q]; tot += cnt[q]; }
+      unsigned int incl = tot;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const unsigned int excl = incl - tot;
+      if (static_cast<int64_t>(excl) < remaining && static_cast<int64_t>(incl) >= remaining) {
+        unsigned int run = excl;
+        for (int q = 0; q < 8; ++q) {
+          if (static_cast<int64_t>(run + cnt[q]) >= remaining) {
+            sh[0] = 255 - 8 * lane - q;
+            sh[1] = remaining - run;
+            break;
+          }
+          run += cnt[q];
+        }
+      }
+    }
+    __syncthreads();
+    prefix |= static_cast<uint64_t>(sh[0]) << shift;
+    mask |= static_cast<uint64_t>(255) << shift;
+    remaining = sh[1];
+    __syncthreads();
+  }
+  // selection flags: above the threshold, or equal to it and among the first `remaining`
+  // equal ones in U order (each thread ranks a contiguous segment of U)
+  const int seg = (total + GT - 1) / GT;
+  const int s0 = tid * seg < total ? tid * seg : total;
+  const int s1 = s0 + seg < total ? s0 + seg : total;
+  int eq = 0;
+  if (!take_all)
+    for (int i = s0; i < s1; ++i) eq += static_cast<uint64_t>(__double_as_longlong(fabs(U_zn[i]))) == prefix;
+  int eqt = 0;
+  int rank = block_excl_scan<GT>(eq, wtot, &eqt);
+  double a1b[1] = {0.0};
+  for (int i = s0; i < s1; ++i) {
+    const uint64_t k = __double_as_longlong(fabs(U_zn[i]));
+    bool take;
+    if (take_all) {
+      take = k != 0;
+    } else {
+      take = k > prefix;
+      if (k == prefix) { take = rank < remaining; ++rank; }
+    }
+    U_c[i] = take ? 1.0 : 0.0;
+    if (take) a1b[0] += fabs(U_zn[i]);
+  }
+  block_sum<1>(a1b, red);
+  const double T = a1b[0];
+  double scale = 0.0;
+  if (T > 0.0) {
+    scale = (t - v) / T;
+    scale = scale > 1.0 ? 1.0 : (scale < -1.0 ? -1.0 : scale);
+  }
+  double a1c[1] = {0.0};
+  for (int i = s0; i < s1; ++i) {
+    double sn = 0.0;
+    if (U_c[i] != 0.0) {
+      const double zr = U_zn[i];
+      sn = scale * dsign(zr);
+      a1c[0] += zr * sn;
+    }
+    if ((__double_as_longlong(sn) | __double_as_longlong(U_s[i])) != 0) a.s[U_idx[i]] = sn;
+  }
+  block_sum<1>(a1c, red);
+  if (tid == 0) consensus_record(a, v, t, a1c[0] - t, tau, a4, steps, 1);
+  return true;
+}
+
+// LISTS: compile the list form in (the multi-column passes, whose consensus is prepared).
+template <int GT, int MW, bool LISTS = false>
 __device__ void consensus_block(const ConsensusArgs& a, unsigned char* dyn_smem = nullptr) {
   __shared__ double red[32 * 4];
   const int tid = threadIdx.x;
   const int64_t n = a.n;
   const double v = a.gs->v, tau_prev = a.gs->tau;
   const double beta = a.N * a.rho_c / a.rho_b;
+  if constexpr (LISTS) {
+    if (a.prepared && a.u_idx && dyn_smem && tau_prev > 0.0 &&
+        consensus_lists<GT>(a, dyn_smem, a.cand_bytes, v, tau_prev, beta, red))
+      return;
+  }
 
   for (int64_t r = a.prepared ? n : tid; r < n; r += GT) {
     double wr;
@@ -433,24 +734,7 @@ __device__ void consensus_block(const ConsensusArgs& a, unsigned char* dyn_smem 
   }
   block_sum<1>(a1c, red);
   const double g = a1c[0] - t;
-  if (tid == 0) {
-    const double vn = v + g;
-    Resid& rec = a.trace[a.gs->iter % a.trace_cap];
-    const double dz = sqrt(a4[2]), zn = sqrt(a4[3]);
-    rec.d_r = sqrt(static_cast<double>(a.N)) * a.rho_c * dz;
-    rec.b_r = fabs(g);
-    rec.d_rel = dz / fmax(zn, 1e-30);
-    rec.b_rel = fabs(g) / fmax(t, 1e-30);
-    rec.t = t;
-    rec.v = vn;
-    rec.tau = tau;
-    rec.znorm = zn;
-    rec.iter = a.gs->iter + 1;
-    rec.zt_steps = steps;
-    a.gs->t = t;
-    a.gs->v = vn;
-    a.gs->tau = tau;
-  }
+  if (tid == 0) consensus_record(a, v, t, g, tau, a4, steps, 0);
 }
 
 // Standalone single-CTA consensus step (n <= 32 * MW * GT).
@@ -465,42 +749,93 @@ __global__ void __launch_bounds__(GT, 1) k_global(ConsensusArgs a) {
 // coefficients c_r, e_r of h (the same formulas as the consensus block).  Run before the
 // pass that carries the consensus CTA (ConsensusArgs::prepared = 1), which then starts at
 // the root search; on B300 FP64 runs at a small fraction of FP32, so this per-entry work
-// (a division per entry) is what one SM should not do for large n.
-static __global__ void k_consensus_prep(const double* __restrict__ x, const double* __restrict__ u,
-                                        const double* __restrict__ s, double* __restrict__ w,
-                                        double* __restrict__ tau_r, double* __restrict__ c_arr,
-                                        double* __restrict__ e_arr, int N, int64_t n, int64_t lda) {
-  const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (r >= n) return;
+// (a division per entry) is what one SM should not do for large n.  Each block of
+// kPrepBlock entries also lists, in index order, its entries of
+// U = {r : tau_r > tau_prev or z_r != 0 or s_r != 0} (tau_prev = gs->tau, the root of the
+// previous step): the consensus CTA's warm-started step visits only those.
+
+// Appends `value` for every thread with `flag` to dst in thread order; *cnt = their number.
+// One block of kPrepBlock threads.
+__device__ __forceinline__ void block_list_append(bool flag, int value, int* __restrict__ dst,
+                                                  int* __restrict__ cnt) {
+  __shared__ int wc[kPrepBlock / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned int m = __ballot_sync(0xffffffffu, flag);
+  if (lane == 0) wc[warp] = __popc(m);
+  __syncthreads();
+  int base = 0;
+  for (int k = 0; k < warp; ++k) base += wc[k];
+  if (flag) dst[base + __popc(m & ((1u << lane) - 1u))] = value;
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int k = 0; k < kPrepBlock / 32; ++k) t += wc[k];
+    *cnt = t;
+  }
+}
+
+__device__ __forceinline__ bool prep_entry(const double* __restrict__ x, const double* __restrict__ u,
+                                           int64_t xo, int64_t ld, int N, double sr, double zr,
+                                           long long tau_prev_bits, double& wr, double& c, double& e,
+                                           double& tr) {
   double acc = 0.0;
-  for (int i = 0; i < N; ++i) acc += x[i * lda + r] + u[i * lda + r];
-  const double wr = acc / N;
-  w[r] = wr;
-  const double sr = s[r], sg = dsign(wr);
-  c_arr[r] = sr * wr - fabs(wr);
-  e_arr[r] = (sr - sg) * (sr - sg);
-  tau_r[r] = wr == 0.0 ? 0.0 : (sg * sr < 1.0 ? fabs(wr) / (1.0 - sg * sr) : HUGE_VAL);
+  for (int i = 0; i < N; ++i) acc += x[i * ld + xo] + u[i * ld + xo];
+  wr = acc / N;
+  const double sg = dsign(wr);
+  c = sr * wr - fabs(wr);
+  e = (sr - sg) * (sr - sg);
+  tr = wr == 0.0 ? 0.0 : (sg * sr < 1.0 ? fabs(wr) / (1.0 - sg * sr) : HUGE_VAL);
+  return __double_as_longlong(tr) > tau_prev_bits ||
+         ((__double_as_longlong(zr) | __double_as_longlong(sr)) << 1) != 0;
+}
+
+static __global__ void __launch_bounds__(kPrepBlock)
+k_consensus_prep(const double* __restrict__ x, const double* __restrict__ u,
+                 const double* __restrict__ s, const double* __restrict__ z,
+                 double* __restrict__ w, double* __restrict__ tau_r, double* __restrict__ c_arr,
+                 double* __restrict__ e_arr, const GlobalState* __restrict__ gs,
+                 int* __restrict__ u_idx, int* __restrict__ u_cnt, int N, int64_t n, int64_t lda) {
+  const int64_t r = static_cast<int64_t>(blockIdx.x) * kPrepBlock + threadIdx.x;
+  bool in_u = false;
+  if (r < n) {
+    double wr, c, e, tr;
+    in_u = prep_entry(x, u, r, lda, N, s[r], z[r], __double_as_longlong(gs->tau), wr, c, e, tr);
+    w[r] = wr;
+    c_arr[r] = c;
+    e_arr[r] = e;
+    tau_r[r] = tr;
+  }
+  block_list_append(in_u, static_cast<int>(r), u_idx + static_cast<int64_t>(blockIdx.x) * kPrepBlock,
+                    u_cnt + blockIdx.x);
 }
 
 // A path (several instances on one A, K = their count): the same per-entry work, written
 // instance-major (instance q's n entries contiguous, from q n), which is the layout its
-// consensus CTAs work on; x and u are feature-major (entry (c, q) at c K + q), s instance-major.
-static __global__ void k_consensus_prep_path(const double* __restrict__ x, const double* __restrict__ u,
-                                             const double* __restrict__ s_cm, double* __restrict__ w_cm,
-                                             double* __restrict__ tau_r, double* __restrict__ c_arr,
-                                             double* __restrict__ e_arr, int N, int64_t n, int K,
-                                             int64_t ldx) {
-  const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (r >= n * K) return;
-  const int64_t q = r / n, c = r - q * n, o = c * K + q;
-  double acc = 0.0;
-  for (int i = 0; i < N; ++i) acc += x[i * ldx + o] + u[i * ldx + o];
-  const double wr = acc / N;
-  w_cm[r] = wr;
-  const double sr = s_cm[r], sg = dsign(wr);
-  c_arr[r] = sr * wr - fabs(wr);
-  e_arr[r] = (sr - sg) * (sr - sg);
-  tau_r[r] = wr == 0.0 ? 0.0 : (sg * sr < 1.0 ? fabs(wr) / (1.0 - sg * sr) : HUGE_VAL);
+// consensus CTAs work on; x and u are feature-major (entry (c, q) at c K + q), s and z
+// instance-major.  Grid (blocks per instance, K); instance q's lists hold indices within
+// the instance, from q n (u_idx) and q gridDim.x (u_cnt).
+static __global__ void __launch_bounds__(kPrepBlock)
+k_consensus_prep_path(const double* __restrict__ x, const double* __restrict__ u,
+                      const double* __restrict__ s_cm, const double* __restrict__ z_cm,
+                      double* __restrict__ w_cm, double* __restrict__ tau_r,
+                      double* __restrict__ c_arr, double* __restrict__ e_arr,
+                      const GlobalState* __restrict__ gs, int* __restrict__ u_idx,
+                      int* __restrict__ u_cnt, int N, int64_t n, int K, int64_t ldx) {
+  const int q = blockIdx.y;
+  const int64_t c = static_cast<int64_t>(blockIdx.x) * kPrepBlock + threadIdx.x;
+  const int64_t r = static_cast<int64_t>(q) * n + c;
+  bool in_u = false;
+  if (c < n) {
+    double wr, cc, e, tr;
+    in_u = prep_entry(x, u, c * K + q, ldx, N, s_cm[r], z_cm[r], __double_as_longlong(gs[q].tau),
+                      wr, cc, e, tr);
+    w_cm[r] = wr;
+    c_arr[r] = cc;
+    e_arr[r] = e;
+    tau_r[r] = tr;
+  }
+  block_list_append(in_u, static_cast<int>(c),
+                    u_idx + static_cast<int64_t>(q) * n + static_cast<int64_t>(blockIdx.x) * kPrepBlock,
+                    u_cnt + static_cast<int64_t>(q) * gridDim.x + blockIdx.x);
 }
 
 // A path: the consensus CTAs' z and s (instance-major) to the feature-major layout the

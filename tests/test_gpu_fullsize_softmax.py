@@ -43,9 +43,11 @@ def run():
         for _ in range(6):                   # iterations 3..8
             s.step(1)
             cons.append(consensus_state(s))
+        lists = bc.get_trace(s.h)["zt_lists"]
     del A_t
     r0, r1 = synth.split_ranges(wl["m"], wl["N"])[0]
     A0 = synth.round_to_bf16(A[r0:r1]).astype(np.float64)
+    cons[0]["lists"] = lists
     return wl, b, A0, st1, st2, (r0, r1), cons
 
 
@@ -105,3 +107,17 @@ def test_consensus_against_oracle_iterations_3_to_8(run):
         taus.append(check_consensus_step(cons[k - 1], cons[k], wl["N"], wl["rho"], 0.5 * wl["rho"],
                                          wl["kappa"]))
     assert max(taus) > 0.0, "the l1 constraint was never active"
+
+
+def test_consensus_steps_3_to_8_ran_on_the_entry_lists(run):
+    """The checked steps are the warm-started list form (only the entries with a breakpoint
+    above the previous root or a nonzero z or s are visited) whenever the previous root is
+    positive and h stays non-positive there."""
+    *_, cons = run
+    lists = cons[0]["lists"]
+    taus = [c["tau"] for c in cons]
+    assert lists.size == len(cons) + 1  # iterations 1..8; cons starts at 2
+    assert lists[0] == 0  # iteration 1: tau_prev = 0
+    # cons[k] holds the state after iteration k + 2, whose record is lists[k + 1]
+    warm = [k for k in range(1, len(cons)) if taus[k - 1] > 0.0]
+    assert warm and sum(lists[k + 1] for k in warm) >= 0.5 * len(warm), (lists, taus)
