@@ -108,9 +108,11 @@ typedef struct {
   int32_t max_iters;     /* outer-iteration cap of bicadmm_solve()                      */
   int32_t check_every;   /* solve(): read residuals back every this many iterations     */
   double tol_rel;        /* solve(): stop when max(p_rel, d_rel, b_rel, i_rel) <= tol   */
-  int32_t pass_rows;     /* tuning: rows per staged panel of the A pass (0 = auto; 64 =
-                            the tensor-core pass of BF16 softmax, chosen by auto when
-                            n <= 2048; 8 = its CUDA-core pass)                         */
+  int32_t pass_rows;     /* tuning: rows per staged panel of the A pass (0 = auto; for
+                            BF16 storage with K > 1 and n <= 2048 the tensor-core pass:
+                            128 = on pairs of SMs (a two-CTA cluster splits the columns;
+                            chosen by auto when n > 128), 64 = on single SMs (chosen by
+                            auto when n <= 128); 8 = its CUDA-core pass)               */
   int32_t pass_stages;   /* tuning: panels in flight per CTA (0 = auto)                 */
 } bicadmm_params;
 

@@ -33,6 +33,7 @@
 #include "multiclass.cuh"
 #include "mc_tc.cuh"
 #include "objective.cuh"
+#include "mc_tc2.cuh"
 #include "gram_tf32.cuh"
 #include "pass.cuh"
 #include "polish.cuh"
@@ -84,6 +85,7 @@ struct bicadmm_ctx {
   int KC = 1;         // compile-time class bucket of the K > 1 kernels
   int64_t ldx = 0;    // n-space row stride, lda K
   bool use_tc = false;  // BF16 softmax: tensor-core A pass (k_fused_pass_tc)
+  bool tc2 = false;     // ... on pairs of SMs (k_fused_pass_tc2, 128-row panels)
   bool tf32 = false;    // BICADMM_PREC_TF32: 32-bit storage of A rounded to TF32 (p.precision
                         // then reads FP32, whose kernels serve it unchanged)
   // a sparsity path (bicadmm_create_path): K = ninst instances of one problem that differ in
@@ -367,7 +369,40 @@ int launch_pass_tc_c(bicadmm_ctx* h, bool with_consensus, int op, int* blocks) {
   return BICADMM_OK;
 }
 
+// The pair kernel; op 1 returns the number of co-resident clusters of two CTAs.
+template <int KC>
+int launch_pass_tc2_c(bicadmm_ctx* h, bool with_consensus, int op, int* blocks) {
+  auto kern = k_fused_pass_tc2<KC>;
+  CK(allow_max_dynamic_smem(kern));
+  if (op == 1) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(2 * static_cast<unsigned>(h->num_sms), 1, 1);
+    cfg.blockDim = dim3(kTc2Threads, 1, 1);
+    cfg.dynamicSmemBytes = h->pass_smem;
+    cfg.stream = h->stream;
+    CK(cudaOccupancyMaxActiveClusters(blocks, kern, &cfg));
+    return BICADMM_OK;
+  }
+  PassGeometry geo{h->d_shard_row0, h->d_panel_start, h->N, h->P_panels, -1};
+  const int ncons = with_consensus ? h->ninst : 0;
+  kern<<<2 * h->G + ((ncons + 1) & ~1), kTc2Threads, h->pass_smem, h->stream>>>(
+      h->tmap, h->lda, h->wpk, h->nslab, h->ldx, h->K,
+      static_cast<const float*>(h->b), static_cast<float*>(h->omega), static_cast<float*>(h->nu),
+      static_cast<float*>(h->slots), h->cta_stats, geo, static_cast<float>(h->M),
+      static_cast<float>(h->p.rho_l), h->p.newton_iters, h->d_err, kWaitLimitCycles,
+      consensus_args(h, with_consensus), h->path ? h->p.loss : -1);
+  CK(cudaGetLastError());
+  return BICADMM_OK;
+}
+
 int launch_pass_tc(bicadmm_ctx* h, bool wc, int op = 0, int* blocks = nullptr) {
+  if (h->tc2) {
+    switch (h->KC) {
+      case 4: return launch_pass_tc2_c<4>(h, wc, op, blocks);
+      case 10: return launch_pass_tc2_c<10>(h, wc, op, blocks);
+      case 16: return launch_pass_tc2_c<16>(h, wc, op, blocks);
+    }
+  }
   switch (h->KC) {
     case 4: return launch_pass_tc_c<4>(h, wc, op, blocks);
     case 10: return launch_pass_tc_c<10>(h, wc, op, blocks);
@@ -394,7 +429,7 @@ int make_tmap(bicadmm_ctx* h) {
   }
   const cuuint64_t dims[2] = {static_cast<cuuint64_t>(h->lda), static_cast<cuuint64_t>(h->p.m)};
   const cuuint64_t strides[1] = {static_cast<cuuint64_t>(h->lda) * 2};
-  const cuuint32_t box[2] = {64, static_cast<cuuint32_t>(kTcRows)};
+  const cuuint32_t box[2] = {64, static_cast<cuuint32_t>(h->tc2 ? kTc2Rows : kTcRows)};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = fn(&h->tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, h->A, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -658,7 +693,7 @@ int validate(const bicadmm_params* p, std::string& why) {
   if (p->inner_iters < 1 || p->newton_iters < 1) { why = "inner_iters and newton_iters must be >= 1"; return BICADMM_ERR_ARG; }
   if (p->max_iters < 0 || p->check_every < 1) { why = "max_iters >= 0 and check_every >= 1 required"; return BICADMM_ERR_ARG; }
   if (p->n * p->K > kMaxN) { why = "n K > 32768 is not supported by this build"; return BICADMM_ERR_UNSUPPORTED; }
-  if (p->pass_rows != 0 && p->pass_rows != 1 && p->pass_rows != 2 && p->pass_rows != 4 && p->pass_rows != 8 && p->pass_rows != 64) { why = "pass_rows must be 0, 1, 2, 4, 8 or 64"; return BICADMM_ERR_ARG; }
+  if (p->pass_rows != 0 && p->pass_rows != 1 && p->pass_rows != 2 && p->pass_rows != 4 && p->pass_rows != 8 && p->pass_rows != 64 && p->pass_rows != 128) { why = "pass_rows must be 0, 1, 2, 4, 8, 64 or 128"; return BICADMM_ERR_ARG; }
   if (p->pass_stages < 0 || p->pass_stages > 8) { why = "pass_stages must be in [0, 8]"; return BICADMM_ERR_ARG; }
   return BICADMM_OK;
 }
@@ -708,18 +743,24 @@ int build_geometry(bicadmm_ctx* h) {
   // A-pass panel geometry
   const size_t row_bytes = static_cast<size_t>(h->lda) * h->asz;
   int R = p.pass_rows;
-  // BF16 softmax rows of <= 2048 columns: tensor-core pass (64-row panels) unless 8-row
-  // CUDA-core panels are asked for.
+  // BF16 multi-column rows of <= 2048 columns: tensor-core pass unless 8-row CUDA-core
+  // panels are asked for; 128-row panels on pairs of SMs (k_fused_pass_tc2) when the row
+  // has at least two 128-column slabs, 64-row panels on single SMs when asked for
+  // (pass_rows 64) or the row is narrower.
   h->use_tc = h->K > 1 && p.precision == BICADMM_PREC_BF16 && h->lda <= 128 * kTcMaxSlabs &&
-              (R == 0 || R == kTcRows);
-  if (R == kTcRows && !h->use_tc) return fail(h, BICADMM_ERR_UNSUPPORTED, "64-row panels are the tensor-core pass (BF16 softmax, n <= 2048)");
+              (R == 0 || R == kTcRows || R == kTc2Rows);
+  h->tc2 = h->use_tc && R != kTcRows && h->lda > 128;
+  if ((R == kTcRows || R == kTc2Rows) && !h->use_tc)
+    return fail(h, BICADMM_ERR_UNSUPPORTED, "64- and 128-row panels are the tensor-core pass (BF16, K > 1, n <= 2048)");
+  if (R == kTc2Rows && !h->tc2)
+    return fail(h, BICADMM_ERR_UNSUPPORTED, "128-row panels need rows of more than 128 columns");
   if (h->K > 1 && !h->use_tc) {
     // Softmax pass: one CTA per SM (register tiles), 8-row panels, up to 4 stages in the
     // single-CTA budget.
     if (R != 0 && R != kPassRowsK) return fail(h, BICADMM_ERR_UNSUPPORTED, "the softmax A pass uses 8-row panels (pass_rows 0 or 8)");
     R = kPassRowsK;
   }
-  if (h->use_tc) R = kTcRows;
+  if (h->use_tc) R = h->tc2 ? kTc2Rows : kTcRows;
   // Auto (one class): the tallest panel (at most 8 rows) of at most 96 KB, so that two CTAs
   // fit an SM.  A panel of 32 KB or more gets one stage: the two CTAs of an SM alternate
   // between loading and computing, and a panel held in registers (FP32) has its stage reloaded
@@ -751,7 +792,7 @@ int build_geometry(bicadmm_ctx* h) {
   h->VPT = h->use_tc ? 1 : (h->K == 1 ? pick_vpt(nvec) : pick_vpt_k(nvec, ve, h->KC, h->esz));
   if (h->VPT < 0) return fail(h, BICADMM_ERR_UNSUPPORTED, "rows too wide for the register-resident A-pass accumulators");
   if (h->use_tc) {
-    h->pass_smem = fused_pass_tc_smem();
+    h->pass_smem = h->tc2 ? fused_pass_tc2_smem() : fused_pass_tc_smem();
     h->nslab = 2 * static_cast<int>((h->lda + kTcStageCols - 1) / kTcStageCols);  // even
   } else if (h->K > 1) {
     const int C = h->KC <= 4 ? 4 : 16;
@@ -786,8 +827,10 @@ int build_geometry(bicadmm_ctx* h) {
   }
   if (rc != BICADMM_OK) return rc;
   if (occ < 1) return fail(h, BICADMM_ERR_UNSUPPORTED, "A-pass variant cannot be resident on an SM");
-  // One resident slot is kept for each consensus CTA that rides on the last pass.
-  const int64_t slots_total = static_cast<int64_t>(occ) * h->num_sms - h->ninst;
+  // One resident slot is kept for each consensus CTA that rides on the last pass (the pair
+  // kernel: occ co-resident pairs, the consensus CTAs taking whole pairs).
+  const int64_t slots_total = h->tc2 ? static_cast<int64_t>(occ) - (h->ninst + 1) / 2
+                                     : static_cast<int64_t>(occ) * h->num_sms - h->ninst;
   if (slots_total < 1) return fail(h, BICADMM_ERR_UNSUPPORTED, "A-pass needs at least two resident CTAs");
   // At least 4 panels per CTA: a shard's A'd partial sums are spread over one slot per CTA
   // that touches it, and every x-update right-hand side sums them (small problems had

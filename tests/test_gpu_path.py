@@ -72,15 +72,16 @@ def test_path_objective_per_instance():
             assert abs(ps.info(q).objective - want) <= 1e-11 * abs(want), q
 
 
-def test_path_bf16_tensor_core_pass():
+@pytest.mark.parametrize("pass_rows", [64, 128])
+def test_path_bf16_tensor_core_pass(pass_rows):
     """BF16 storage, n <= 2048: the multi-column pass runs on the tensor cores (A X and A'D
-    as skinny GEMMs over the instances' columns)."""
+    as skinny GEMMs over the instances' columns), on single SMs (64) or SM pairs (128)."""
     import torch
     P = synth.small_problem(ref.LOSS_LOGISTIC, m=4000, n=192, nnz=10, N=3, M=2, kappa=10, seed=12)
     kappas = [4, 10, 16, 40]
     iters = 15
     with bc.PathSolver(P.A.astype(np.float32), P.b, loss=P.loss, N=P.N, M=P.M, kappas=kappas,
-                       gamma=P.gamma, rho_c=P.rho, precision=bc.PREC_BF16, pass_rows=64,
+                       gamma=P.gamma, rho_c=P.rho, precision=bc.PREC_BF16, pass_rows=pass_rows,
                        stream=torch.cuda.current_stream()) as ps:
         ps.step(iters)
         orcs = _oracles(P, kappas, iters, A=synth.round_to_bf16(P.A))

@@ -69,12 +69,26 @@ def test_softmax_bf16_vs_oracle_on_rounded_A(pass_rows):
     (5000, 130, 16, 5, 2, 50, 10),      # 16 classes, one partial slab
     (3000, 200, 10, 40, 2, 20, 6),      # 75-row shards: a full and an 11-row panel each
 ])
-def test_softmax_bf16_tensor_core_pass(case):
+@pytest.mark.parametrize("pass_rows", [64, 128])
+def test_softmax_bf16_tensor_core_pass(case, pass_rows):
+    """64: single-SM kernel (64-row panels); 128: the pair kernel (two-CTA clusters split the
+    columns: 16 slabs 8 / 8, 3 slabs 2 / 1, 2 slabs of which the second is mostly padding)."""
     m, n, K, N, M, kappa, iters = case
     P = synth.sparse_softmax(m=m, n=n, K=K, nnz=kappa, N=N, M=M, kappa=kappa, seed=13)
     Ab = synth.round_to_bf16(P.A)
-    st, _ = run_gpu(P, iters, precision=bc.PREC_BF16, A=P.A, pass_rows=64)
+    st, _ = run_gpu(P, iters, precision=bc.PREC_BF16, A=P.A, pass_rows=pass_rows)
     compare_state(st, run_oracle(P, iters, A=Ab), TOL32)
+
+
+def test_pair_pass_needs_two_slabs():
+    """128-row panels split the row's 128-column slabs between two CTAs: rows of at most 128
+    columns are refused (auto takes the single-SM kernel there)."""
+    P = synth.sparse_softmax(m=500, n=100, K=4, nnz=10, N=2, M=2, kappa=10, seed=3)
+    with pytest.raises(bc.BicadmmError) as e:
+        run_gpu(P, 2, precision=bc.PREC_BF16, A=P.A, pass_rows=128)
+    assert e.value.code == -7
+    st, _ = run_gpu(P, 6, precision=bc.PREC_BF16, A=P.A)
+    compare_state(st, run_oracle(P, 6, A=synth.round_to_bf16(P.A)), TOL32)
 
 
 @pytest.mark.parametrize("loss", [ref.LOSS_SQUARED, ref.LOSS_LOGISTIC, ref.LOSS_SQHINGE])
