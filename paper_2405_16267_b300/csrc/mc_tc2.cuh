@@ -107,6 +107,22 @@ __device__ __forceinline__ bool mbar_wait_cluster_or_abort(uint64_t* bar, uint32
   return true;
 }
 
+// The shard table entries a CTA's panels need (first panel and first row of shards
+// base .. base + count - 1), in shared memory when they fit: every panel lookup of the three
+// roles then reads shared memory instead of chasing global loads.
+constexpr int kTc2GeoCache = 66;
+struct Tc2Geo {
+  const int64_t* ps;  // panel_start[base ...]
+  const int64_t* r0;  // shard_row0[base ...]
+  int base, N;
+  __device__ void locate(int64_t p, int& i, int64_t& row0, int& nrows) const {
+    while (i + 1 < N && ps[i + 1 - base] <= p) ++i;
+    row0 = r0[i - base] + (p - ps[i - base]) * kTc2Rows;
+    const int64_t rem = r0[i + 1 - base] - row0;
+    nrows = rem < kTc2Rows ? static_cast<int>(rem) : kTc2Rows;
+  }
+};
+
 // ------------------------------------------------------------------ k_fused_pass_tc2
 // Grid: 2 G panel CTAs (G pairs, a pair = one cluster) and, on the last sweep, the
 // consensus CTAs (one per instance, their count rounded up to even; a spare one returns).
@@ -148,12 +164,34 @@ k_fused_pass_tc2(const __grid_constant__ CUtensorMap tmap, int64_t lda,
   double* xstat = reinterpret_cast<double*>(counts + 2);            // [3] rank 1's row sums
   float* red = reinterpret_cast<float*>(xstat + 4);                 // [4 warps][3]
 
+  __shared__ int64_t geo_ps[kTc2GeoCache], geo_r0[kTc2GeoCache];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t rank = cluster_ctarank(), partner = rank ^ 1u;
   const int pair = static_cast<int>(blockIdx.x) >> 1, G = npc >> 1;
   const int64_t p_begin = static_cast<int64_t>(pair) * geo.P / G;
   const int64_t p_end = static_cast<int64_t>(pair + 1) * geo.P / G;
   const int np = static_cast<int>(p_end - p_begin);
+  // shards of this pair's first and last panels (binary search over the shards' first panels)
+  auto shard_search = [&](int64_t p) {
+    int lo = 0, hi = geo.N - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (geo.panel_start[mid] <= p) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+  };
+  const int shard0 = shard_search(p_begin);
+  const int shard1 = np > 0 ? shard_search(p_end - 1) : shard0;
+  const int ncache = shard1 - shard0 + 2;  // entries shard0 .. shard1 + 1 (<= N)
+  const bool cached = ncache <= kTc2GeoCache;
+  if (cached) {
+    for (int i = tid; i < ncache; i += blockDim.x) {
+      geo_ps[i] = geo.panel_start[shard0 + i];
+      geo_r0[i] = geo.shard_row0[shard0 + i];
+    }
+  }
+  const Tc2Geo gv{cached ? geo_ps : geo.panel_start, cached ? geo_r0 : geo.shard_row0,
+                  cached ? shard0 : 0, geo.N};
   // this CTA's slabs: the first ceil(n/2) 128-column slabs for rank 0, the rest for rank 1
   const int nsl_all = static_cast<int>((lda + 127) / 128), h0 = (nsl_all + 1) / 2;
   const int sl0 = rank ? h0 : 0, nsl = rank ? nsl_all - h0 : h0;
@@ -186,17 +224,8 @@ k_fused_pass_tc2(const __grid_constant__ CUtensorMap tmap, int64_t lda,
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  int shard0 = 0;
-  {
-    int lo = 0, hi = geo.N - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (geo.panel_start[mid] <= p_begin) lo = mid; else hi = mid - 1;
-    }
-    shard0 = lo;
-  }
   auto panel_at = [&](int k, int& hint, int64_t& row0, int& nrows) {
-    locate_panel<kTc2Rows>(geo, p_begin + k, hint, row0, nrows);
+    gv.locate(p_begin + k, hint, row0, nrows);
   };
   auto shard_of = [&](int k) -> int {
     if (k < 0 || k >= np) return -1;
