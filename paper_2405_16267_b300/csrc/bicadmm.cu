@@ -792,7 +792,7 @@ int build_geometry(bicadmm_ctx* h) {
   h->VPT = h->use_tc ? 1 : (h->K == 1 ? pick_vpt(nvec) : pick_vpt_k(nvec, ve, h->KC, h->esz));
   if (h->VPT < 0) return fail(h, BICADMM_ERR_UNSUPPORTED, "rows too wide for the register-resident A-pass accumulators");
   if (h->use_tc) {
-    h->pass_smem = h->tc2 ? fused_pass_tc2_smem() : fused_pass_tc_smem();
+    h->pass_smem = h->tc2 ? fused_pass_tc2_smem(h->KC) : fused_pass_tc_smem();
     h->nslab = 2 * static_cast<int>((h->lda + kTcStageCols - 1) / kTcStageCols);  // even
   } else if (h->K > 1) {
     const int C = h->KC <= 4 ? 4 : 16;

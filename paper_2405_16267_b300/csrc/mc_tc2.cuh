@@ -41,7 +41,11 @@ namespace bic {
 
 constexpr int kTc2Rows = 128;                       // panel rows (the forward's M)
 constexpr int kTc2Threads = 256;
-constexpr int kTc2Stages = 4;
+// ring stages: 4 of 40 KB, 3 for 16 classes (whose staged row data take 12 KB more)
+template <int KC>
+__host__ __device__ constexpr int tc2_stages() { return KC > 10 ? 3 : 4; }
+// one panel's row data staged by the loader warps: nu and omega (KC floats a row) and b
+__host__ __device__ constexpr int tc2_row_bytes(int KC) { return (2 * 128 * KC + 128) * 4; }
 constexpr int kTc2BoxBytes = kTc2Rows * 128;        // a 64-column x 128-row BF16 box: 16 KB
 constexpr int kTc2StageABytes = 2 * kTc2BoxBytes;   // one 128-column slab
 constexpr int kTc2WBytes = 2 * 4096;                // its W tile: [box] 32 x 64 BF16 (hi | lo)
@@ -52,10 +56,12 @@ constexpr int kTc2XBytes = kTc2Rows * 16 * 4;       // partial row dots: 128 row
 constexpr int kTc2TmemCols = 512;                   // D1 x2 at 0 / 32, D2 slab s at 64 + 32 s
 constexpr int kTc2D2Col = 64;
 
-inline size_t fused_pass_tc2_smem() {
-  // alignment, ring, two d tiles, two exchange buffers, barriers and scalars
-  return 1024 + static_cast<size_t>(kTc2Stages) * kTc2StageBytes + 2 * kTc2DBytes +
-         2 * kTc2XBytes + 512;
+inline size_t fused_pass_tc2_smem(int KC) {
+  // alignment, ring, two d tiles, two exchange buffers, two row-data buffers, barriers and
+  // scalars
+  const int S = KC > 10 ? tc2_stages<16>() : tc2_stages<10>();
+  return 1024 + static_cast<size_t>(S) * kTc2StageBytes + 2 * kTc2DBytes + 2 * kTc2XBytes +
+         2 * static_cast<size_t>(tc2_row_bytes(KC)) + 512;
 }
 
 // ------------------------------------------------------------------ cluster PTX wrappers
@@ -78,6 +84,16 @@ __device__ __forceinline__ void st_cluster_v4(uint32_t raddr, float a, float b, 
   asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(raddr), "f"(a), "f"(b),
                "f"(c), "f"(d)
                : "memory");
+}
+// Store 16 bytes into another CTA's shared memory, completing as 16 transaction bytes on that
+// CTA's barrier at rbar (no fence: the barrier's phase carries the data).
+__device__ __forceinline__ void st_async_v4(uint32_t raddr, float a, float b, float c, float d,
+                                            uint32_t rbar) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
+          raddr),
+      "f"(a), "f"(b), "f"(c), "f"(d), "r"(rbar)
+      : "memory");
 }
 __device__ __forceinline__ void st_cluster_f64(uint32_t raddr, double a) {
   asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(raddr), "d"(a) : "memory");
@@ -142,7 +158,8 @@ k_fused_pass_tc2(const __grid_constant__ CUtensorMap tmap, int64_t lda,
     if (q < ncons) consensus_block<kTc2Threads, kConsMW, true>(consensus_instance(cons, q), smem_raw);
     return;
   }
-  constexpr int S = kTc2Stages;
+  constexpr int S = tc2_stages<KC>();
+  constexpr int RB = tc2_row_bytes(KC);
   constexpr uint32_t IDESC_FWD = idesc_bf16(128, 32, false, false);
   constexpr uint32_t IDESC_BWD = idesc_bf16(128, 32, true, false);
   unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -150,7 +167,8 @@ k_fused_pass_tc2(const __grid_constant__ CUtensorMap tmap, int64_t lda,
   unsigned char* ring = base;
   unsigned char* ds = ring + S * kTc2StageBytes;   // [2] d tiles
   float* xbuf = reinterpret_cast<float*>(ds + 2 * kTc2DBytes);  // [2][128][16] partner's partials
-  uint64_t* full = reinterpret_cast<uint64_t*>(xbuf + 2 * kTc2Rows * 16);
+  unsigned char* rows = reinterpret_cast<unsigned char*>(xbuf + 2 * kTc2Rows * 16);  // [2] row data
+  uint64_t* full = reinterpret_cast<uint64_t*>(rows + 2 * RB);
   uint64_t* empty = full + S;
   uint64_t* d1full = empty + S;   // [2]
   uint64_t* dready = d1full + 2;  // [2]
@@ -158,7 +176,9 @@ k_fused_pass_tc2(const __grid_constant__ CUtensorMap tmap, int64_t lda,
   uint64_t* flushed = bwddone + 1;
   uint64_t* drainbar = flushed + 1;
   uint64_t* xfull = drainbar + 1;  // [2] the partner's 128 rows of partials have arrived
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(xfull + 2);
+  uint64_t* rowfull = xfull + 2;   // [2] a panel's row data are staged
+  uint64_t* rowfree = rowfull + 2; // [2] the epilogue has read them
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(rowfree + 2);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   long long* counts = reinterpret_cast<long long*>(tmem_slot + 2);  // [0] issued, [1] consumed
   double* xstat = reinterpret_cast<double*>(counts + 2);            // [3] rank 1's row sums
@@ -211,6 +231,10 @@ k_fused_pass_tc2(const __grid_constant__ CUtensorMap tmap, int64_t lda,
     mbar_init(drainbar, 1);
     mbar_init(&xfull[0], 128);
     mbar_init(&xfull[1], 128);
+    mbar_init(&rowfull[0], 64);
+    mbar_init(&rowfull[1], 64);
+    mbar_init(&rowfree[0], 128);
+    mbar_init(&rowfree[1], 128);
     *abort_flag = 0;
     counts[0] = counts[1] = 0;
     fence_barrier_init();
@@ -341,6 +365,47 @@ k_fused_pass_tc2(const __grid_constant__ CUtensorMap tmap, int64_t lda,
       if (!okk) *abort_v = 1;
       return okk;
     });
+  } else if (warp >= 6) {
+    // ---------------------------------------------------------------- row-data loaders
+    // nu, omega (K floats a row, contiguous over the panel) and b of the panels ahead, into
+    // two shared-memory buffers; the epilogue releases a buffer once it has read its row.
+    const int lt = tid - 192;  // 0..63
+    int hint = shard0;
+    for (int k = 0; k < np; ++k) {
+      const int buf = k & 1;
+      if (k >= 2 && !mbar_wait_or_abort(&rowfree[buf], static_cast<uint32_t>(((k - 2) >> 1) & 1), wait_limit, abort_v)) {
+        *abort_v = 1;
+        break;
+      }
+      int64_t row0;
+      int nr;
+      panel_at(k, hint, row0, nr);
+      float* rnu = reinterpret_cast<float*>(rows + buf * RB);
+      float* rom = rnu + kTc2Rows * KC;
+      float* rbv = rom + kTc2Rows * KC;
+      const float* snu = nu + row0 * K;
+      const float* som = omega + row0 * K;
+      const int cnt = nr * K;
+      for (int i0 = lt; i0 < cnt; i0 += 4 * 64) {
+        float va[4], vb[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + 64 * u;
+          va[u] = i < cnt ? snu[i] : 0.f;
+          vb[u] = i < cnt ? som[i] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + 64 * u;
+          if (i < cnt) {
+            rnu[i] = va[u];
+            rom[i] = vb[u];
+          }
+        }
+      }
+      for (int i = lt; i < nr; i += 64) rbv[i] = b[row0 + i];
+      mbar_arrive(&rowfull[buf]);
+    }
   } else if (warp < 4) {
     // ---------------------------------------------------------------- epilogue warps
     const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
@@ -348,36 +413,18 @@ k_fused_pass_tc2(const __grid_constant__ CUtensorMap tmap, int64_t lda,
     const bool own_row = (r >> 6) == static_cast<int>(rank);  // omega, nu and sums of this row
     const uint32_t x_remote0 = mapa_shared(smem_addr(xbuf + r * 16), partner);
     const uint32_t xfull_remote0 = mapa_shared(smem_addr(&xfull[0]), partner);
+    const float invM = 1.f / Mf;
     int seg = 0;
     bool eok = true;
     int hint = shard0;
-    float nur[KC], wv[KC];
-    int y = 0;
-    float yb = 0.f;
-    auto prefetch = [&](int k) {
-      int64_t row0 = 0;
-      int nrows = 0;
-      if (k < np) {
-        int h = shard0;
-        panel_at(k, h, row0, nrows);
-      }
-      const bool valid = k < np && r < nrows;
-#pragma unroll
-      for (int q = 0; q < KC; ++q) {
-        nur[q] = (valid && q < K) ? nu[(row0 + r) * K + q] : 0.f;
-        wv[q] = (valid && q < K) ? omega[(row0 + r) * K + q] : 0.f;
-      }
-      y = valid ? static_cast<int>(b[row0 + r]) : 0;
-      yb = valid ? b[row0 + r] : 0.f;
-    };
-    prefetch(0);
     for (int k = 0; k < np && eok; ++k) {
       int64_t row0;
       int nrows;
       panel_at(k, hint, row0, nrows);
       const int shard = hint;
       const int buf = k & 1;
-      if (!mbar_wait_or_abort(&d1full[buf], static_cast<uint32_t>((k >> 1) & 1), wait_limit, abort_v)) { eok = false; break; }
+      const uint32_t par = static_cast<uint32_t>((k >> 1) & 1);
+      if (!mbar_wait_or_abort(&d1full[buf], par, wait_limit, abort_v)) { eok = false; break; }
       tc_fence_after();
       uint32_t v[16], vl[16];
       tmem_ld16(tmem + lane_base + 32 * buf, v);
@@ -385,27 +432,50 @@ k_fused_pass_tc2(const __grid_constant__ CUtensorMap tmap, int64_t lda,
       float part[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) part[q] = __uint_as_float(v[q]) + __uint_as_float(vl[q]);
-      // this CTA's partial row dots into the partner's buffer, then its barrier
-      const uint32_t xr = x_remote0 + buf * kTc2XBytes;
+      // expect the partner's 64 bytes for this row, then send ours (they complete on its barrier)
+      mbar_arrive_expect_tx(&xfull[buf], 64);
+      const uint32_t xr = x_remote0 + buf * kTc2XBytes, xb = xfull_remote0 + buf * 8;
 #pragma unroll
-      for (int q = 0; q < 16; q += 4) st_cluster_v4(xr + q * 4, part[q], part[q + 1], part[q + 2], part[q + 3]);
-      mbar_arrive_remote(xfull_remote0 + buf * 8);
-      if (!mbar_wait_cluster_or_abort(&xfull[buf], static_cast<uint32_t>((k >> 1) & 1), wait_limit, abort_v)) { eok = false; break; }
-      const float* xp = xbuf + buf * kTc2Rows * 16 + r * 16;
+      for (int q = 0; q < 16; q += 4) st_async_v4(xr + q * 4, part[q], part[q + 1], part[q + 2], part[q + 3], xb);
+      // this panel's row data
       const bool valid = r < nrows;
-      float Axb[KC], aa[KC], w[KC], nk[KC];
-      const int yk = y;
-      const float ybk = yb;
+      if (!mbar_wait_or_abort(&rowfull[buf], par, wait_limit, abort_v)) { eok = false; break; }
+      float nk[KC], w[KC];
+      int yk = 0;
+      float ybk = 0.f;
+      {
+        const float* rnu = reinterpret_cast<const float*>(rows + buf * RB);
+        const float* rom = rnu + kTc2Rows * KC;
+        const float* rbv = rom + kTc2Rows * KC;
+#pragma unroll
+        for (int q = 0; q < KC; ++q) {
+          nk[q] = (valid && q < K) ? rnu[r * K + q] : 0.f;
+          w[q] = (valid && q < K) ? rom[r * K + q] : 0.f;
+        }
+        ybk = valid ? rbv[r] : 0.f;
+        yk = static_cast<int>(ybk);
+      }
+      mbar_arrive(&rowfree[buf]);
+      if (!mbar_wait_cluster_or_abort(&xfull[buf], par, wait_limit, abort_v)) { eok = false; break; }
+      float other[16];
+      {
+        const float4* xp = reinterpret_cast<const float4*>(xbuf + buf * kTc2Rows * 16 + r * 16);
+#pragma unroll
+        for (int c4 = 0; c4 < 4; ++c4) {
+          const float4 t4 = xp[c4];
+          other[4 * c4 + 0] = t4.x;
+          other[4 * c4 + 1] = t4.y;
+          other[4 * c4 + 2] = t4.z;
+          other[4 * c4 + 3] = t4.w;
+        }
+      }
+      float Axb[KC], aa[KC];
 #pragma unroll
       for (int q = 0; q < KC; ++q) {
-        const float other = xp[q];
         // rank order: both CTAs form the same sum
-        Axb[q] = (rank == 0 ? part[q] + other : other + part[q]) / Mf;
-        nk[q] = nur[q];
-        w[q] = wv[q];
+        Axb[q] = (rank == 0 ? part[q] + other[q] : other[q] + part[q]) * invM;
         aa[q] = Axb[q] + nk[q];
       }
-      prefetch(k + 1);  // the next panel's rows: the loads overlap the prox
       if (valid) {
         if (path_loss < 0) {
           softmax_prox_row<KC>(w, aa, yk, K, Mf, rho_l, newton_iters);
