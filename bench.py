@@ -167,21 +167,22 @@ class ClockSampler:
 # DRAM traffic of one pass launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of a 20000-row launch of the same kernel, scaled by rows to the
 # 200000-row launch.  Reported only while the kernel sources are the captured ones.
-PASS_TRAFFIC = {"sources_sha256": "6234c825340d3eca3ae24daa693e4da9772079735f7c7a85f0118a825418429f", "bytes_per_launch": 4.0490e+09,
+PASS_TRAFFIC = {"sources_sha256": "495bc488df9731928980879c8ab46f4d0954380d7e8fa097e2a382ab3c1b1156", "bytes_per_launch": 4.0525e+09,
                 "capture": "profiles/k_fused_pass_sparse_logistic_200000x5000_fp32.md"}
 PASS_SOURCES = ["paper_2405_16267_b300/csrc/pass.cuh", "paper_2405_16267_b300/csrc/nspace.cuh",
                 "paper_2405_16267_b300/csrc/common.cuh"]
 
 
 # The same for the tensor-core softmax pass (60000-row capture scaled to 500000 rows).
-TC_TRAFFIC = {"sources_sha256": "3431c4620b268f7c867ce0869d7721a15ad16dd3c0067029c07113c33634fcb4", "bytes_per_launch": 2.4525e+09,
+TC_TRAFFIC = {"sources_sha256": "b3166aca059dfe4c2e8d42e393fb6e4cee95da46b68099a2460b9df62d56a709", "bytes_per_launch": 2.5740e+09,
               "capture": "profiles/k_fused_pass_tc_sparse_softmax_500000x2000x10_bf16.md"}
-TC_SOURCES = ["paper_2405_16267_b300/csrc/mc_tc.cuh", "paper_2405_16267_b300/csrc/nspace.cuh",
-              "paper_2405_16267_b300/csrc/common.cuh", "paper_2405_16267_b300/csrc/pass.cuh"]
+TC_SOURCES = ["paper_2405_16267_b300/csrc/mc_tc2.cuh", "paper_2405_16267_b300/csrc/mc_tc.cuh",
+              "paper_2405_16267_b300/csrc/nspace.cuh", "paper_2405_16267_b300/csrc/common.cuh",
+              "paper_2405_16267_b300/csrc/pass.cuh"]
 
 # The same kernel on the sparsity path (10 logistic instances as its columns; 60000-row
 # capture scaled to 500000 rows).
-PATH_TRAFFIC = {"sources_sha256": "3431c4620b268f7c867ce0869d7721a15ad16dd3c0067029c07113c33634fcb4", "bytes_per_launch": 2.4435e+09,
+PATH_TRAFFIC = {"sources_sha256": "b3166aca059dfe4c2e8d42e393fb6e4cee95da46b68099a2460b9df62d56a709", "bytes_per_launch": 2.4160e+09,
                 "capture": "profiles/k_fused_pass_tc_logistic_path10_500000x2000_bf16.md"}
 
 
@@ -462,7 +463,7 @@ def run_softmax(args, rank, world):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm,
                      "traffic": pass_traffic(TC_TRAFFIC, TC_SOURCES) if wl["m"] == SOFTMAX["m"] else None,
-                     "kernel": "k_fused_pass_tc",
+                     "kernel": "k_fused_pass_tc2",
                      "peak_kind": peak_kind + " copy bandwidth",
                      "algorithmic_bytes_per_launch": pass_bytes, "avg_launch_ms": avg_pass_s * 1e3,
                      "launches_timed": pass_launches},
@@ -473,7 +474,7 @@ def run_softmax(args, rank, world):
 
 def softmax_leg(args):
     """The softmax workload's figures (tensor-core pass), measured in the default run so they
-    appear beside the headline: its own value, roofline of k_fused_pass_tc and end to end."""
+    appear beside the headline: its own value, roofline of k_fused_pass_tc2 and end to end."""
     import copy
     a = copy.copy(args)
     a.steps = min(args.steps, 300)
@@ -562,7 +563,7 @@ def run_path(args, rank, world):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm,
                      "traffic": pass_traffic(PATH_TRAFFIC, TC_SOURCES) if m == PATH["m"] else None,
-                     "kernel": "k_fused_pass_tc",
+                     "kernel": "k_fused_pass_tc2",
                      "peak_kind": peak_kind + " copy bandwidth",
                      "algorithmic_bytes_per_launch": pass_bytes, "avg_launch_ms": avg_pass_s * 1e3,
                      "launches_timed": pass_launches},
