@@ -851,9 +851,9 @@ int build_geometry(bicadmm_ctx* h) {
     h->slot_hi[i] = owner(h->panel_start[i + 1] - 1) + i;
   }
   h->nslots = h->G + h->N;
-  // CTAs per shard of k_dual (each loops over its columns): at most 8, so that few CTAs
-  // take part in the last-CTA ticket
-  h->dual_chunks = static_cast<int>(std::min<int64_t>(8, (h->ldx + kDualThreads - 1) / kDualThreads));
+  // CTAs per shard of k_dual (each loops over its columns): at most 32, so that a thread has
+  // a few columns (their loads are latency-bound) and the last-CTA ticket stays short
+  h->dual_chunks = static_cast<int>(std::min<int64_t>(32, (h->ldx + kDualThreads - 1) / kDualThreads));
   return BICADMM_OK;
 }
 

@@ -33,7 +33,7 @@ __global__ void k_check_labels(const TM* __restrict__ b, int64_t m, int K, int* 
 }
 
 // ------------------------------------------------------------------------------ k_xupd_k
-// Grid (row tiles of ROWS, M, N), XT threads, one warp per row of P_ij.  R_ij (n_j x K) is
+// Grid (row tiles of ROWS, M, N), XT threads, a warp on RB rows of P_ij at a time.  R_ij (n_j x K) is
 // read in its own (column-major-in-K) order and staged transposed in shared memory,
 // [KC][ldp + 4] (zero padded; the 4-element pad spreads the transposing stores over the
 // banks), so a lane reads the K values of its VE consecutive columns as K 16-byte loads;
@@ -58,48 +58,76 @@ k_xupd_k(const TP* __restrict__ P, const int64_t* __restrict__ P_off,
   for (int e = threadIdx.x; e < lds * KC; e += XT) rs[e] = TP(0);
   __syncthreads();
   const double* rsrc = r + i * ldx + static_cast<int64_t>(col0) * K;
-  for (int e = threadIdx.x; e < nj * K; e += XT) {  // contiguous reads
-    const int bq = e / K, k = e - bq * K;
-    rs[k * lds + bq] = static_cast<TP>(rsrc[e]);
+  const int tot = nj * K;
+  for (int e0 = threadIdx.x; e0 < tot; e0 += 4 * XT) {  // contiguous reads, four in flight
+    double v4[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v4[u] = e0 + u * XT < tot ? rsrc[e0 + u * XT] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + u * XT;
+      if (e < tot) {
+        const int bq = e / K, k = e - bq * K;
+        rs[k * lds + bq] = static_cast<TP>(v4[u]);
+      }
+    }
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const TP* Pb = P + P_off[i * M + j];
   const int nv = ldp / VE;
-  for (int row = row_begin + warp; row < row_begin + ROWS && row < nj; row += XT / 32) {
-    const V* pr = reinterpret_cast<const V*>(Pb + static_cast<int64_t>(row) * ldp);
-    TP acc[C];
+  // RB rows of P per warp pass: every R vector read from shared memory feeds RB rows (one
+  // read per RB rows instead of per row, which made shared memory the bound)
+  constexpr int RB = sizeof(TP) == 8 ? 2 : 4;
+  for (int rb = row_begin + warp * RB; rb < row_begin + ROWS && rb < nj; rb += (XT / 32) * RB) {
+    const V* pr[RB];
 #pragma unroll
-    for (int k = 0; k < C; ++k) acc[k] = TP(0);
+    for (int t = 0; t < RB; ++t)
+      pr[t] = reinterpret_cast<const V*>(Pb + static_cast<int64_t>(rb + t < nj ? rb + t : rb) * ldp);
+    TP accs[RB][C];
+#pragma unroll
+    for (int t = 0; t < RB; ++t)
+#pragma unroll
+      for (int k = 0; k < C; ++k) accs[t][k] = TP(0);
     for (int bv = lane; bv < nv; bv += 32) {
-      const V pv = pr[bv];
-      const TP* pe = reinterpret_cast<const TP*>(&pv);
+      V pv[RB];
+#pragma unroll
+      for (int t = 0; t < RB; ++t) pv[t] = pr[t][bv];
 #pragma unroll
       for (int k = 0; k < KC; ++k) {
         const V rv = reinterpret_cast<const V*>(rs + k * lds)[bv];
         const TP* re = reinterpret_cast<const TP*>(&rv);
 #pragma unroll
-        for (int e = 0; e < VE; ++e) acc[k] = fma(pe[e], re[e], acc[k]);
+        for (int t = 0; t < RB; ++t) {
+          const TP* pe = reinterpret_cast<const TP*>(&pv[t]);
+#pragma unroll
+          for (int e = 0; e < VE; ++e) accs[t][k] = fma(pe[e], re[e], accs[t][k]);
+        }
       }
     }
-    const TP sum = warp_reduce_scatter<C>(acc, lane);
-    const int q = (lane >> (5 - (C == 4 ? 2 : (C == 8 ? 3 : 4)))) & (C - 1);
-    if ((lane & ((32 / C) - 1)) == 0 && q < K) {
-      const int64_t o = i * ldx + static_cast<int64_t>(col0 + row) * K + q;
-      const double xn = x[o] + static_cast<double>(sum);
-      x[o] = xn;
-      xlo[o] = static_cast<TP>(xn);
-      if (wpk) {
-        // the same entry as BF16 hi/lo in the tensor-core pass's W tiles: per shard, per
-        // 64-column box a 32 x 64 tile (rows 0-15 hi of the classes, 16-31 lo), 128-byte
-        // swizzle; boxes in column order (two per 128-column slab)
-        const int col = col0 + row;
-        const float v = static_cast<float>(xn);
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-        unsigned char* t = wpk + (static_cast<int64_t>(i) * nslab * 2 + (col >> 6)) * 4096;
-        *reinterpret_cast<__nv_bfloat16*>(t + sw128_off(q, col & 63)) = hi;
-        *reinterpret_cast<__nv_bfloat16*>(t + sw128_off(q + 16, col & 63)) = lo;
+#pragma unroll
+    for (int tr = 0; tr < RB; ++tr) {
+      const int row = rb + tr;
+      if (row >= nj) break;  // warp-uniform
+      const TP sum = warp_reduce_scatter<C>(accs[tr], lane);
+      const int q = (lane >> (5 - (C == 4 ? 2 : (C == 8 ? 3 : 4)))) & (C - 1);
+      if ((lane & ((32 / C) - 1)) == 0 && q < K) {
+        const int64_t o = i * ldx + static_cast<int64_t>(col0 + row) * K + q;
+        const double xn = x[o] + static_cast<double>(sum);
+        x[o] = xn;
+        xlo[o] = static_cast<TP>(xn);
+        if (wpk) {
+          // the same entry as BF16 hi/lo in the tensor-core pass's W tiles: per shard, per
+          // 64-column box a 32 x 64 tile (rows 0-15 hi of the classes, 16-31 lo), 128-byte
+          // swizzle; boxes in column order (two per 128-column slab)
+          const int col = col0 + row;
+          const float v = static_cast<float>(xn);
+          const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+          const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+          unsigned char* t = wpk + (static_cast<int64_t>(i) * nslab * 2 + (col >> 6)) * 4096;
+          *reinterpret_cast<__nv_bfloat16*>(t + sw128_off(q, col & 63)) = hi;
+          *reinterpret_cast<__nv_bfloat16*>(t + sw128_off(q + 16, col & 63)) = lo;
+        }
       }
     }
   }

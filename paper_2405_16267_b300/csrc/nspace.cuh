@@ -915,18 +915,37 @@ k_dual(double* __restrict__ u, const double* __restrict__ x, const double* __res
   __shared__ bool last;
   const int i = blockIdx.y, nch = gridDim.x;
   double a[2] = {0.0, 0.0};
-  // each CTA takes the columns blockIdx.x * DT + tid + k * nch * DT of its shard
-  for (int64_t col = static_cast<int64_t>(blockIdx.x) * DT + threadIdx.x; col < lda;
-       col += static_cast<int64_t>(nch) * DT) {
-    const int64_t o = i * lda + col;
-    const double xv = x[o], zv = z[col], dv = xv - zv;
-    const double un = u[o] + dv;
-    u[o] = un;
-    TM q = TM(0);  // the slots are partial sums in the arithmetic type of the pass
-    for (int sl = slot_lo[i]; sl <= slot_hi[i]; ++sl) q += slots[sl * lda + col];
-    r[o] = rho_l * static_cast<double>(q) + rho_c * (zv - un) - c0 * xv;
-    a[0] += dv * dv;  // padding columns hold zeros
-    a[1] += xv * xv;
+  // each CTA takes the columns blockIdx.x * DT + tid + k * nch * DT of its shard, two per
+  // step with all their loads issued before use (the loop is latency-bound)
+  const int s_lo = slot_lo[i], s_hi = slot_hi[i];
+  const int64_t stride = static_cast<int64_t>(nch) * DT;
+  for (int64_t c0l = static_cast<int64_t>(blockIdx.x) * DT + threadIdx.x; c0l < lda; c0l += 2 * stride) {
+    double xv[2], zv[2], uv[2];
+    TM q[2] = {TM(0), TM(0)};  // the slots are partial sums in the arithmetic type of the pass
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t col = c0l + h * stride;
+      const bool ok = col < lda;
+      const int64_t o = i * lda + (ok ? col : 0);
+      xv[h] = ok ? x[o] : 0.0;
+      zv[h] = ok ? z[col] : 0.0;
+      uv[h] = ok ? u[o] : 0.0;
+      if (ok)
+        for (int sl = s_lo; sl <= s_hi; ++sl) q[h] += slots[sl * lda + col];
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t col = c0l + h * stride;
+      if (col < lda) {
+        const int64_t o = i * lda + col;
+        const double dv = xv[h] - zv[h];
+        const double un = uv[h] + dv;
+        u[o] = un;
+        r[o] = rho_l * static_cast<double>(q[h]) + rho_c * (zv[h] - un) - c0 * xv[h];
+        a[0] += dv * dv;  // padding columns hold zeros
+        a[1] += xv[h] * xv[h];
+      }
+    }
   }
   block_sum<2>(a, red);
   if (threadIdx.x == 0) {
