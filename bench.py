@@ -175,7 +175,7 @@ PASS_SOURCES = ["paper_2405_16267_b300/csrc/pass.cuh", "paper_2405_16267_b300/cs
 
 # The same for the tensor-core softmax pass (60000-row capture scaled to 500000 rows).
 TC_TRAFFIC = {"sources_sha256": "b3166aca059dfe4c2e8d42e393fb6e4cee95da46b68099a2460b9df62d56a709", "bytes_per_launch": 2.5740e+09,
-              "capture": "profiles/k_fused_pass_tc_sparse_softmax_500000x2000x10_bf16.md"}
+              "capture": "profiles/k_fused_pass_tc2_sparse_softmax_500000x2000x10_bf16.md"}
 TC_SOURCES = ["paper_2405_16267_b300/csrc/mc_tc2.cuh", "paper_2405_16267_b300/csrc/mc_tc.cuh",
               "paper_2405_16267_b300/csrc/nspace.cuh", "paper_2405_16267_b300/csrc/common.cuh",
               "paper_2405_16267_b300/csrc/pass.cuh"]
