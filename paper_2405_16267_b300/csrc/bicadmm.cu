@@ -46,6 +46,7 @@ namespace {
 constexpr int kPassThreads = 256;
 constexpr int kDualThreads = 256;
 constexpr int kXupdThreads = 256;
+constexpr int kCholSplitCols = 256;  // blocks this wide or wider: the GPU-wide Cholesky
 constexpr int kXupdRows = 32;
 constexpr int kXupdRowsK = 128;  // K > 1: rows of P per CTA (one staging of R_ij per CTA)
 constexpr int kCholThreads = 256;
@@ -1059,9 +1060,14 @@ int build_factors(bicadmm_ctx* h, const std::function<int(int)>* load_shard = nu
   const int inv_warps = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(8, (200 << 10) / (8 * h->max_nj))));
   const size_t inv_sm = static_cast<size_t>(inv_warps) * h->max_nj * sizeof(double);
   if (nb_panel > 0) {
-    if (nb_panel == 32) e = cudaFuncSetAttribute(k_chol_blk<kCholThreads, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(chol_sm));
-    else if (nb_panel == 16) e = cudaFuncSetAttribute(k_chol_blk<kCholThreads, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(chol_sm));
-    else e = cudaFuncSetAttribute(k_chol_blk<kCholThreads, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(chol_sm));
+    if (nb_panel == 32) e = cudaFuncSetAttribute(k_chol_panel<kCholThreads, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(chol_sm));
+    else if (nb_panel == 16) e = cudaFuncSetAttribute(k_chol_panel<kCholThreads, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(chol_sm));
+    else e = cudaFuncSetAttribute(k_chol_panel<kCholThreads, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(chol_sm));
+    if (e == cudaSuccess) {
+      if (nb_panel == 32) e = cudaFuncSetAttribute(k_chol_blk<kCholThreads, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(chol_sm));
+      else if (nb_panel == 16) e = cudaFuncSetAttribute(k_chol_blk<kCholThreads, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(chol_sm));
+      else e = cudaFuncSetAttribute(k_chol_blk<kCholThreads, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(chol_sm));
+    }
     if (e == cudaSuccess && inv_sm > 48 * 1024)
       e = cudaFuncSetAttribute(k_inv_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(inv_sm));
   }
@@ -1071,9 +1077,36 @@ int build_factors(bicadmm_ctx* h, const std::function<int(int)>* load_shard = nu
     const int64_t* goff = h->d_G_off + static_cast<int64_t>(s0) * h->M;
     const int64_t* poff = h->d_P_off + static_cast<int64_t>(s0) * h->M;
     const unsigned nb = static_cast<unsigned>(ns * h->M);
-    if (nb_panel == 32) k_chol_blk<kCholThreads, 32><<<nb, kCholThreads, chol_sm, st>>>(G, goff, h->d_blk_col0, h->M, h->p.rho_l, h->c0, h->d_err);
-    else if (nb_panel == 16) k_chol_blk<kCholThreads, 16><<<nb, kCholThreads, chol_sm, st>>>(G, goff, h->d_blk_col0, h->M, h->p.rho_l, h->c0, h->d_err);
-    else k_chol_blk<kCholThreads, 8><<<nb, kCholThreads, chol_sm, st>>>(G, goff, h->d_blk_col0, h->M, h->p.rho_l, h->c0, h->d_err);
+    // Blocks of at least kCholSplitCols columns: the Cholesky over the whole GPU (scale, then
+    // per NB-column panel one panel launch, a CTA per block, and one trailing-update launch, a
+    // CTA per 64 x 64 tile per block); narrower blocks: one CTA per block for the whole
+    // factorisation (fewer launches; the same arithmetic)
+    if (h->max_nj < kCholSplitCols) {
+      if (nb_panel == 32) k_chol_blk<kCholThreads, 32><<<nb, kCholThreads, chol_sm, st>>>(G, goff, h->d_blk_col0, h->M, h->p.rho_l, h->c0, h->d_err);
+      else if (nb_panel == 16) k_chol_blk<kCholThreads, 16><<<nb, kCholThreads, chol_sm, st>>>(G, goff, h->d_blk_col0, h->M, h->p.rho_l, h->c0, h->d_err);
+      else k_chol_blk<kCholThreads, 8><<<nb, kCholThreads, chol_sm, st>>>(G, goff, h->d_blk_col0, h->M, h->p.rho_l, h->c0, h->d_err);
+      h->launches += 1;
+    } else {
+    const unsigned sc_chunks = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(64,
+        (static_cast<int64_t>(h->max_nj) * h->max_nj + 256 * 64 - 1) / (256 * 64))));
+    k_chol_scale<kCholThreads><<<dim3(nb, sc_chunks), kCholThreads, 0, st>>>(G, goff, h->d_blk_col0, h->M, h->p.rho_l, h->c0);
+    h->launches += 1;
+    for (int kb = 0; kb < h->max_nj; kb += nb_panel) {
+      if (nb_panel == 32) k_chol_panel<kCholThreads, 32><<<nb, kCholThreads, chol_sm, st>>>(G, goff, h->d_blk_col0, h->M, kb, h->d_err);
+      else if (nb_panel == 16) k_chol_panel<kCholThreads, 16><<<nb, kCholThreads, chol_sm, st>>>(G, goff, h->d_blk_col0, h->M, kb, h->d_err);
+      else k_chol_panel<kCholThreads, 8><<<nb, kCholThreads, chol_sm, st>>>(G, goff, h->d_blk_col0, h->M, kb, h->d_err);
+      h->launches += 1;
+      const int nt = h->max_nj - kb - nb_panel;
+      if (nt > 0) {
+        const int Tt = (nt + 63) / 64;
+        const dim3 ug(static_cast<unsigned>(Tt * (Tt + 1) / 2), nb);
+        if (nb_panel == 32) k_chol_update<kCholThreads, 32><<<ug, kCholThreads, 0, st>>>(G, goff, h->d_blk_col0, h->M, kb);
+        else if (nb_panel == 16) k_chol_update<kCholThreads, 16><<<ug, kCholThreads, 0, st>>>(G, goff, h->d_blk_col0, h->M, kb);
+        else k_chol_update<kCholThreads, 8><<<ug, kCholThreads, 0, st>>>(G, goff, h->d_blk_col0, h->M, kb);
+        h->launches += 1;
+      }
+    }
+    }
     cudaError_t ee = cudaGetLastError();
     if (ee != cudaSuccess) return ee;
     k_inv_fwd<<<dim3(nb, (h->max_nj + inv_warps - 1) / inv_warps), 32 * inv_warps, inv_sm, st>>>(G, goff, h->d_blk_col0, h->M, YT);
@@ -1081,7 +1114,7 @@ int build_factors(bicadmm_ctx* h, const std::function<int(int)>* load_shard = nu
     const int T = (h->max_nj + 63) / 64;
     k_yty<TM><<<dim3(T * (T + 1) / 2, h->M, ns), 256, 0, st>>>(YT, goff, h->d_blk_col0, h->d_blk_ldp, h->M,
                                                                  static_cast<TM*>(h->Pm), poff);
-    h->launches += 3;
+    h->launches += 2;
     return cudaGetLastError();
   };
   // With the host pipeline (shards arriving one by one), each shard is factorised as soon as

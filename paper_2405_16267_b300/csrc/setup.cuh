@@ -241,6 +241,145 @@ k_chol_blk(double* __restrict__ G, const int64_t* __restrict__ G_off, const int*
   }
 }
 
+// Cholesky factor K = L L' (K = rho_l G + c0 I) of every block, in place in the lower
+// triangle (the entries above the diagonal are left as they were), right-looking with
+// NB-column panels and spread over the GPU: the host launches, per panel, one CTA per block
+// for the panel (its NB x NB diagonal block factored by one warp, the rows below solved
+// against it by every thread, the panel held column-major in shared memory) and then one
+// CTA per 64 x 64 tile of every block's trailing lower triangle (4 x 4 entries per thread,
+// summed over the panel's columns in order).  One CTA per block for the whole factorisation
+// took about 17 ms for 625 columns at one SM's FP64 rate (k_chol_blk above, kept for blocks
+// under 256 columns, where this form's launches would cost more than they save).
+// K = rho_l G + c0 I for every block.  Grid (blocks, chunks).
+template <int CT>
+__global__ void __launch_bounds__(CT)
+k_chol_scale(double* __restrict__ G, const int64_t* __restrict__ G_off, const int* __restrict__ blk_col0,
+             int M, double rho_l, double c0) {
+  const int blk = blockIdx.x, j = blk % M;
+  const int nj = blk_col0[j + 1] - blk_col0[j];
+  double* K = G + G_off[blk];
+  const int64_t tot = static_cast<int64_t>(nj) * nj;
+  for (int64_t e = static_cast<int64_t>(blockIdx.y) * CT + threadIdx.x; e < tot;
+       e += static_cast<int64_t>(gridDim.y) * CT) {
+    const int a = static_cast<int>(e / nj), bq = static_cast<int>(e - static_cast<int64_t>(a) * nj);
+    K[e] = rho_l * K[e] + (a == bq ? c0 : 0.0);
+  }
+}
+
+// Panel kb of every block (one CTA per block): factor the diagonal NB x NB block and solve
+// the rows below against it; blocks with nj <= kb return.
+template <int CT, int NB>
+__global__ void __launch_bounds__(CT)
+k_chol_panel(double* __restrict__ G, const int64_t* __restrict__ G_off, const int* __restrict__ blk_col0,
+             int M, int kb, int* __restrict__ err) {
+  static_assert(CT == 256 && NB <= 32, "one lane per diagonal-block row");
+  extern __shared__ double panT[];  // [NB][ldpan]
+  const int blk = blockIdx.x, j = blk % M;
+  const int nj = blk_col0[j + 1] - blk_col0[j];
+  if (kb >= nj) return;
+  const int ldpan = nj + 1;
+  double* K = G + G_off[blk];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = nj - kb < NB ? nj - kb : NB, nr = nj - kb;
+  for (int e = tid; e < nr * nb; e += CT) {
+    const int r = e / nb, k = e - r * nb;
+    panT[k * ldpan + r] = r >= k ? K[static_cast<int64_t>(kb + r) * nj + kb + k] : 0.0;
+  }
+  __syncthreads();
+  if (warp == 0) {  // diagonal block: lane = row
+    for (int c = 0; c < nb; ++c) {
+      double d = panT[c * ldpan + c];
+      if (lane == 0 && !(d > 0.0)) set_err(err, DEV_NONPOS_PIVOT);
+      d = d > 0.0 ? sqrt(d) : 1.0;
+      __syncwarp();
+      if (lane > c && lane < nb) panT[c * ldpan + lane] /= d;
+      if (lane == c) panT[c * ldpan + c] = d;
+      __syncwarp();
+      if (lane > c && lane < nb) {
+        const double lr = panT[c * ldpan + lane];
+        for (int k = c + 1; k <= lane; ++k) panT[k * ldpan + lane] -= lr * panT[c * ldpan + k];
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int r = nb + tid; r < nr; r += CT) {
+    double x[NB];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) x[k] = k < nb ? panT[k * ldpan + r] : 0.0;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+      if (k < nb) {
+        double sum = x[k];
+#pragma unroll
+        for (int q = 0; q < k; ++q) sum = fma(-x[q], panT[q * ldpan + k], sum);
+        x[k] = sum / panT[k * ldpan + k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+      if (k < nb) panT[k * ldpan + r] = x[k];
+  }
+  __syncthreads();
+  for (int e = tid; e < nr * nb; e += CT) {
+    const int r = e / nb, k = e - r * nb;
+    if (r >= k) K[static_cast<int64_t>(kb + r) * nj + kb + k] = panT[k * ldpan + r];
+  }
+}
+
+// Trailing update after panel kb: grid (64 x 64 tiles of the widest block's trailing lower
+// triangle, blocks); tile (ti, tj), tj <= ti, of block b: K[r][c] -= sum_k L[r][k] L[c][k]
+// over the panel's NB columns (rows of L read from K, staged in shared memory).
+template <int CT, int NB>
+__global__ void __launch_bounds__(CT)
+k_chol_update(double* __restrict__ G, const int64_t* __restrict__ G_off, const int* __restrict__ blk_col0,
+              int M, int kb) {
+  __shared__ double La[NB][64], Lb[NB][64];
+  const int blk = blockIdx.y, j = blk % M;
+  const int nj = blk_col0[j + 1] - blk_col0[j];
+  if (nj - kb <= NB) return;  // no trailing part
+  const int nb = NB, nr = nj - kb, nt = nr - nb, T = (nt + 63) / 64;
+  const int tile = blockIdx.x;
+  if (tile >= T * (T + 1) / 2) return;
+  int ti = 0, q = tile;
+  while (q > ti) { q -= ti + 1; ++ti; }
+  const int tj = q;
+  const int r0 = nb + ti * 64, c0t = nb + tj * 64;
+  double* K = G + G_off[blk];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int e = tid; e < NB * 64; e += CT) {
+    const int k = e / 64, i = e - k * 64;
+    const int r = r0 + i, c = c0t + i;
+    La[k][i] = r < nr ? K[static_cast<int64_t>(kb + r) * nj + kb + k] : 0.0;
+    Lb[k][i] = c < nr ? K[static_cast<int64_t>(kb + c) * nj + kb + k] : 0.0;
+  }
+  __syncthreads();
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int bq = 0; bq < 4; ++bq) acc[a][bq] = 0.0;
+  for (int k = 0; k < nb; ++k) {
+    double av[4], bv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      av[a] = La[k][ty + 16 * a];
+      bv[a] = Lb[k][tx + 16 * a];
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int bq = 0; bq < 4; ++bq) acc[a][bq] = fma(av[a], bv[bq], acc[a][bq]);
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int bq = 0; bq < 4; ++bq) {
+      const int r = r0 + ty + 16 * a, c = c0t + tx + 16 * bq;
+      if (r < nr && c <= r) K[static_cast<int64_t>(kb + r) * nj + kb + c] -= acc[a][bq];
+    }
+}
+
 // Y = L^-1 column by column (one warp per column c: forward substitution L y = e_c, y in
 // shared memory), stored transposed: YT row c = column c of Y (zero before c).
 __global__ void k_inv_fwd(const double* __restrict__ G, const int64_t* __restrict__ G_off,
