@@ -381,7 +381,13 @@ k_chol_update(double* __restrict__ G, const int64_t* __restrict__ G_off, const i
 }
 
 // Y = L^-1 column by column (one warp per column c: forward substitution L y = e_c, y in
-// shared memory), stored transposed: YT row c = column c of Y (zero before c).
+// shared memory), stored transposed: YT row c = column c of Y (zero before c).  Rows go 32
+// at a time: lane l adds L[a0 + r][k] y[k] for the known entries k = c + l, c + l + 32, ...
+// into 32 row accumulators (coalesced reads of L), one warp reduce-scatter gives lane r the
+// sum of row a0 + r, and the 32 x 32 diagonal block is solved in the warp with reciprocals
+// of its diagonal formed in parallel.  On this part's FP64 pipe a per-row warp reduction
+// and division cost more than the row's multiply-adds; this form spends one reduction and
+// one division instruction per 32 rows.
 __global__ void k_inv_fwd(const double* __restrict__ G, const int64_t* __restrict__ G_off,
                           const int* __restrict__ blk_col0, int M, double* __restrict__ YT) {
   extern __shared__ double ycol[];  // [warps][nj]
@@ -392,12 +398,29 @@ __global__ void k_inv_fwd(const double* __restrict__ G, const int64_t* __restric
   if (c >= nj) return;
   const double* K = G + G_off[blk];
   double* y = ycol + static_cast<int64_t>(warp) * nj;
-  for (int a = c; a < nj; ++a) {
-    const double* La = K + static_cast<int64_t>(a) * nj;
-    double part = 0.0;
-    for (int bq = c + lane; bq < a; bq += 32) part = fma(La[bq], y[bq], part);
-    part = warp_sum(part);
-    if (lane == 0) y[a] = ((a == c ? 1.0 : 0.0) - part) / La[a];
+  for (int a0 = c; a0 < nj; a0 += 32) {
+    const int nr = nj - a0 < 32 ? nj - a0 : 32;
+    double acc[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) acc[r] = 0.0;
+    for (int k = c + lane; k < a0; k += 32) {
+      const double yk = y[k];
+#pragma unroll
+      for (int r = 0; r < 32; ++r)
+        if (r < nr) acc[r] = fma(K[static_cast<int64_t>(a0 + r) * nj + k], yk, acc[r]);
+    }
+    const double sum = warp_reduce_scatter<32>(acc, lane);  // lane r: row a0 + r
+    const bool mine = lane < nr;
+    const int64_t rowo = static_cast<int64_t>(a0 + (mine ? lane : 0)) * nj;
+    const double dinv = mine ? 1.0 / K[rowo + a0 + lane] : 0.0;
+    double x = (a0 + lane == c ? 1.0 : 0.0) - sum;
+    double yme = 0.0;
+    for (int t = 0; t < nr; ++t) {
+      const double yt = __shfl_sync(0xffffffffu, x * dinv, t);
+      if (lane == t) yme = yt;
+      if (lane > t && mine) x = fma(-K[rowo + a0 + t], yt, x);
+    }
+    if (mine) y[a0 + lane] = yme;
     __syncwarp();
   }
   double* Yr = YT + G_off[blk] + static_cast<int64_t>(c) * nj;
