@@ -47,6 +47,7 @@ constexpr int kPassThreads = 256;
 constexpr int kDualThreads = 256;
 constexpr int kXupdThreads = 256;
 constexpr int kCholSplitCols = 256;  // blocks this wide or wider: the GPU-wide Cholesky
+constexpr int kCholChunk = 64;       // rows of a panel solved per CTA in the GPU-wide Cholesky
 constexpr int kXupdRows = 32;
 constexpr int kXupdRowsK = 128;  // K > 1: rows of P per CTA (one staging of R_ij per CTA)
 constexpr int kCholThreads = 256;
@@ -1052,22 +1053,29 @@ int build_factors(bicadmm_ctx* h, const std::function<int(int)>* load_shard = nu
   for (int cand : {32, 16, 8})
     if (static_cast<size_t>(cand) * (h->max_nj + 1) * sizeof(double) <= (200u << 10)) { nb_panel = cand; break; }
   double* YT = nullptr;
+  int* tick = nullptr;  // per block: tickets of the GPU-wide Cholesky's panel CTAs
   if (nb_panel > 0) {
     e = cudaMalloc(&YT, std::max<int64_t>(h->G_total, 1) * sizeof(double));
-    if (e != cudaSuccess) { cudaGetLastError(); YT = nullptr; nb_panel = 0; e = cudaSuccess; }
+    if (e == cudaSuccess) e = cudaMalloc(&tick, static_cast<size_t>(h->N) * h->M * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(tick, 0, static_cast<size_t>(h->N) * h->M * sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (YT) cudaFree(YT);
+      if (tick) cudaFree(tick);
+      YT = nullptr;
+      tick = nullptr;
+      nb_panel = 0;
+      e = cudaSuccess;
+    }
   }
   const size_t chol_sm = static_cast<size_t>(nb_panel) * (h->max_nj + 1) * sizeof(double);
   const int inv_warps = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(8, (200 << 10) / (8 * h->max_nj))));
   const size_t inv_sm = static_cast<size_t>(inv_warps) * h->max_nj * sizeof(double);
   if (nb_panel > 0) {
-    if (nb_panel == 32) e = cudaFuncSetAttribute(k_chol_panel<kCholThreads, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(chol_sm));
-    else if (nb_panel == 16) e = cudaFuncSetAttribute(k_chol_panel<kCholThreads, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(chol_sm));
-    else e = cudaFuncSetAttribute(k_chol_panel<kCholThreads, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(chol_sm));
-    if (e == cudaSuccess) {
-      if (nb_panel == 32) e = cudaFuncSetAttribute(k_chol_blk<kCholThreads, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(chol_sm));
-      else if (nb_panel == 16) e = cudaFuncSetAttribute(k_chol_blk<kCholThreads, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(chol_sm));
-      else e = cudaFuncSetAttribute(k_chol_blk<kCholThreads, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(chol_sm));
-    }
+    if (nb_panel == 32) e = cudaFuncSetAttribute(k_chol_blk<kCholThreads, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(chol_sm));
+    else if (nb_panel == 16) e = cudaFuncSetAttribute(k_chol_blk<kCholThreads, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(chol_sm));
+    else e = cudaFuncSetAttribute(k_chol_blk<kCholThreads, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(chol_sm));
     if (e == cudaSuccess && inv_sm > 48 * 1024)
       e = cudaFuncSetAttribute(k_inv_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(inv_sm));
   }
@@ -1092,9 +1100,12 @@ int build_factors(bicadmm_ctx* h, const std::function<int(int)>* load_shard = nu
     k_chol_scale<kCholThreads><<<dim3(nb, sc_chunks), kCholThreads, 0, st>>>(G, goff, h->d_blk_col0, h->M, h->p.rho_l, h->c0);
     h->launches += 1;
     for (int kb = 0; kb < h->max_nj; kb += nb_panel) {
-      if (nb_panel == 32) k_chol_panel<kCholThreads, 32><<<nb, kCholThreads, chol_sm, st>>>(G, goff, h->d_blk_col0, h->M, kb, h->d_err);
-      else if (nb_panel == 16) k_chol_panel<kCholThreads, 16><<<nb, kCholThreads, chol_sm, st>>>(G, goff, h->d_blk_col0, h->M, kb, h->d_err);
-      else k_chol_panel<kCholThreads, 8><<<nb, kCholThreads, chol_sm, st>>>(G, goff, h->d_blk_col0, h->M, kb, h->d_err);
+      const int below = std::max(0, h->max_nj - kb - nb_panel);
+      const dim3 pg(nb, static_cast<unsigned>(std::max(1, (below + kCholChunk - 1) / kCholChunk)));
+      int* tk = tick + static_cast<int64_t>(s0) * h->M;
+      if (nb_panel == 32) k_chol_panel<kCholThreads, 32, kCholChunk><<<pg, kCholThreads, 0, st>>>(G, goff, h->d_blk_col0, h->M, kb, h->d_err, tk);
+      else if (nb_panel == 16) k_chol_panel<kCholThreads, 16, kCholChunk><<<pg, kCholThreads, 0, st>>>(G, goff, h->d_blk_col0, h->M, kb, h->d_err, tk);
+      else k_chol_panel<kCholThreads, 8, kCholChunk><<<pg, kCholThreads, 0, st>>>(G, goff, h->d_blk_col0, h->M, kb, h->d_err, tk);
       h->launches += 1;
       const int nt = h->max_nj - kb - nb_panel;
       if (nt > 0) {
@@ -1211,6 +1222,7 @@ int build_factors(bicadmm_ctx* h, const std::function<int(int)>* load_shard = nu
     for (cudaEvent_t ev : fev) cudaEventDestroy(ev);
     cudaFree(G);
     if (YT) cudaFree(YT);
+    if (tick) cudaFree(tick);
     if (d_items32) cudaFree(d_items32);
     return rc;
   }
@@ -1260,6 +1272,7 @@ int build_factors(bicadmm_ctx* h, const std::function<int(int)>* load_shard = nu
   for (cudaEvent_t ev : fev) cudaEventDestroy(ev);
   cudaFree(G);
   if (YT) cudaFree(YT);
+  if (tick) cudaFree(tick);
   if (d_items32) cudaFree(d_items32);
   if (rc != BICADMM_OK) return rc;
   return check_device_error(h);

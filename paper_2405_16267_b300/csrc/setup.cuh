@@ -249,7 +249,8 @@ k_chol_blk(double* __restrict__ G, const int64_t* __restrict__ G_off, const int*
 // CTA per 64 x 64 tile of every block's trailing lower triangle (4 x 4 entries per thread,
 // summed over the panel's columns in order).  One CTA per block for the whole factorisation
 // took about 17 ms for 625 columns at one SM's FP64 rate (k_chol_blk above, kept for blocks
-// under 256 columns, where this form's launches would cost more than they save).
+// under 256 columns, where this form's launches would cost more than they save; its results
+// agree with this form's to rounding).
 // K = rho_l G + c0 I for every block.  Grid (blocks, chunks).
 template <int CT>
 __global__ void __launch_bounds__(CT)
@@ -266,64 +267,98 @@ k_chol_scale(double* __restrict__ G, const int64_t* __restrict__ G_off, const in
   }
 }
 
-// Panel kb of every block (one CTA per block): factor the diagonal NB x NB block and solve
-// the rows below against it; blocks with nj <= kb return.
-template <int CT, int NB>
+// Panel kb of every block, grid (blocks, row chunks of RC rows): each CTA factors the
+// diagonal NB x NB block (warp 0; every CTA of a block gets the same factor) and solves its
+// chunk of the rows below against it.  The factored diagonal block is written by the last
+// of the block's CTAs to finish (a ticket on tick[block], reset by that CTA), so that no CTA
+// reads it from K after it was overwritten; no CTA waits for another.  Divisions by
+// the diagonal are multiplications by its reciprocals, formed once per panel (on this part
+// an FP64 division costs a dozen FP64 instructions, and a row's solve had one per column).
+// Blocks with nj <= kb return.
+template <int CT, int NB, int RC>
 __global__ void __launch_bounds__(CT)
 k_chol_panel(double* __restrict__ G, const int64_t* __restrict__ G_off, const int* __restrict__ blk_col0,
-             int M, int kb, int* __restrict__ err) {
-  static_assert(CT == 256 && NB <= 32, "one lane per diagonal-block row");
-  extern __shared__ double panT[];  // [NB][ldpan]
+             int M, int kb, int* __restrict__ err, int* __restrict__ tick) {
+  static_assert(CT == 256 && NB <= 32 && RC <= CT, "one lane per diagonal-block row, a row per thread");
+  constexpr int LD = NB + RC + 1;    // rows held: the diagonal block, then the chunk
+  __shared__ double panT[NB * LD];   // [k][row]
+  __shared__ double rinv[NB];
+  __shared__ bool last;
   const int blk = blockIdx.x, j = blk % M;
   const int nj = blk_col0[j + 1] - blk_col0[j];
   if (kb >= nj) return;
-  const int ldpan = nj + 1;
   double* K = G + G_off[blk];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nb = nj - kb < NB ? nj - kb : NB, nr = nj - kb;
-  for (int e = tid; e < nr * nb; e += CT) {
-    const int r = e / nb, k = e - r * nb;
-    panT[k * ldpan + r] = r >= k ? K[static_cast<int64_t>(kb + r) * nj + kb + k] : 0.0;
+  const int r_lo = nb + static_cast<int>(blockIdx.y) * RC;  // first chunk row (relative to kb)
+  if (blockIdx.y > 0 && r_lo >= nr) return;
+  const int nc = nr - r_lo < RC ? (nr - r_lo > 0 ? nr - r_lo : 0) : RC;  // chunk rows
+  // local row i: i < nb the diagonal block's row i, i >= nb chunk row r_lo + i - nb
+  for (int e = tid; e < (nb + nc) * nb; e += CT) {
+    const int i = e / nb, k = e - i * nb;
+    const int r = i < nb ? i : r_lo + i - nb;
+    panT[k * LD + i] = r >= k ? K[static_cast<int64_t>(kb + r) * nj + kb + k] : 0.0;
   }
   __syncthreads();
   if (warp == 0) {  // diagonal block: lane = row
     for (int c = 0; c < nb; ++c) {
-      double d = panT[c * ldpan + c];
-      if (lane == 0 && !(d > 0.0)) set_err(err, DEV_NONPOS_PIVOT);
+      double d = panT[c * LD + c];
+      if (lane == 0 && blockIdx.y == 0 && !(d > 0.0)) set_err(err, DEV_NONPOS_PIVOT);
       d = d > 0.0 ? sqrt(d) : 1.0;
+      const double di = 1.0 / d;
       __syncwarp();
-      if (lane > c && lane < nb) panT[c * ldpan + lane] /= d;
-      if (lane == c) panT[c * ldpan + c] = d;
+      if (lane > c && lane < nb) panT[c * LD + lane] *= di;
+      if (lane == c) {
+        panT[c * LD + c] = d;
+        rinv[c] = di;
+      }
       __syncwarp();
       if (lane > c && lane < nb) {
-        const double lr = panT[c * ldpan + lane];
-        for (int k = c + 1; k <= lane; ++k) panT[k * ldpan + lane] -= lr * panT[c * ldpan + k];
+        const double lr = panT[c * LD + lane];
+        for (int k = c + 1; k <= lane; ++k) panT[k * LD + lane] -= lr * panT[c * LD + k];
       }
       __syncwarp();
     }
   }
   __syncthreads();
-  for (int r = nb + tid; r < nr; r += CT) {
+  // chunk rows: x L11' = a, i.e. x_k = (a_k - sum_{q<k} x_q L11[k][q]) / L11[k][k]
+  if (tid < nc) {
+    const int i = nb + tid;
     double x[NB];
 #pragma unroll
-    for (int k = 0; k < NB; ++k) x[k] = k < nb ? panT[k * ldpan + r] : 0.0;
+    for (int k = 0; k < NB; ++k) x[k] = k < nb ? panT[k * LD + i] : 0.0;
 #pragma unroll
     for (int k = 0; k < NB; ++k) {
       if (k < nb) {
         double sum = x[k];
 #pragma unroll
-        for (int q = 0; q < k; ++q) sum = fma(-x[q], panT[q * ldpan + k], sum);
-        x[k] = sum / panT[k * ldpan + k];
+        for (int q = 0; q < k; ++q) sum = fma(-x[q], panT[q * LD + k], sum);
+        x[k] = sum * rinv[k];
       }
     }
 #pragma unroll
     for (int k = 0; k < NB; ++k)
-      if (k < nb) panT[k * ldpan + r] = x[k];
+      if (k < nb) panT[k * LD + i] = x[k];
   }
   __syncthreads();
-  for (int e = tid; e < nr * nb; e += CT) {
-    const int r = e / nb, k = e - r * nb;
-    if (r >= k) K[static_cast<int64_t>(kb + r) * nj + kb + k] = panT[k * ldpan + r];
+  for (int e = tid; e < nc * nb; e += CT) {
+    const int i = nb + e / nb, k = e % nb;
+    K[static_cast<int64_t>(kb + r_lo + i - nb) * nj + kb + k] = panT[k * LD + i];
+  }
+  // the block's CTAs: chunk 0 and every chunk that starts above nr
+  const int nact = nr - nb > RC ? (nr - nb + RC - 1) / RC : 1;
+  __syncthreads();  // this CTA's reads of the diagonal block are done
+  if (tid == 0) {
+    __threadfence();
+    last = atomicAdd(&tick[blk], 1) == nact - 1;
+  }
+  __syncthreads();
+  if (last) {
+    for (int e = tid; e < nb * nb; e += CT) {
+      const int i = e / nb, k = e % nb;
+      if (i >= k) K[static_cast<int64_t>(kb + i) * nj + kb + k] = panT[k * LD + i];
+    }
+    if (tid == 0) tick[blk] = 0;
   }
 }
 

@@ -22,6 +22,8 @@ CASES = [  # (m, n, N, M, K)
     (220, 64, 4, 1, 1),       # 55-row shards: one partial stage
     (1500, 150, 3, 2, 3),     # softmax, three classes (same block matrices)
     (2000, 900, 2, 1, 1),     # a 900-column block: 16-column Cholesky panels
+    (4000, 640, 2, 1, 1),     # a 640-column block: ten 64-row chunks per Cholesky panel
+    (5000, 1300, 2, 1, 1),    # 1300 columns: 16-column panels, twenty chunks per panel
     (3600, 3500, 1, 1, 1),    # a 3500-column block: too wide for a panel in shared memory,
                               # the column-by-column kernels
 ]
