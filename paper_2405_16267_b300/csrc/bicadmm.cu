@@ -1045,6 +1045,8 @@ int build_factors(bicadmm_ctx* h, const std::function<int(int)>* load_shard = nu
 
   int rc = BICADMM_OK;
   Gram32Item* d_items32 = nullptr;
+  double* gscratch = nullptr;  // the split Gram tiles' partials and tickets
+  int* gtick = nullptr;
 
   // Blocked factorisation when an NB-column panel of the widest block fits in shared memory:
   // Cholesky, Y = L^-1 by columns, P = Y'Y by tiles (n^3/2 FMAs per block); otherwise the
@@ -1155,17 +1157,41 @@ int build_factors(bicadmm_ctx* h, const std::function<int(int)>* load_shard = nu
     // chunk) items over each block's own columns, chunks at or right of the strip.  FP32
     // storage splits A into TF32 hi + lo (three products); TF32 storage (rounded first) and
     // BF16 storage (exact in TF32) take one product.
+    // A launch with few tiles splits each tile's rows into parts (at most
+    // 8, at least four 32-row stages each), a CTA per part: the softmax shape's four
+    // 500-column blocks give 40 tiles per shard, and one CTA per tile walking all 15625 rows
+    // made each shard's Gram matrices 1.9 ms on the setup stream, longer than its copy.
+    int tiles_shard = 0;
+    for (int j = 0; j < h->M; ++j) {
+      const int t = (h->blk_col0[j + 1] - h->blk_col0[j] + 127) / 128;
+      tiles_shard += t * (t + 1) / 2;
+    }
+    const int64_t tiles_launch = static_cast<int64_t>(tiles_shard) * (load_shard ? 1 : h->N);
+    int64_t min_rows = h->p.m;
+    for (int i = 0; i < h->N; ++i) min_rows = std::min<int64_t>(min_rows, h->shard_row0[i + 1] - h->shard_row0[i]);
+    // (only below half an SM count: the partials cost scratch traffic, and 120 tiles of the
+    // 200000 x 5000 shards already kept the Gram under the copy time)
+    int nparts = tiles_launch * 2 >= h->num_sms ? 1 :
+        static_cast<int>(std::min<int64_t>(8, (2 * h->num_sms + tiles_launch - 1) / std::max<int64_t>(tiles_launch, 1)));
+    nparts = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(nparts, min_rows / (4 * kG32StageRows))));
     std::vector<Gram32Item> items;
     std::vector<size_t> first(h->N + 1, 0);  // items of shard i: [first[i], first[i + 1])
     for (int i = 0; i < h->N; ++i) {
       first[i] = items.size();
+      int g = load_shard ? 0 : i * tiles_shard;  // tile index within its launch
       for (int j = 0; j < h->M; ++j) {
         const int nj = h->blk_col0[j + 1] - h->blk_col0[j];
         for (int a = 0; a < (nj + 127) / 128; ++a)
-          for (int bq = a; bq < (nj + 127) / 128; ++bq) items.push_back(Gram32Item{i, j, a, bq});
+          for (int bq = a; bq < (nj + 127) / 128; ++bq, ++g)
+            for (int pt = 0; pt < nparts; ++pt) items.push_back(Gram32Item{i, j, a, bq, pt, nparts, g});
       }
     }
     first[h->N] = items.size();
+    if (nparts > 1) {
+      e = cudaMalloc(&gscratch, static_cast<size_t>(tiles_launch) * nparts * 128 * 128 * sizeof(double));
+      if (e == cudaSuccess) e = cudaMalloc(&gtick, static_cast<size_t>(tiles_launch) * sizeof(int));
+      if (e == cudaSuccess) e = cudaMemsetAsync(gtick, 0, static_cast<size_t>(tiles_launch) * sizeof(int), h->stream);
+    }
     constexpr bool kBf16 = std::is_same<TA, __nv_bfloat16>::value;
     const int terms = (kBf16 || h->tf32) ? 1 : 3;
     e = cudaMalloc(&d_items32, std::max<size_t>(items.size(), 1) * sizeof(Gram32Item));
@@ -1194,10 +1220,10 @@ int build_factors(bicadmm_ctx* h, const std::function<int(int)>* load_shard = nu
         const TA* Ap = static_cast<const TA*>(h->A);
         if (terms == 3)
           k_gram_tf32<3, TA><<<grid, kG32Threads, sm, h->stream>>>(Ap, h->lda, d_items32 + i0, h->d_shard_row0,
-              h->d_blk_col0, G, h->d_G_off, h->M, h->d_err, kWaitLimitCycles);
+              h->d_blk_col0, G, h->d_G_off, h->M, gscratch, gtick, h->d_err, kWaitLimitCycles);
         else
           k_gram_tf32<1, TA><<<grid, kG32Threads, sm, h->stream>>>(Ap, h->lda, d_items32 + i0, h->d_shard_row0,
-              h->d_blk_col0, G, h->d_G_off, h->M, h->d_err, kWaitLimitCycles);
+              h->d_blk_col0, G, h->d_G_off, h->M, gscratch, gtick, h->d_err, kWaitLimitCycles);
         e = cudaGetLastError();
         h->launches += 1;
       }
@@ -1224,6 +1250,8 @@ int build_factors(bicadmm_ctx* h, const std::function<int(int)>* load_shard = nu
     if (YT) cudaFree(YT);
     if (tick) cudaFree(tick);
     if (d_items32) cudaFree(d_items32);
+    if (gscratch) cudaFree(gscratch);
+    if (gtick) cudaFree(gtick);
     return rc;
   }
   if (per_shard) {
@@ -1274,6 +1302,8 @@ int build_factors(bicadmm_ctx* h, const std::function<int(int)>* load_shard = nu
   if (YT) cudaFree(YT);
   if (tick) cudaFree(tick);
   if (d_items32) cudaFree(d_items32);
+  if (gscratch) cudaFree(gscratch);
+  if (gtick) cudaFree(gtick);
   if (rc != BICADMM_OK) return rc;
   return check_device_error(h);
 }

@@ -106,8 +106,14 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Work item of the TF32 Gram (one CTA): shard, block, strip a (128 columns), chunk b (128).
+// A work item: the (a, b) 128 x 128 tile of block `block`'s Gram matrix over shard `shard`'s
+// rows, or over part `part` of them (`nparts` contiguous pieces, each a CTA, for a shard's
+// few tiles to fill the GPU): a part writes its partial tile to scratch tile
+// `group * nparts + part`, and the last part to finish (a ticket per group) adds the
+// partials in part order into G.
 struct Gram32Item {
   int shard, block, a, b;
+  int part, nparts, group;
 };
 
 // TMEM columns: the running products of the current chain (hi hi' in BIG; hi lo' + lo hi' in
@@ -122,7 +128,8 @@ __global__ void __launch_bounds__(kG32Threads, 1)
 k_gram_tf32(const TIN* __restrict__ A, int64_t lda, const Gram32Item* __restrict__ items,
             const int64_t* __restrict__ shard_row0, const int* __restrict__ blk_col0,
             double* __restrict__ G, const int64_t* __restrict__ G_off, int M,
-            int* __restrict__ err, long long wait_limit) {
+            double* __restrict__ scratch, int* __restrict__ tick, int* __restrict__ err,
+            long long wait_limit) {
   constexpr int CW = 128;
   constexpr int S = g32_stages(CW, TERMS);
   constexpr int SB = g32_stage_bytes(CW, TERMS);
@@ -152,8 +159,14 @@ k_gram_tf32(const TIN* __restrict__ A, int64_t lda, const Gram32Item* __restrict
   const int N = (cvalid + 15) & ~15;                           // MMA N (multiple of 16)
   const bool sic = it.a == it.b;                               // strip = chunk
   const int cfill = sic ? CW : N;  // chunk tile rows holding data (all 128 when it is the strip too)
-  const int64_t r_begin = shard_row0[it.shard], r_end = shard_row0[it.shard + 1];
-  const int nstg = static_cast<int>((r_end - r_begin + kG32StageRows - 1) / kG32StageRows);
+  // this item's rows: its part of the shard, cut at 32-row stage boundaries
+  const int64_t rs0 = shard_row0[it.shard], rs1 = shard_row0[it.shard + 1];
+  const int64_t nst_all = (rs1 - rs0 + kG32StageRows - 1) / kG32StageRows;
+  const int64_t st_lo = nst_all * it.part / it.nparts, st_hi = nst_all * (it.part + 1) / it.nparts;
+  const int64_t r_begin = rs0 + st_lo * kG32StageRows;
+  const int64_t r_end = rs0 + st_hi * kG32StageRows < rs1 ? rs0 + st_hi * kG32StageRows : rs1;
+  const int nstg = static_cast<int>(st_hi - st_lo);
+  __shared__ int last_part;
   // a chain ends after stage s when (s + 1) % F == 0 and stage s + S exists (its staging is
   // where the fold happens); the last chain runs to the end and is folded in the epilogue
   auto chain_end = [&](int s) { return (s + 1) % F == 0 && s + S < nstg; };
@@ -311,11 +324,17 @@ k_gram_tf32(const TIN* __restrict__ A, int64_t lda, const Gram32Item* __restrict
             double val = static_cast<double>(__uint_as_float(vb[q]));
             if (TERMS == 3) val += static_cast<double>(__uint_as_float(vs[q]));
             if (folded) val += static_cast<double>(__uint_as_float(sa[q])) + static_cast<double>(__uint_as_float(ca[q]));
-            Gb[static_cast<int64_t>(l1) * nj + l2] = val;
-            Gb[static_cast<int64_t>(l2) * nj + l1] = val;
+            if (it.nparts == 1) {
+              Gb[static_cast<int64_t>(l1) * nj + l2] = val;
+              Gb[static_cast<int64_t>(l2) * nj + l1] = val;
+            } else {
+              scratch[(static_cast<int64_t>(it.group) * it.nparts + it.part) * (128 * 128) +
+                      (32 * lq + lane) * 128 + 16 * cc + q] = val;
+            }
           }
         }
       }
+      if (it.nparts > 1) __threadfence();  // the partial tile before this CTA's ticket
       tc_fence_before();
     } else {
       *abort_v = 1;
@@ -377,6 +396,30 @@ k_gram_tf32(const TIN* __restrict__ A, int64_t lda, const Gram32Item* __restrict
   if (warp == 0) {
     tc_fence_after();
     tmem_dealloc(tmem, 512);
+  }
+  if (it.nparts > 1 && !*abort_v) {
+    // the last part of the group adds the partials in part order and writes both triangles
+    if (tid == 0) last_part = atomicAdd(&tick[it.group], 1) == it.nparts - 1;
+    __syncthreads();
+    if (last_part && warp < 8) {
+      const int lq = warp & 3, half = warp >> 2;
+      double* Gb = G + G_off[it.shard * M + it.block];
+      const int l1 = sa0 + 32 * lq + lane;
+      for (int cc = 4 * half; cc < 4 * half + 4 && 16 * cc < N; ++cc) {
+        for (int q = 0; q < 16; ++q) {
+          const int l2 = cb0 + 16 * cc + q;
+          if (l1 < nj && l2 >= l1 && l2 < nj) {
+            double val = 0.0;
+            for (int p = 0; p < it.nparts; ++p)
+              val += __ldcg(&scratch[(static_cast<int64_t>(it.group) * it.nparts + p) * (128 * 128) +
+                                     (32 * lq + lane) * 128 + 16 * cc + q]);
+            Gb[static_cast<int64_t>(l1) * nj + l2] = val;
+            Gb[static_cast<int64_t>(l2) * nj + l1] = val;
+          }
+        }
+      }
+    }
+    if (last_part && tid == 0) tick[it.group] = 0;
   }
 }
 
