@@ -167,14 +167,14 @@ class ClockSampler:
 # DRAM traffic of one pass launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of a 20000-row launch of the same kernel, scaled by rows to the
 # 200000-row launch.  Reported only while the kernel sources are the captured ones.
-PASS_TRAFFIC = {"sources_sha256": "495bc488df9731928980879c8ab46f4d0954380d7e8fa097e2a382ab3c1b1156", "bytes_per_launch": 4.0525e+09,
+PASS_TRAFFIC = {"sources_sha256": "940c910688671c2b2641adce3f8669399b2ea437cfef2e84003a1aa1cd4c0f75", "bytes_per_launch": 4.0495e+09,
                 "capture": "profiles/k_fused_pass_sparse_logistic_200000x5000_fp32.md"}
 PASS_SOURCES = ["paper_2405_16267_b300/csrc/pass.cuh", "paper_2405_16267_b300/csrc/nspace.cuh",
                 "paper_2405_16267_b300/csrc/common.cuh"]
 
 
 # The same for the tensor-core softmax pass (60000-row capture scaled to 500000 rows).
-TC_TRAFFIC = {"sources_sha256": "b3166aca059dfe4c2e8d42e393fb6e4cee95da46b68099a2460b9df62d56a709", "bytes_per_launch": 2.5740e+09,
+TC_TRAFFIC = {"sources_sha256": "df6c577684cb10e0d4a81cc9a69867b485f6fba34cb1f2f361a1ad6f3a43c79a", "bytes_per_launch": 2.5625e+09,
               "capture": "profiles/k_fused_pass_tc2_sparse_softmax_500000x2000x10_bf16.md"}
 TC_SOURCES = ["paper_2405_16267_b300/csrc/mc_tc2.cuh", "paper_2405_16267_b300/csrc/mc_tc.cuh",
               "paper_2405_16267_b300/csrc/nspace.cuh", "paper_2405_16267_b300/csrc/common.cuh",
@@ -182,7 +182,7 @@ TC_SOURCES = ["paper_2405_16267_b300/csrc/mc_tc2.cuh", "paper_2405_16267_b300/cs
 
 # The same kernel on the sparsity path (10 logistic instances as its columns; 60000-row
 # capture scaled to 500000 rows).
-PATH_TRAFFIC = {"sources_sha256": "b3166aca059dfe4c2e8d42e393fb6e4cee95da46b68099a2460b9df62d56a709", "bytes_per_launch": 2.4160e+09,
+PATH_TRAFFIC = {"sources_sha256": "df6c577684cb10e0d4a81cc9a69867b485f6fba34cb1f2f361a1ad6f3a43c79a", "bytes_per_launch": 2.4093e+09,
                 "capture": "profiles/k_fused_pass_tc_logistic_path10_500000x2000_bf16.md"}
 
 
