@@ -463,25 +463,39 @@ __global__ void k_inv_fwd(const double* __restrict__ G, const int64_t* __restric
 }
 
 // P_ij = K^-1 = L^-T L^-1 = Y' Y: P[a][b] = sum_{k >= max(a, b)} YT[a][k] YT[b][k], FP64
-// sums, written in TP with row stride ldp (both triangles; the tile pair (0, 0) also zeroes
-// the padding columns).  Grid (upper-triangle 64 x 64 tile pairs, M, N), 4 x 4 per thread.
+// sums, written in TP with row stride ldp (both triangles; the item (0, 0) of a block also
+// zeroes the padding columns).  Grid (items, 1, shards), 4 x 4 per thread.  An item is the
+// 64 x 64 tile pair (ti, tj), ti <= tj, of block j over k in [tj 64, nj), or one part of
+// that range: the sum of a tile far from the diagonal is several times that of one near
+// it, and one CTA per tile left most SMs idle behind the longest.  A part writes its partial
+// tile to scratch (the block's region of G, free once the inverse has read L) and the last
+// part of a tile (a ticket) adds the partials in part order.
+struct YtyItem {
+  int j, ti, tj;
+  int part, nparts;
+  int tick;  // the tile's ticket within a shard's tiles
+  int scr;   // its first partial tile (of 64 x 64 doubles) within the block's scratch
+  int pad;
+};
+
 template <typename TP>
 __global__ void __launch_bounds__(256)
 k_yty(const double* __restrict__ YT, const int64_t* __restrict__ G_off, const int* __restrict__ blk_col0,
-      const int* __restrict__ blk_ldp, int M, TP* __restrict__ P, const int64_t* __restrict__ P_off) {
+      const int* __restrict__ blk_ldp, int M, TP* __restrict__ P, const int64_t* __restrict__ P_off,
+      const YtyItem* __restrict__ items, int kspan, double* __restrict__ G, int* __restrict__ tick,
+      int ntiles) {
   constexpr int TILE = 64, KC = 32;
   __shared__ double As[KC][TILE + 1];
   __shared__ double Bs[KC][TILE + 1];
-  const int i = blockIdx.z, j = blockIdx.y, blk = i * M + j;
+  __shared__ int last_part;
+  const YtyItem it = items[blockIdx.x];
+  const int i = blockIdx.z, j = it.j, blk = i * M + j;
   const int nj = blk_col0[j + 1] - blk_col0[j], ldp = blk_ldp[j];
-  const int T = (nj + TILE - 1) / TILE;
-  int q = blockIdx.x, ti = 0;
-  while (q >= T - ti) { q -= T - ti; ++ti; if (ti >= T) return; }
-  const int tj = ti + q;  // ti <= tj
+  const int ti = it.ti, tj = it.tj;
   const double* Y = YT + G_off[blk];
   TP* Pb = P + P_off[blk];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  if (blockIdx.x == 0 && ldp > nj) {
+  if (ti == 0 && tj == 0 && it.part == 0 && ldp > nj) {
     for (int64_t e = threadIdx.x; e < static_cast<int64_t>(nj) * (ldp - nj); e += 256) {
       const int a = static_cast<int>(e / (ldp - nj)), cc = nj + static_cast<int>(e - static_cast<int64_t>(a) * (ldp - nj));
       Pb[static_cast<int64_t>(a) * ldp + cc] = TP(0);
@@ -493,12 +507,14 @@ k_yty(const double* __restrict__ YT, const int64_t* __restrict__ G_off, const in
 #pragma unroll
     for (int bq = 0; bq < 4; ++bq) acc[a][bq] = 0.0;
   // YT[a][k] = 0 for k < a, so the sum starts at the column tile's first index
-  for (int k0 = tj * TILE; k0 < nj; k0 += KC) {
+  const int k_lo = tj * TILE + it.part * kspan;
+  const int k_hi = it.part + 1 == it.nparts ? nj : tj * TILE + (it.part + 1) * kspan;
+  for (int k0 = k_lo; k0 < k_hi; k0 += KC) {
     for (int e = threadIdx.x; e < KC * TILE; e += 256) {
       const int r = e / KC, k = e - r * KC;
       const int ra = ti * TILE + r, rb = tj * TILE + r, kk = k0 + k;
-      As[k][r] = (ra < nj && kk < nj) ? Y[static_cast<int64_t>(ra) * nj + kk] : 0.0;
-      Bs[k][r] = (rb < nj && kk < nj) ? Y[static_cast<int64_t>(rb) * nj + kk] : 0.0;
+      As[k][r] = (ra < nj && kk < k_hi) ? Y[static_cast<int64_t>(ra) * nj + kk] : 0.0;
+      Bs[k][r] = (rb < nj && kk < k_hi) ? Y[static_cast<int64_t>(rb) * nj + kk] : 0.0;
     }
     __syncthreads();
 #pragma unroll 8
@@ -512,6 +528,30 @@ k_yty(const double* __restrict__ YT, const int64_t* __restrict__ G_off, const in
         for (int bq = 0; bq < 4; ++bq) acc[a][bq] = fma(av[a], bv[bq], acc[a][bq]);
     }
     __syncthreads();
+  }
+  if (it.nparts > 1) {
+    double* scr = G + G_off[blk] + static_cast<int64_t>(it.scr) * (TILE * TILE);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int bq = 0; bq < 4; ++bq)
+        scr[static_cast<int64_t>(it.part) * (TILE * TILE) + (ty + 16 * a) * TILE + tx + 16 * bq] = acc[a][bq];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0)
+      last_part = atomicAdd(&tick[static_cast<int64_t>(i) * ntiles + it.tick], 1) == it.nparts - 1;
+    __syncthreads();
+    if (!last_part) return;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int bq = 0; bq < 4; ++bq) {
+        double v = 0.0;
+        for (int p = 0; p < it.nparts; ++p)
+          v += __ldcg(&scr[static_cast<int64_t>(p) * (TILE * TILE) + (ty + 16 * a) * TILE + tx + 16 * bq]);
+        acc[a][bq] = v;
+      }
+    if (threadIdx.x == 0) tick[static_cast<int64_t>(i) * ntiles + it.tick] = 0;
   }
 #pragma unroll
   for (int a = 0; a < 4; ++a)
