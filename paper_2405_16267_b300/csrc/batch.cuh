@@ -62,6 +62,16 @@ struct BatchInst {
   int* err;
 };
 
+// Panels in flight per CTA of the wide-row pass at most (its mbarrier slots).
+constexpr int kBatchSlots = 16;
+
+// The copy issuer's view of the segment of the next panel it copies (shared memory).
+struct BatchCursor {
+  const void* A;
+  int64_t lda, first, next_first, row0, end;
+  int s, rpp;
+};
+
 // One segment: the rows of shard `shard` of instance `inst`, cut into panels of `rpp` rows
 // (rpp * row bytes <= the stage size, rpp <= R of the kernel).
 struct BatchSeg {
@@ -88,13 +98,19 @@ k_fused_pass_batch(const BatchInst* __restrict__ inst, const BatchSeg* __restric
   const int64_t p_end = static_cast<int64_t>(c + 1) * P / G;
   const int64_t np = p_end - p_begin;
 
-  // layout: S stages of stage_bytes | S mbarriers | red[R][NW] | d[R]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + S * stage_bytes);
-  TM* red = reinterpret_cast<TM*>(bars + S);
+  // layout: a ring of S * stage_bytes | kBatchSlots mbarriers | the panels' ring offsets |
+  // the issuer's segment cursor | red[R][NW] | d[R].  Panels (at most stage_bytes each) are placed end to end in the ring,
+  // so an instance with short panels keeps several of them in flight; panel k waits on
+  // barrier k % kBatchSlots.
+  const uint32_t ring = static_cast<uint32_t>(S * stage_bytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + ring);
+  uint32_t* poff = reinterpret_cast<uint32_t*>(bars + kBatchSlots);
+  BatchCursor* icur = reinterpret_cast<BatchCursor*>(poff + kBatchSlots);
+  TM* red = reinterpret_cast<TM*>(icur + 1);
   TM* d_s = red + R * NW;
 
   if (tid == 0) {
-    for (int st = 0; st < S; ++st) mbar_init(&bars[st], 1);
+    for (int st = 0; st < kBatchSlots; ++st) mbar_init(&bars[st], 1);
     fence_barrier_init();
   }
   __syncthreads();
@@ -118,21 +134,60 @@ k_fused_pass_batch(const BatchInst* __restrict__ inst, const BatchSeg* __restric
     seg0 = lo;
   }
 
+  // Thread 0 issues the copies.  Panels [done, n_issued) are in flight and occupy the ring
+  // from poff[done % kBatchSlots] up to `head`, wrapping at most once; a panel is placed at
+  // `head` when it fits before the ring's end, else at 0 when it fits before the oldest one.
+  // Every size and offset is a multiple of 16 bytes (rows are padded to 16-byte vectors).
+  // Its segment cursor (the current segment's rows, its instance's A and lda, and where the
+  // next segment starts) sits in shared memory, so that an issue reads the tables only when
+  // it crosses into a later segment.
   int64_t n_issued = 0;
-  int issue_seg = seg0;
-  auto issue = [&](int64_t k) {
-    int64_t row0;
-    int nrows;
-    locate(p_begin + k, issue_seg, row0, nrows);
-    const BatchInst& I = inst[seg[issue_seg].inst];
-    const int st = static_cast<int>(k % S);
-    const uint32_t bytes = static_cast<uint32_t>(nrows * I.lda * sizeof(TA));
-    mbar_arrive_expect_tx(&bars[st], bytes);
-    bulk_copy_g2s(smem_raw + st * stage_bytes, static_cast<const TA*>(I.A) + row0 * I.lda, bytes,
-                  &bars[st]);
+  uint32_t head = 0;
+  auto icur_load = [&](int s) {
+    const BatchSeg& g = seg[s];
+    const BatchInst& I = inst[g.inst];
+    icur->A = I.A;
+    icur->lda = I.lda;
+    icur->first = g.first_panel;
+    icur->next_first = s + 1 < nseg ? seg[s + 1].first_panel : static_cast<int64_t>(0x7fffffffffffffffLL);
+    icur->row0 = g.row0;
+    icur->end = g.row0 + g.rows;
+    icur->s = s;
+    icur->rpp = g.rpp;
+  };
+  if (tid == 0) icur_load(seg0);
+  auto try_issue = [&](int64_t done) -> bool {
+    if (n_issued >= np || n_issued - done >= kBatchSlots) return false;
+    const int64_t p = p_begin + n_issued;
+    while (p >= icur->next_first) icur_load(icur->s + 1);
+    const int64_t row0 = icur->row0 + (p - icur->first) * icur->rpp;
+    const int64_t lda_i = icur->lda;
+    const int nrows = static_cast<int>(icur->end - row0 < icur->rpp ? icur->end - row0 : icur->rpp);
+    const uint32_t bytes = static_cast<uint32_t>(nrows * lda_i * sizeof(TA));
+    uint32_t at = 0;
+    if (n_issued > done) {
+      const uint32_t tail = poff[done % kBatchSlots];
+      if (head > tail) {
+        if (head + bytes <= ring) at = head;
+        else if (bytes <= tail) at = 0;
+        else return false;
+      } else if (head + bytes <= tail) {
+        at = head;
+      } else {
+        return false;
+      }
+    }
+    const int sl = static_cast<int>(n_issued % kBatchSlots);
+    poff[sl] = at;
+    head = at + bytes;
+    mbar_arrive_expect_tx(&bars[sl], bytes);
+    bulk_copy_g2s(smem_raw + at, static_cast<const TA*>(icur->A) + row0 * lda_i, bytes, &bars[sl]);
+    ++n_issued;
+    return true;
   };
   if (tid == 0) {
-    for (; n_issued < np && n_issued < S; ++n_issued) issue(n_issued);
+    while (try_issue(0)) {
+    }
   }
 
   // x_i in the storage type when it is the arithmetic type, else (BF16) in the arithmetic type
@@ -224,18 +279,19 @@ k_fused_pass_batch(const BatchInst* __restrict__ inst, const BatchSeg* __restric
       nu_r = static_cast<const TM*>(I.nu)[row0 + lane];
       om_r = static_cast<const TM*>(I.omega)[row0 + lane];
     }
-    const int st = static_cast<int>(k % S);
-    const uint32_t parity = static_cast<uint32_t>((k / S) & 1);
-    const bool ok = mbar_wait_bounded(&bars[st], parity, wait_limit);
+    const int sl = static_cast<int>(k % kBatchSlots);
+    const uint32_t parity = static_cast<uint32_t>((k / kBatchSlots) & 1);
+    const bool ok = mbar_wait_bounded(&bars[sl], parity, wait_limit);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         set_err(I.err, DEV_TIMEOUT_PASS);
         for (int64_t q = k; q < n_issued; ++q)
-          mbar_wait_bounded(&bars[q % S], static_cast<uint32_t>((q / S) & 1), wait_limit);
+          mbar_wait_bounded(&bars[q % kBatchSlots], static_cast<uint32_t>((q / kBatchSlots) & 1), wait_limit);
       }
       return;
     }
-    const V* sv = reinterpret_cast<const V*>(smem_raw + st * stage_bytes);
+    // poff[sl] was written before the barrier above
+    const V* sv = reinterpret_cast<const V*>(smem_raw + poff[sl]);
 
     TM dot[R];
 #pragma unroll
@@ -310,9 +366,9 @@ k_fused_pass_batch(const BatchInst* __restrict__ inst, const BatchSeg* __restric
       }
     }
     __syncthreads();
-    if (tid == 0 && n_issued < np) {
-      issue(n_issued);
-      ++n_issued;
+    if (tid == 0) {
+      while (try_issue(k + 1)) {
+      }
     }
   }
   if (cur_seg >= 0) flush_acc(cur_seg);

@@ -1752,8 +1752,10 @@ int batch_build(bicadmm_batch_ctx* b, int stage_kb, int S) {
     return bfail(b, BICADMM_ERR_UNSUPPORTED, "stage smaller than the widest row");
   const int ve = static_cast<int>(16 / b->asz);
   constexpr int NW = kPassThreads / 32;
-  // wide pass: stages | mbarriers | red[R][NW] | d[R]
-  b->smem = S * b->stage_bytes + S * sizeof(uint64_t) + static_cast<size_t>(R) * (NW + 1) * b->esz + 16;
+  // wide pass: ring of S stages | kBatchSlots mbarriers and ring offsets | the issuer's
+  // cursor | red[R][NW] | d[R]
+  b->smem = S * b->stage_bytes + kBatchSlots * (sizeof(uint64_t) + sizeof(uint32_t)) + sizeof(BatchCursor) +
+            static_cast<size_t>(R) * (NW + 1) * b->esz + 16;
   // narrow pass: stages | mbarriers | red and d (R * 32 rows each) | the row groups' A'd
   // partial sums (one vector per thread) | per-warp statistics
   b->smem_n = S * b->stage_bytes + S * sizeof(uint64_t) +
