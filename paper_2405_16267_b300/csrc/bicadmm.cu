@@ -856,8 +856,17 @@ int build_geometry(bicadmm_ctx* h) {
   }
   h->nslots = h->G + h->N;
   // CTAs per shard of k_dual (each loops over its columns): at most 32, so that a thread has
-  // a few columns (their loads are latency-bound) and the last-CTA ticket stays short
-  h->dual_chunks = static_cast<int>(std::min<int64_t>(32, (h->ldx + kDualThreads - 1) / kDualThreads));
+  // a few columns (their loads are latency-bound) and the last-CTA ticket stays short, and
+  // no more than the GPU holds at once over all shards (a second wave of CTAs would start
+  // only as the first one finishes)
+  int dual_occ = 0;
+  if (h->esz == 8)
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&dual_occ, k_dual<double, kDualThreads>, kDualThreads, 0));
+  else
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&dual_occ, k_dual<float, kDualThreads>, kDualThreads, 0));
+  const int64_t dual_wave = std::max<int64_t>(1, static_cast<int64_t>(dual_occ) * h->num_sms / h->N);
+  h->dual_chunks = static_cast<int>(std::min<int64_t>(
+      std::min<int64_t>(32, dual_wave), (h->ldx + kDualThreads - 1) / kDualThreads));
   return BICADMM_OK;
 }
 

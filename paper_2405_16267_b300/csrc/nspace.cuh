@@ -867,25 +867,50 @@ __device__ __forceinline__ void dual_final_sums(const double* __restrict__ part,
                                                 const double* __restrict__ cta_stats, int G,
                                                 double (&out)[5]) {
   constexpr int NW = DT / 32;
+  constexpr int U = 4;  // shards of a warp whose partial sums are loaded together
   __shared__ double fin[NW * 5];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double w[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  for (int ii = warp; ii < N; ii += NW) {
-    double s0 = 0.0, s1 = 0.0;
-    for (int c = lane; c < nch; c += 32) {
-      s0 += part[(static_cast<int64_t>(ii) * nch + c) * 2 + 0];
-      s1 += part[(static_cast<int64_t>(ii) * nch + c) * 2 + 1];
-    }
-    s0 = warp_sum(s0);
-    s1 = warp_sum(s1);
-    w[0] += sqrt(s0);
-    w[1] += sqrt(s1);
-  }
+  // The pass CTAs' statistics, two strided entries per thread in flight at once (the same
+  // order of additions as one entry at a time).
   double g[3] = {0.0, 0.0, 0.0};
-  for (int q = threadIdx.x; q < G; q += DT) {
-    g[0] += cta_stats[q * 4 + 0];
-    g[1] += cta_stats[q * 4 + 1];
-    g[2] += cta_stats[q * 4 + 2];
+  for (int q0 = threadIdx.x; q0 < G; q0 += 2 * DT) {
+    double v[2][3];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = q0 + h * DT;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) v[h][k] = q < G ? cta_stats[q * 4 + k] : 0.0;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) g[k] += v[h][k];
+  }
+  // The shard sums: U shards of a warp at a time (w, w + NW, ...), all their loads issued
+  // before the first warp sum; the square roots are added in shard order as before.
+  for (int ii0 = warp; ii0 < N; ii0 += U * NW) {
+    double s0[U], s1[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) s0[u] = s1[u] = 0.0;
+    for (int c = lane; c < nch; c += 32) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int ii = ii0 + u * NW;
+        if (ii < N) {
+          s0[u] += part[(static_cast<int64_t>(ii) * nch + c) * 2 + 0];
+          s1[u] += part[(static_cast<int64_t>(ii) * nch + c) * 2 + 1];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const double a0 = warp_sum(s0[u]), a1 = warp_sum(s1[u]);
+      if (ii0 + u * NW < N) {
+        w[0] += sqrt(a0);
+        w[1] += sqrt(a1);
+      }
+    }
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) w[2 + k] = warp_sum(g[k]);
@@ -958,6 +983,10 @@ k_dual(double* __restrict__ u, const double* __restrict__ x, const double* __res
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // thread 0 reads the iteration counter and the record's ||z|| (from earlier launches)
+  // before the sums, so that their latency overlaps the sums'
+  double zn0 = 0.0;
+  if (threadIdx.x == 0) zn0 = trace[gs->iter % trace_cap].znorm;
   double fs[5];
   dual_final_sums<DT>(part, N, nch, cta_stats, G, fs);
   {
@@ -967,7 +996,7 @@ k_dual(double* __restrict__ u, const double* __restrict__ x, const double* __res
       // column (one record each gets them, with ||z|| over all instances); one instance:
       // its own record.
       const int nq = ninst > 1 ? ninst : 1;
-      double zn = trace[gs->iter % trace_cap].znorm;
+      double zn = zn0;
       if (nq > 1) {
         double zn2 = 0.0;
         for (int q = 0; q < nq; ++q) {
