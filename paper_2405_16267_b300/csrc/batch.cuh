@@ -311,11 +311,11 @@ k_fused_pass_batch(const BatchInst* __restrict__ inst, const BatchSeg* __restric
         }
       }
     }
-#pragma unroll
-    for (int r = 0; r < R; ++r) dot[r] = warp_sum(dot[r]);
-    if (lane == 0) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) red[r * NW + warp] = dot[r];
+    {
+      // the warp's R row sums in one reduce-scatter (R - 1 + 5 - log2 R shuffles instead of
+      // 5 R): lane r (32 / R) holds row r's
+      const TM dsum = warp_reduce_scatter<R>(dot, lane);
+      if ((lane & (32 / R - 1)) == 0) red[(lane / (32 / R)) * NW + warp] = dsum;
     }
     __syncthreads();
 
