@@ -167,14 +167,14 @@ class ClockSampler:
 # DRAM traffic of one pass launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of a 20000-row launch of the same kernel, scaled by rows to the
 # 200000-row launch.  Reported only while the kernel sources are the captured ones.
-PASS_TRAFFIC = {"sources_sha256": "9f310ed63b3510744dd5a927080eb7a81e021a1e2750b8cfc320229f062d6757", "bytes_per_launch": 4.0519e+09,
+PASS_TRAFFIC = {"sources_sha256": "55c0b0a1e2e140e183d15c83d9823000ed48dfcc2b6d8bf539f9755eae87ffce", "bytes_per_launch": 4.0515e+09,
                 "capture": "profiles/k_fused_pass_sparse_logistic_200000x5000_fp32.md"}
 PASS_SOURCES = ["paper_2405_16267_b300/csrc/pass.cuh", "paper_2405_16267_b300/csrc/nspace.cuh",
                 "paper_2405_16267_b300/csrc/common.cuh"]
 
 
 # The same for the tensor-core softmax pass (60000-row capture scaled to 500000 rows).
-TC_TRAFFIC = {"sources_sha256": "9d3322901506c857262363a5fb08075b6f230607d76f9fa06bf516cede23a87b", "bytes_per_launch": 2.5971e+09,
+TC_TRAFFIC = {"sources_sha256": "b4105c4f6d30152bbae7a217a3a40b307f7ecc3dcace1198a3dbeba1ff4b0a2c", "bytes_per_launch": 2.5902e+09,
               "capture": "profiles/k_fused_pass_tc2_sparse_softmax_500000x2000x10_bf16.md"}
 TC_SOURCES = ["paper_2405_16267_b300/csrc/mc_tc2.cuh", "paper_2405_16267_b300/csrc/mc_tc.cuh",
               "paper_2405_16267_b300/csrc/nspace.cuh", "paper_2405_16267_b300/csrc/common.cuh",
@@ -182,7 +182,7 @@ TC_SOURCES = ["paper_2405_16267_b300/csrc/mc_tc2.cuh", "paper_2405_16267_b300/cs
 
 # The same kernel on the sparsity path (10 logistic instances as its columns; 60000-row
 # capture scaled to 500000 rows).
-PATH_TRAFFIC = {"sources_sha256": "9d3322901506c857262363a5fb08075b6f230607d76f9fa06bf516cede23a87b", "bytes_per_launch": 2.4537e+09,
+PATH_TRAFFIC = {"sources_sha256": "b4105c4f6d30152bbae7a217a3a40b307f7ecc3dcace1198a3dbeba1ff4b0a2c", "bytes_per_launch": 2.4557e+09,
                 "capture": "profiles/k_fused_pass_tc_logistic_path10_500000x2000_bf16.md"}
 
 

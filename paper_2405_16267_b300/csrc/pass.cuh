@@ -278,11 +278,17 @@ k_fused_pass(const TA* __restrict__ A, int64_t lda, const TM* __restrict__ xlo_i
         }
       }
     }
+    if constexpr ((R & (R - 1)) == 0) {
+      // the warp's R row sums in one reduce-scatter: lane r (32 / R) holds row r's
+      const TM dsum = warp_reduce_scatter<R>(dot, lane);
+      if ((lane & (32 / R - 1)) == 0) red[(lane / (32 / R)) * NW + warp] = dsum;
+    } else {
 #pragma unroll
-    for (int r = 0; r < R; ++r) dot[r] = warp_sum(dot[r]);
-    if (lane == 0) {
+      for (int r = 0; r < R; ++r) dot[r] = warp_sum(dot[r]);
+      if (lane == 0) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) red[r * NW + warp] = dot[r];
+        for (int r = 0; r < R; ++r) red[r * NW + warp] = dot[r];
+      }
     }
     __syncthreads();
     if constexpr (kHoldA) {  // every thread holds its part of the panel: reload the stage
