@@ -14,7 +14,8 @@ buffers (create + setup + K iterations + get_x, H2D of A and b inside the timed 
 The default line also carries `legs.softmax` (the 500000 x 2000 x 10 BF16 softmax workload's
 value, tensor-core pass roofline and end-to-end figure) and `legs.path` (10 logistic
 instances at kappa 20..800 on one 500000 x 2000 BF16 A, one tensor-core pass per sweep for
-all of them, against one single-kappa handle); skip both with --no-legs.
+all of them, against one single-kappa handle) and `legs.batch` (256 uneven FP32 instances
+advanced by batched launches); skip them with --no-legs.
 
 --impl reference times the FP64 CPU oracle on a bounded sample (one of the 16 shards): its
 steps are shard iterations (steps x ms_per_step = the time spent) and its value is the
@@ -58,7 +59,7 @@ def parse():
     ap.add_argument("--inner", type=int, default=1, help="inner sharing sweeps J per iteration")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance leg")
     ap.add_argument("--no-legs", action="store_true",
-                    help="default workload only: skip the softmax leg added to its line")
+                    help="default workload only: skip the softmax, path and batch legs added to its line")
     ap.add_argument("--workload", default="logistic", choices=["logistic", "softmax", "batch", "serve", "path"],
                     help="softmax: 500000 x 2000 BF16, 10 classes (tensor-core pass); "
                          "batch: 256 uneven instances advanced by batched launches; "
@@ -690,6 +691,23 @@ def run_batch(args, rank, world):
     }
 
 
+def batch_leg(args):
+    """The batched workload's figures (256 uneven FP32 instances, autotuned tiling, CUDA
+    graph), measured in the default run: its value, per-instance rate, whole-iteration
+    roofline and speedup over the same handles stepped one at a time."""
+    import copy
+    a = copy.copy(args)
+    a.steps = min(args.steps, 50)
+    a.warmup = max(args.warmup, 3)
+    a.batch = 256
+    a.precision = "fp32"
+    r = run_batch(a, 0, 1)
+    keep = ("metric", "value", "unit", "steps", "ms_per_step", "dtype", "config",
+            "instance_iters_per_s", "roofline", "batch_speedup_vs_sequential", "gpu_launches",
+            "clocks")
+    return {k: r[k] for k in keep if k in r}
+
+
 # ----------------------------------------------------------------------------- serve
 
 def run_serve(args, rank, world):
@@ -934,7 +952,7 @@ def main():
             res["cpu_baseline"] = run_oracle_sample(dict(WORKLOAD), steps=8, warmup=1, budget_s=20.0)
         if world == 1 and not args.no_legs and args.m is None:
             res["legs"] = {}
-            for name, leg in (("softmax", softmax_leg), ("path", path_leg)):
+            for name, leg in (("softmax", softmax_leg), ("path", path_leg), ("batch", batch_leg)):
                 try:
                     res["legs"][name] = leg(args)
                 except Exception as exc:  # a leg never costs the headline line
