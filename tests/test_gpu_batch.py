@@ -204,3 +204,36 @@ def test_batch_rejects_bad_requests():
     finally:
         for s in sol:
             s.close()
+
+
+def test_batch_ring_mixed_panel_sizes():
+    """Wide-row instances whose panels span 19 to 96 KB in the default one-ring tiling (96 KB
+    in FP32), tall enough that each CTA of the pass streams a few dozen panels of several
+    instances through its ring (placement next to the newest panel, wrapping to the start):
+    each instance within 1e-4 of itself stepped alone."""
+    import torch
+    specs = [(bc.LOSS_SQUARED, 12000, 600, 3, 2, 8), (bc.LOSS_SQHINGE, 12000, 1500, 4, 3, 20),
+             (bc.LOSS_LOGISTIC, 12000, 2500, 3, 5, 30), (bc.LOSS_SQUARED, 12000, 4000, 4, 8, 40)]
+    probs = [synth.small_problem(loss, m=m, n=n, nnz=kappa, N=N, M=M, kappa=kappa, seed=500 + k)
+             for k, (loss, m, n, N, M, kappa) in enumerate(specs)]
+    iters = 8
+    alone = []
+    for s in _solvers(probs, bc.PREC_FP32):
+        s.step(iters)
+        alone.append(s.state())
+        s.close()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sol = _solvers(probs, bc.PREC_FP32)
+        b = bc.batch_create(sol, stream=stream, flags=0)
+        assert bc.batch_tiling(b) == (96, 1)
+        launches = bc.batch_step(b, iters)
+        stream.synchronize()
+        bc.batch_destroy(b)
+        states = [s.state() for s in sol]
+        for s in sol:
+            s.close()
+    assert launches == 4 * iters  # no narrow instance: x-update, pass, consensus, dual
+    for st, want, P in zip(states, alone, probs):
+        for k in ("z", "x", "omega", "nu"):
+            assert rel_err(st[k], want[k]) <= 1e-4, (P.name, k)
