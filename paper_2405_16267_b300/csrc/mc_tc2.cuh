@@ -298,7 +298,8 @@ k_fused_pass_tc2(const __grid_constant__ CUtensorMap tmap, int64_t lda,
           }
           unsigned char* dst = ring + st * kTc2StageBytes;
           mbar_arrive_expect_tx(&full[st], kTc2StageABytes + (fwd ? kTc2WBytes : 0));
-          const int x0 = (sl0 + sg) * 128;
+          // the backward takes its slabs newest first (the shortest reuse distances in L2)
+          const int x0 = (sl0 + (fwd ? sg : nsl - 1 - sg)) * 128;
           tma_load_2d_hint(dst, &tmap, x0, static_cast<int>(row0), &full[st], fwd ? keep : drop);
           tma_load_2d_hint(dst + kTc2BoxBytes, &tmap, x0 + 64, static_cast<int>(row0), &full[st],
                            fwd ? keep : drop);
@@ -343,7 +344,7 @@ k_fused_pass_tc2(const __grid_constant__ CUtensorMap tmap, int64_t lda,
                              dsc(tk, sa + kTc2StageABytes + bx * 4096 + ks * 32), IDESC_FWD,
                              (sg | bx | ks) != 0 ? 1u : 0u);
         } else {
-          const uint32_t d2 = tmem + kTc2D2Col + 32 * sg;
+          const uint32_t d2 = tmem + kTc2D2Col + 32 * (nsl - 1 - sg);
           const uint32_t db = ds_a + (k & 1) * kTc2DBytes;
 #pragma unroll
           for (int ks = 0; ks < 8; ++ks)
