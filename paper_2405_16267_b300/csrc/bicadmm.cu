@@ -388,7 +388,7 @@ int launch_pass_tc2_c(bicadmm_ctx* h, bool with_consensus, int op, int* blocks) 
     return BICADMM_OK;
   }
   PassGeometry geo{h->d_shard_row0, h->d_panel_start, h->N, h->P_panels, -1};
-  const int ncons = with_consensus ? h->ninst : 0;
+  const int ncons = with_consensus ? tc2_cons_ctas(h->ninst) : 0;
   kern<<<2 * h->G + ((ncons + 1) & ~1), kTc2Threads, h->pass_smem, h->stream>>>(
       h->tmap, h->lda, h->wpk, h->nslab, h->ldx, h->K,
       static_cast<const float*>(h->b), static_cast<float*>(h->omega), static_cast<float*>(h->nu),
@@ -832,8 +832,8 @@ int build_geometry(bicadmm_ctx* h) {
   if (rc != BICADMM_OK) return rc;
   if (occ < 1) return fail(h, BICADMM_ERR_UNSUPPORTED, "A-pass variant cannot be resident on an SM");
   // One resident slot is kept for each consensus CTA that rides on the last pass (the pair
-  // kernel: occ co-resident pairs, the consensus CTAs taking whole pairs).
-  const int64_t slots_total = h->tc2 ? static_cast<int64_t>(occ) - (h->ninst + 1) / 2
+  // kernel: occ co-resident pairs, its at most two consensus CTAs taking one pair).
+  const int64_t slots_total = h->tc2 ? static_cast<int64_t>(occ) - (tc2_cons_ctas(h->ninst) + 1) / 2
                                      : static_cast<int64_t>(occ) * h->num_sms - h->ninst;
   if (slots_total < 1) return fail(h, BICADMM_ERR_UNSUPPORTED, "A-pass needs at least two resident CTAs");
   // At least 4 panels per CTA: a shard's A'd partial sums are spread over one slot per CTA

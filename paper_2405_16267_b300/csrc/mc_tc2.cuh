@@ -139,9 +139,18 @@ struct Tc2Geo {
   }
 };
 
+// Consensus CTAs of a launch at most: the instances of a path are spread over them and each
+// runs its instances' steps one after another (the list-form step of one instance is short
+// beside the pass), so that the other pairs stay on the panel stream.
+constexpr int kTc2ConsCtas = 2;
+__host__ __device__ constexpr int tc2_cons_ctas(int ninst) {
+  return ninst < kTc2ConsCtas ? ninst : kTc2ConsCtas;
+}
+
 // ------------------------------------------------------------------ k_fused_pass_tc2
 // Grid: 2 G panel CTAs (G pairs, a pair = one cluster) and, on the last sweep, the
-// consensus CTAs (one per instance, their count rounded up to even; a spare one returns).
+// consensus CTAs (tc2_cons_ctas of the instances, their count rounded up to even; a spare
+// one returns).
 template <int KC>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTc2Threads, 1)
 k_fused_pass_tc2(const __grid_constant__ CUtensorMap tmap, int64_t lda,
@@ -151,11 +160,16 @@ k_fused_pass_tc2(const __grid_constant__ CUtensorMap tmap, int64_t lda,
                  float Mf, float rho_l, int newton_iters, int* __restrict__ err,
                  long long wait_limit, ConsensusArgs cons, int path_loss) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  const int ncons = consensus_ctas(cons);
-  const int npc = static_cast<int>(gridDim.x) - ((ncons + 1) & ~1);  // panel CTAs
+  const int ninst_c = consensus_ctas(cons);
+  const int nct = tc2_cons_ctas(ninst_c);
+  const int npc = static_cast<int>(gridDim.x) - ((nct + 1) & ~1);  // panel CTAs
   if (static_cast<int>(blockIdx.x) >= npc) {
-    const int q = static_cast<int>(blockIdx.x) - npc;
-    if (q < ncons) consensus_block<kTc2Threads, kConsMW, true>(consensus_instance(cons, q), smem_raw);
+    // instances q0, q0 + nct, ... (nct >= 1 whenever q0 < ninst_c)
+    const int q0 = static_cast<int>(blockIdx.x) - npc;
+    for (int q = q0; q < ninst_c; q += nct) {
+      if (q != q0) __syncthreads();  // the previous instance's shared memory is free
+      consensus_block<kTc2Threads, kConsMW, true>(consensus_instance(cons, q), smem_raw);
+    }
     return;
   }
   constexpr int S = tc2_stages<KC>();
